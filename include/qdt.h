@@ -1,0 +1,170 @@
+/*
+ * qdt.h -- C ABI of the GB300 quaternion Dirac-Coulomb-Breit AO->MO integral
+ * transformation library (libqdt.so).
+ *
+ * The library computes the four-index spinor MO integrals (pq|rs) of
+ * arXiv 2606.04316 (Eqs. AOtoMO, DCInt, GauntInt, gaugeInt) by the AO-driven
+ * direct quaternion-density route (Sec. 2.4, Eqs. Den, QuaternionScatter,
+ * firsthalf, secondhalf) with density-weighted Cauchy-Schwarz screening
+ * (Sec. 2.5, Eq. SchwarzDen).  Every arithmetic step of a transformation runs
+ * in the library's own CUDA kernels on one sm_103a GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Units: atomic units (bohr, hartree).
+ *  - Large-component basis: contracted Cartesian Gaussians
+ *      chi_mu = N_mu sum_p d_p (x-A_x)^i (y-A_y)^j (z-A_z)^k exp(-alpha_p |r-A|^2),
+ *    every Cartesian component normalised to <chi|chi> = 1 by the library;
+ *    components of a shell of order l in the order i = l..0, j = l-i..0.
+ *  - Small-component basis: the derivative functions d/dr_K chi_mu, K = x,y,z,
+ *    stored at index 3 mu + K (nS = 3 nL; restricted kinetic balance, Eq. RKB,
+ *    with the factor sigma.p/(2c) carried by the coefficients).
+ *  - MO coefficients are Kramers-restricted quaternions q = q0 + q1 i + q2 j + q3 k
+ *    per basis row and Kramers pair k.  Spinor 2k has two-spinor coefficients
+ *    (alpha, beta) = (q0 + i q1, q2 + i q3); spinor 2k+1 is its Kramers partner
+ *    (-conj(beta), conj(alpha)).
+ *  - Mulliken order: (pq|rs) = int int psi_p^+ O psi_q (1) K(r12) psi_r^+ O psi_s (2).
+ *      QDT_COULOMB: O = 1, K = 1/r12                          (Eqs. Coulomb, DCInt)
+ *      QDT_GAUNT:   sum_J O = alpha_J on both sides, K = 1/r12 (Eq. GauntInt)
+ *      QDT_GAUGE:   sum_IJ alpha_I (1), alpha_J (2), K = r_I r_J / r^3 (Eq. gaugeInt)
+ *    The Breit operator of Eq. breit is -1/2 GAUNT - 1/2 GAUGE; blocks are
+ *    returned unsigned and separately.
+ *  - Screening: shell quartet (AB|CD) is skipped iff Q_AB * (Q_CD * Dmax_CD) < tau,
+ *    Q = max sqrt((ab|ab)) over the shell pair (Coulomb kernel, also for the
+ *    gauge block), Dmax = max |real part| of the symmetrised quaternion density
+ *    of the ket pair over its functions and all active Kramers-pair columns.
+ *    tau = 0 keeps every quartet.
+ *
+ * Packed output layout (one block after another, COULOMB, GAUNT, GAUGE order
+ * of the bits set in `blocks`): let n = k_end - k_begin active Kramers pairs,
+ * pair index pq = P n - P (P-1)/2 + (Q - P) for P <= Q (nP = n(n+1)/2 pairs), and
+ * quadruple index t = pq nP - pq (pq-1)/2 + (rs - pq) for pq <= rs.  Entry t holds
+ * 16 doubles O[i][j] (i, j = 0..3) = sum_ab,cd Dq_i^{PQ}(ab) (ab|K|cd) Dq_j^{RS}(cd),
+ * where Dq_0..3 are Re A, Im A, Re B, Im B of the symmetrised spinor densities
+ * A = D^{2P,2Q}, B = D^{2P+1,2Q} (Eq. QuaternionScatter in real form).
+ * qdt_unpack() expands it to the full complex (pq|rs).
+ *
+ * Errors: every int-returning call returns QDT_OK (0) or a negative QDT_ERR_*;
+ * qdt_last_error() then describes the failure.  No call aborts the process
+ * and no exception crosses the ABI.  A context is not thread-safe: use one
+ * context per host thread.
+ *
+ * Pointers: inputs of qdt_set_basis / qdt_set_coefficients and the output of
+ * qdt_transform may be host or device pointers (the library checks with
+ * cudaPointerGetAttributes); the library copies inputs and never keeps a
+ * caller pointer after the call returns.  All work is ordered on the
+ * context's stream; qdt_transform returns after the output is complete.
+ */
+#ifndef QDT_H
+#define QDT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QDT_OK 0
+#define QDT_ERR_ARG (-1)            /* invalid argument or size                    */
+#define QDT_ERR_OOM (-2)            /* device allocation failed                    */
+#define QDT_ERR_CUDA (-3)           /* a CUDA runtime call or kernel failed        */
+#define QDT_ERR_STATE (-4)          /* basis or coefficients not set               */
+#define QDT_ERR_UNIMPLEMENTED (-5)  /* option not built                            */
+#define QDT_ERR_TIMEOUT (-6)        /* a bounded device wait gave up               */
+#define QDT_ERR_ADMISSION (-7)      /* request does not fit the memory pool        */
+
+#define QDT_COULOMB 1u
+#define QDT_GAUNT 2u
+#define QDT_GAUGE 4u
+
+#define QDT_FP64 0                  /* all-FP64 contractions                        */
+#define QDT_SPLIT 1                 /* Ozaki BF16 slices, exact FP32 chunks, FP64 recombination */
+
+#define QDT_MAX_L 2                 /* largest large-component shell order accepted */
+
+typedef struct qdt_ctx qdt_ctx;
+
+/* Per-call statistics (filled when the pointer is non-NULL). */
+typedef struct {
+    double ms_total;            /* wall time of the call on the stream (CUDA events) */
+    double ms_density;          /* quaternion pair density (Eq. Den)                  */
+    double ms_screen;           /* screening: ket ordering and survivor counts        */
+    double ms_eri;              /* AO integral tiles (stage i)                        */
+    double ms_half1;            /* first half-transform GEMMs (Eq. firsthalf)         */
+    double ms_half2;            /* second half-transform GEMMs (Eq. secondhalf)       */
+    double ms_pack;             /* packing of the canonical quadruples                */
+    double flops_half1;         /* algorithmic FP64-equivalent flops, first half      */
+    double flops_half2;         /* algorithmic FP64-equivalent flops, second half     */
+    long long quartets_total[3];/* shell quartets per block (Coulomb, Gaunt, gauge)   */
+    long long quartets_kept[3]; /* shell quartets surviving the screening             */
+    long long eri_values;       /* AO integral values produced                        */
+    int kernel_launches;        /* library kernels launched by the call               */
+    int precision;              /* QDT_FP64 or QDT_SPLIT                              */
+    int slices;                 /* BF16 slices per operand in the split form          */
+} qdt_stats;
+
+/*
+ * Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to
+ * order all work on, or NULL for a stream the context creates and owns.
+ * Returns QDT_OK and *ctx, or QDT_ERR_CUDA / QDT_ERR_OOM (then *ctx = NULL).
+ */
+int qdt_create(qdt_ctx **ctx, int device, void *cuda_stream);
+
+/* Release every device and host resource of the context (NULL is allowed). */
+void qdt_destroy(qdt_ctx *ctx);
+
+/*
+ * Set the large-component basis (the small-component derivative basis follows
+ * from it).  xyz[n_centers][3]; per shell: centre index, order l (0..QDT_MAX_L),
+ * number of primitives; exps/coefs hold sum(shell_nprim) exponents and raw
+ * contraction coefficients, shell after shell.  Builds the shell-pair tables,
+ * the Hermite expansion coefficients and the Schwarz diagonals on the GPU
+ * (Eq. SchwarzDen).  Invalidates the coefficients.  QDT_ERR_ARG on bad sizes.
+ */
+int qdt_set_basis(qdt_ctx *ctx, int n_centers, const double *xyz, int n_shells,
+                  const int *shell_center, const int *shell_l, const int *shell_nprim,
+                  const double *exps, const double *coefs);
+
+/* Number of large-component functions nL of the current basis (0 if none). */
+int qdt_num_functions(const qdt_ctx *ctx);
+
+/*
+ * Set the quaternion MO coefficients: CL[nL][nK][4] and CS[3 nL][nK][4],
+ * row-major doubles (host or device).  QDT_ERR_STATE without a basis.
+ */
+int qdt_set_coefficients(qdt_ctx *ctx, int nK, const double *CL, const double *CS);
+
+/* Bytes of the packed output of qdt_transform for these blocks and range. */
+size_t qdt_packed_size(const qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end);
+
+/*
+ * Transform: packed (pq|rs) for the Kramers pairs [k_begin, k_end) of the
+ * current coefficients, for every block bit set in `blocks`, with Schwarz
+ * threshold `schwarz_tau` >= 0 and `precision` QDT_FP64 or QDT_SPLIT.
+ * `out` (host or device, caller-owned) receives qdt_packed_size() bytes;
+ * `out_bytes` must be at least that.  Device scratch is allocated and kept by
+ * the context between calls.  `stats` may be NULL.
+ */
+int qdt_transform(qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end, double schwarz_tau,
+                  int precision, double *out, size_t out_bytes, qdt_stats *stats);
+
+/*
+ * Expand one packed block (`block` = QDT_COULOMB, QDT_GAUNT or QDT_GAUGE) of n
+ * Kramers pairs to the full complex array full[2n][2n][2n][2n] of
+ * interleaved (re, im) doubles, on the context's GPU.  Both pointers are
+ * device pointers.
+ */
+int qdt_unpack(qdt_ctx *ctx, const double *packed, int n_kramers, unsigned block, double *full);
+
+/* Text of the last error of this context ("" if none); valid until the next call. */
+const char *qdt_last_error(const qdt_ctx *ctx);
+
+/* Library version string. */
+const char *qdt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QDT_H */

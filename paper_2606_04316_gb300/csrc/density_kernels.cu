@@ -1,0 +1,346 @@
+// density_kernels.cu -- quaternion pair densities (paper Eqs. Den and
+// QuaternionScatter), density-weighted Schwarz screening order (Eq. SchwarzDen)
+// and the row gathers / packing that feed and drain the contractions.
+#include <math.h>
+
+#include "qdt_internal.cuh"
+
+namespace qdt {
+
+struct cplx { double re, im; };
+__device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ inline cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__device__ inline cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ inline cplx cconj(cplx a) { return {a.re, -a.im}; }
+__device__ inline cplx cneg(cplx a) { return {-a.re, -a.im}; }
+__device__ inline cplx ctimes_i(cplx a) { return {-a.im, a.re}; }
+
+// Two-spinor coefficients of row f, Kramers pair k: alpha = q0 + i q1, beta = q2 + i q3.
+__device__ inline void spinor(const double *Cq, int nK, int f, int k, cplx &al, cplx &be) {
+    const double *q = Cq + ((size_t)f * nK + k) * 4;
+    al = {q[0], q[1]};
+    be = {q[2], q[3]};
+}
+
+__device__ inline void decode_fp(const PairDev &pr, int nfb, int fp, int &fa, int &fb) {
+    if (pr.sa == pr.sb) {
+        int a = 0, base = 0;
+        while (base + (nfb - a) <= fp) { base += nfb - a; ++a; }
+        fa = a; fb = a + (fp - base);
+    } else {
+        fa = fp / nfb; fb = fp % nfb;
+    }
+}
+
+__device__ inline void atomic_max_nonneg(double *addr, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMax((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// Coulomb: row (a,b) of a class-0 pair, columns (RS, part):
+//   A = D^{RS}_{ab} + D^{RS}_{ba},  B = D^{R'S}_{ab} + D^{R'S}_{ba}  (a != b; a == b: single term)
+//   D^{xy}_{ab} = sum_tau conj(C[a,tau,x]) C[b,tau,y];  for the partner R':
+//   conj(C[a,alpha,R']) = -C[a,beta,R],  conj(C[a,beta,R']) = C[a,alpha,R].
+__global__ void density_coulomb_kernel(const PairDev *pairs, const int *bra_order,
+                                       const ShellDev *shells, const double *Cq, int nK, int k0,
+                                       const int *rsR, const int *rsS, int nRS, double *D,
+                                       double *Dmax) {
+    const int sp = bra_order[blockIdx.x];
+    const PairDev pr = pairs[sp];
+    const ShellDev A = shells[pr.sa], B = shells[pr.sb];
+    const long long ld = 4LL * nRS;
+    double vmax = 0.0;
+    for (long long idx = threadIdx.x; idx < (long long)pr.nfp * nRS; idx += blockDim.x) {
+        int fp = (int)(idx / nRS), rs = (int)(idx - (long long)fp * nRS);
+        int fa, fb;
+        decode_fp(pr, B.nfunc, fp, fa, fb);
+        int ia = A.foff + fa, ib = B.foff + fb;
+        int R = k0 + rsR[rs], S = k0 + rsS[rs];
+        cplx aaR, abR, aaS, abS, baR, bbR, baS, bbS;
+        spinor(Cq, nK, ia, R, aaR, abR);
+        spinor(Cq, nK, ia, S, aaS, abS);
+        spinor(Cq, nK, ib, R, baR, bbR);
+        spinor(Cq, nK, ib, S, baS, bbS);
+        cplx Dab = cadd(cmul(cconj(aaR), baS), cmul(cconj(abR), bbS));
+        cplx Bab = csub(cmul(aaR, bbS), cmul(abR, baS));
+        cplx Av = Dab, Bv = Bab;
+        if (ia != ib) {
+            cplx Dba = cadd(cmul(cconj(baR), aaS), cmul(cconj(bbR), abS));
+            cplx Bba = csub(cmul(baR, abS), cmul(bbR, aaS));
+            Av = cadd(Av, Dba);
+            Bv = cadd(Bv, Bba);
+        }
+        double *o = D + (pr.rowoff + fp) * ld + 4LL * rs;
+        o[0] = Av.re; o[1] = Av.im; o[2] = Bv.re; o[3] = Bv.im;
+        vmax = fmax(vmax, fmax(fmax(fabs(Av.re), fabs(Av.im)), fmax(fabs(Bv.re), fabs(Bv.im))));
+    }
+    // block max -> Dmax[sp]
+    __shared__ double red[256];
+    red[threadIdx.x] = vmax;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomic_max_nonneg(Dmax + sp, red[0]);
+}
+
+// sigma_J between the spin components: c = (conj(C[u,alpha,x]), conj(C[u,beta,x])),
+// d = (C[v,alpha,y], C[v,beta,y]).
+__device__ inline cplx sigma_form(int J, cplx c1, cplx c2, cplx d1, cplx d2) {
+    if (J == 0) return cadd(cmul(c1, d2), cmul(c2, d1));                          // sigma_x
+    if (J == 1) return ctimes_i(csub(cmul(c2, d1), cmul(c1, d2)));                // sigma_y
+    return csub(cmul(c1, d1), cmul(c2, d2));                                      // sigma_z
+}
+
+// Gaunt / gauge: rows (a in L, b in S), columns (J, RS, part) of the folded
+// L-S alpha densities D^J_{ab} + D^J_{ba} (Eqs. GauntInt, gaugeInt).
+__global__ void density_gaunt_kernel(const PairDev *pairs, const int *bra_order,
+                                     const ShellDev *shells, const double *Cq, int nK, int k0,
+                                     const int *rsR, const int *rsS, int nRS, double *D,
+                                     double *Dmax) {
+    const int sp = bra_order[blockIdx.x];
+    const PairDev pr = pairs[sp];
+    const ShellDev A = shells[pr.sa], B = shells[pr.sb];
+    const long long ld = 12LL * nRS;
+    double vmax = 0.0;
+    for (long long idx = threadIdx.x; idx < (long long)pr.nfp * nRS; idx += blockDim.x) {
+        int fp = (int)(idx / nRS), rs = (int)(idx - (long long)fp * nRS);
+        int fa = fp / B.nfunc, fb = fp % B.nfunc;
+        int ia = A.foff + fa, ib = B.foff + fb;
+        int R = k0 + rsR[rs], S = k0 + rsS[rs];
+        cplx aaR, abR, aaS, abS, baR, bbR, baS, bbS;
+        spinor(Cq, nK, ia, R, aaR, abR);
+        spinor(Cq, nK, ia, S, aaS, abS);
+        spinor(Cq, nK, ib, R, baR, bbR);
+        spinor(Cq, nK, ib, S, baS, bbS);
+        for (int J = 0; J < 3; ++J) {
+            // x = R: (conj alpha, conj beta); x = R': (-beta, alpha)
+            cplx A1 = sigma_form(J, cconj(aaR), cconj(abR), baS, bbS);
+            cplx A2 = sigma_form(J, cconj(baR), cconj(bbR), aaS, abS);
+            cplx B1 = sigma_form(J, cneg(abR), aaR, baS, bbS);
+            cplx B2 = sigma_form(J, cneg(bbR), baR, aaS, abS);
+            cplx Av = cadd(A1, A2), Bv = cadd(B1, B2);
+            double *o = D + (pr.rowoff + fp) * ld + (long long)J * 4 * nRS + 4LL * rs;
+            o[0] = Av.re; o[1] = Av.im; o[2] = Bv.re; o[3] = Bv.im;
+            vmax = fmax(vmax, fmax(fmax(fabs(Av.re), fabs(Av.im)), fmax(fabs(Bv.re), fabs(Bv.im))));
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = vmax;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomic_max_nonneg(Dmax + sp, red[0]);
+}
+
+void launch_density(bool gaunt, const PairDev *pairs, const int *bra_order, int nsp,
+                    const ShellDev *shells, const double *Cq, int nK, int k0, const int *rsR,
+                    const int *rsS, int nRS, double *D, double *Dmax, cudaStream_t s) {
+    if (nsp <= 0) return;
+    if (gaunt)
+        density_gaunt_kernel<<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
+    else
+        density_coulomb_kernel<<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
+    QDT_CHECK_LAUNCH();
+}
+
+// ----------------------------------------------------------- ket ordering
+// w_CD = Q_CD * Dmax_CD; ket positions sorted by w descending (ties: pair id
+// ascending) by rank counting.  A bra pair AB keeps exactly the ket prefix
+// with Q_AB * w >= tau (the product is monotone in w).
+__global__ void ket_rank_kernel(const double *Q, const double *Dmax, int n, double *w_sorted,
+                                int *ket_sp) {
+    __shared__ double tile[1024];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double wi = (i < n) ? Q[i] * Dmax[i] : 0.0;
+    int rank = 0;
+    for (int j0 = 0; j0 < n; j0 += 1024) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < 1024; j += blockDim.x)
+            tile[j] = (j0 + j < n) ? Q[j0 + j] * Dmax[j0 + j] : -1.0;
+        __syncthreads();
+        if (i < n) {
+            int jn = min(1024, n - j0);
+            for (int j = 0; j < jn; ++j) {
+                double wj = tile[j];
+                rank += (wj > wi) || (wj == wi && j0 + j < i);
+            }
+        }
+    }
+    if (i < n) {
+        ket_sp[rank] = i;
+        w_sorted[rank] = wi;
+    }
+}
+
+// exclusive prefix sums of nfp over the sorted ket order (single CTA)
+__global__ void ket_col_kernel(const PairDev *pairs, const int *ket_sp, int n, long long *col) {
+    __shared__ long long part[1024];
+    long long carry = 0;
+    for (int base = 0; base < n; base += 1024) {
+        int i = base + threadIdx.x;
+        long long v = (i < n) ? pairs[ket_sp[i]].nfp : 0;
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            long long t = (threadIdx.x >= off) ? part[threadIdx.x - off] : 0;
+            __syncthreads();
+            part[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < n) col[i] = carry + part[threadIdx.x] - v;
+        long long tot = part[1023];
+        __syncthreads();
+        carry += tot;
+    }
+    if (threadIdx.x == 0) col[n] = carry;
+}
+
+// prefix[sp] = number of sorted ket positions kept by bra pair sp
+__global__ void prefix_kernel(const double *Q, const double *w_sorted, int n, double tau, int *prefix) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double q = Q[i];
+    int lo = 0, hi = n;                       // first position with q * w < tau
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (q * w_sorted[mid] >= tau) lo = mid + 1; else hi = mid;
+    }
+    prefix[i] = lo;
+}
+
+void launch_ket_order(const double *Q, const double *Dmax, int nsp, double *w, int *ket_sp,
+                      cudaStream_t s) {
+    if (nsp <= 0) return;
+    ket_rank_kernel<<<(nsp + 255) / 256, 256, 0, s>>>(Q, Dmax, nsp, w, ket_sp);
+    QDT_CHECK_LAUNCH();
+}
+
+void launch_ket_columns(const PairDev *pairs, const int *ket_sp, int nsp, long long *ket_col,
+                        cudaStream_t s) {
+    ket_col_kernel<<<1, 1024, 0, s>>>(pairs, ket_sp, nsp, ket_col);
+    QDT_CHECK_LAUNCH();
+}
+
+void launch_prefix_lengths(const double *Q, const double *w_sorted, int nsp, double tau, int *prefix,
+                           cudaStream_t s) {
+    if (nsp <= 0) return;
+    prefix_kernel<<<(nsp + 255) / 256, 256, 0, s>>>(Q, w_sorted, nsp, tau, prefix);
+    QDT_CHECK_LAUNCH();
+}
+
+// dst rows of sorted ket position k  <-  src rows of its pair (bra order)
+__global__ void gather_rows_kernel(const double *src, const PairDev *pairs, const int *ket_sp,
+                                   const long long *ket_col, long long rowlen, double *dst) {
+    int k = blockIdx.x;
+    PairDev pr = pairs[ket_sp[k]];
+    const double *s = src + pr.rowoff * rowlen;
+    double *d = dst + ket_col[k] * rowlen;
+    long long n = (long long)pr.nfp * rowlen;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
+}
+
+void launch_gather_rows(const double *src, const PairDev *pairs, const int *ket_sp,
+                        const long long *ket_col, int nsp, long long rowlen, double *dst,
+                        cudaStream_t s) {
+    if (nsp <= 0) return;
+    gather_rows_kernel<<<nsp, 256, 0, s>>>(src, pairs, ket_sp, ket_col, rowlen, dst);
+    QDT_CHECK_LAUNCH();
+}
+
+__global__ void zero_kernel(double *p, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = 0.0;
+}
+
+void launch_zero(double *p, long long n, cudaStream_t s) {
+    if (n <= 0) return;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    zero_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, n);
+    QDT_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------- packing
+// out[t][16], t = pq nP - pq(pq-1)/2 + (rs - pq) for pq <= rs:
+// out[t][4i+j] = O[4 pq + i][4 rs + j]
+__global__ void pack_kernel(const double *O, long long ldo, int nP, double *out) {
+    int pq = blockIdx.y;
+    for (int rs = pq + blockIdx.x * blockDim.x + threadIdx.x; rs < nP; rs += gridDim.x * blockDim.x) {
+        long long t = (long long)pq * nP - (long long)pq * (pq - 1) / 2 + (rs - pq);
+        double *o = out + t * 16;
+        for (int i = 0; i < 4; ++i) {
+            const double *src = O + (4LL * pq + i) * ldo + 4LL * rs;
+            for (int j = 0; j < 4; ++j) o[4 * i + j] = src[j];
+        }
+    }
+}
+
+void launch_pack(const double *O, long long ldo, int nKa, double *out, cudaStream_t s) {
+    int nP = nKa * (nKa + 1) / 2;
+    if (nP <= 0) return;
+    dim3 grid((nP + 255) / 256, nP);
+    pack_kernel<<<grid, 256, 0, s>>>(O, ldo, nP, out);
+    QDT_CHECK_LAUNCH();
+}
+
+// -------------------------------------------------------------- unpacking
+// Symmetrised spinor density of spinor pair (x, y) as sign * [conj] Z with
+// Z = A (which 0) or B (which 1) of Kramers pairs X <= Y:
+//   (x, y) = (X, Y): A;  (X', Y): B;  (X, Y'): -conj B (Coulomb), +conj B (alpha);
+//   (X', Y'): conj A (Coulomb), -conj A (alpha);  X > Y: conj of the swapped pair.
+struct DMap { int X, Y, which; double sign; bool cj; };
+
+__device__ inline DMap dmap(int x, int y, bool alpha) {
+    int X = x >> 1, bx = x & 1, Y = y >> 1, by = y & 1;
+    bool swap = X > Y;
+    if (swap) { int t = X; X = Y; Y = t; t = bx; bx = by; by = t; }
+    DMap m;
+    m.X = X; m.Y = Y;
+    if (!bx && !by) { m.which = 0; m.sign = 1.0; m.cj = false; }
+    else if (bx && !by) { m.which = 1; m.sign = 1.0; m.cj = false; }
+    else if (!bx && by) { m.which = 1; m.sign = alpha ? 1.0 : -1.0; m.cj = true; }
+    else { m.which = 0; m.sign = alpha ? -1.0 : 1.0; m.cj = true; }
+    if (swap) m.cj = !m.cj;
+    return m;
+}
+
+__global__ void unpack_kernel(const double *packed, int nKa, int alpha, double *full) {
+    const int n = 2 * nKa;
+    const long long total = (long long)n * n * n * n;
+    const int nP = nKa * (nKa + 1) / 2;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+         id += (long long)gridDim.x * blockDim.x) {
+        int s = (int)(id % n), r = (int)((id / n) % n), q = (int)((id / n / n) % n), p = (int)(id / n / n / n);
+        DMap m1 = dmap(p, q, alpha != 0), m2 = dmap(r, s, alpha != 0);
+        int i1 = m1.X * nKa - m1.X * (m1.X - 1) / 2 + (m1.Y - m1.X);
+        int i2 = m2.X * nKa - m2.X * (m2.X - 1) / 2 + (m2.Y - m2.X);
+        int re1 = 2 * m1.which, im1 = re1 + 1, re2 = 2 * m2.which, im2 = re2 + 1;
+        const double *blk;
+        bool tr = i1 > i2;
+        if (!tr) blk = packed + ((long long)i1 * nP - (long long)i1 * (i1 - 1) / 2 + (i2 - i1)) * 16;
+        else blk = packed + ((long long)i2 * nP - (long long)i2 * (i2 - 1) / 2 + (i1 - i2)) * 16;
+        auto O = [&](int a, int b) { return tr ? blk[4 * b + a] : blk[4 * a + b]; };
+        double t1 = m1.cj ? -1.0 : 1.0, t2 = m2.cj ? -1.0 : 1.0;
+        double vr = O(re1, re2) - t1 * t2 * O(im1, im2);
+        double vi = t2 * O(re1, im2) + t1 * O(im1, re2);
+        double sg = m1.sign * m2.sign;
+        full[2 * id] = sg * vr;
+        full[2 * id + 1] = sg * vi;
+    }
+}
+
+void launch_unpack(const double *packed, int nKa, int gaunt_like, double *full, cudaStream_t s) {
+    long long n = 2LL * nKa, total = n * n * n * n;
+    if (total <= 0) return;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    unpack_kernel<<<(unsigned)blocks, 256, 0, s>>>(packed, nKa, gaunt_like, full);
+    QDT_CHECK_LAUNCH();
+}
+
+}  // namespace qdt

@@ -1,0 +1,156 @@
+// qdt_internal.cuh -- internal types and helpers of libqdt (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/qdt.h"
+
+namespace qdt {
+
+// ------------------------------------------------------------------ limits
+constexpr int kMaxLShell = QDT_MAX_L;              // large-component shell order
+constexpr int kMaxLFunc = kMaxLShell + 1;          // derivative functions reach l+1
+constexpr int kMaxLPair = 2 * kMaxLFunc;           // Hermite order of a pair
+constexpr int kMaxLTot = 2 * kMaxLPair + 2;        // + 2 for the gauge kernel
+constexpr int kBoysNMax = kMaxLTot + 1;            // orders needed
+constexpr int kBoysTaylor = 7;                     // Taylor terms of the table
+constexpr double kBoysDelta = 0.05;                // table spacing in T
+constexpr double kBoysTMax = 36.0;                 // table range; asymptotic beyond
+constexpr int kBoysGrid = 721;                     // 36 / 0.05 + 1
+constexpr int kBoysCols = kBoysNMax + kBoysTaylor + 1;
+
+__host__ __device__ constexpr int nherm(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+__host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+// Hermite / Cartesian triple index: all triples of order <= L, ordered by
+// order, then x-major inside one order.
+__host__ __device__ inline int hidx(int t, int u, int v) {
+    int s = t + u + v, uv = u + v;
+    return s * (s + 1) * (s + 2) / 6 + uv * (uv + 1) / 2 + v;
+}
+
+// ------------------------------------------------------------------ errors
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define QDT_CUDA_TRY(expr)                                                             \
+    do {                                                                               \
+        cudaError_t _e = (expr);                                                       \
+        if (_e != cudaSuccess)                                                         \
+            throw ::qdt::Error{QDT_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)}; \
+    } while (0)
+
+#define QDT_CHECK_LAUNCH() QDT_CUDA_TRY(cudaGetLastError())
+
+inline void arg_check(bool ok, const std::string &m) {
+    if (!ok) throw Error{QDT_ERR_ARG, m};
+}
+
+// ------------------------------------------------------------- device data
+// One shell of the combined list: L shells 0..n-1, derivative (S) shells n..2n-1.
+struct ShellDev {
+    double A[3];
+    int l;          // order of the parent large-component shell
+    int isS;        // 1 for a derivative shell
+    int nfunc;      // ncart(l) or 3 ncart(l)
+    int foff;       // first function in the combined list F = L (0..nL-1), S (nL..)
+    int nprim;
+    int poff;       // first primitive in the exponent/coefficient arrays
+    int noff;       // first normalisation constant (per Cartesian component)
+};
+
+// Shell pair of a class.  Class 0 (Coulomb): LL pairs A<=B then SS pairs A<=B;
+// class 1 (Gaunt and gauge): L x S pairs.
+struct PairDev {
+    int sa, sb;     // combined shell indices
+    int nfp;        // function pairs stored (upper triangle if sa == sb)
+    int Lab;        // Hermite order of the pair
+    int npp;        // primitive pairs
+    int ppoff;      // first primitive pair
+    long long rowoff;   // first row in the bra (Q-sorted) order
+};
+
+struct PrimPairDev {
+    double p;
+    double P[3];
+    long long eoff; // offset of this primitive pair's E matrix [nfp][nherm(Lab)]
+};
+
+// Host + device tables of one pair class.
+struct PairClass {
+    int nsp = 0;
+    long long M = 0;            // function pairs (rows)
+    std::vector<PairDev> h_pairs;
+    std::vector<int> bra_order; // shell pair ids, Q descending
+    std::vector<double> h_Q;
+    PairDev *d_pairs = nullptr;
+    PrimPairDev *d_pp = nullptr;
+    double *d_E = nullptr;
+    double *d_Q = nullptr;
+    int *d_bra_order = nullptr;
+    long long npp_total = 0, e_total = 0;
+    int maxnfp = 0, maxLab = 0;
+};
+
+// ------------------------------------------------------------------ kernels
+struct EriParams {
+    const ShellDev *shells;
+    const PairDev *pairs;
+    const PrimPairDev *pp;
+    const double *E;
+    const double *boys;         // [kBoysGrid][kBoysCols]
+    const int *ket_sp;          // shell pair id at each sorted ket position
+    const long long *ket_col;   // first column of each sorted ket position
+    double *W;                  // output rows
+    long long ldw;
+    long long row0;             // bra-order row of W's first row
+    int gauge;                  // 0: Coulomb kernel; 1: gauge kernel (9 components)
+    int with_coulomb;           // gauge mode: also write the plain Coulomb block
+    double *Wc;                 // gauge mode: Coulomb block output (may be null)
+    long long ldwc;
+};
+
+struct EriTask {                // one CTA: bra shell pair x range of ket positions
+    int bra_sp;
+    int k0, k1;
+};
+
+void launch_boys_table(double *d_tab, cudaStream_t s);
+void launch_shell_norms(const ShellDev *shells, int nL_shells, const double *exps,
+                        const double *coefs, double *norms, cudaStream_t s);
+void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxnfp, int maxLab,
+                cudaStream_t s);
+void launch_schwarz(const ShellDev *shells, const PairDev *pairs, const PrimPairDev *pp,
+                    const double *E, const double *boys, int npairs, int maxnfp, int maxLab,
+                    double *Q, double *scratch, cudaStream_t s);
+
+void launch_ket_order(const double *Q, const double *Dmax, int nsp, double *w, int *ket_sp,
+                      cudaStream_t s);
+void launch_ket_columns(const PairDev *pairs, const int *ket_sp, int nsp, long long *ket_col,
+                        cudaStream_t s);
+void launch_prefix_lengths(const double *Q, const double *w_sorted, int nsp, double tau,
+                           int *prefix, cudaStream_t s);
+void launch_gather_rows(const double *src, const PairDev *pairs, const int *ket_sp,
+                        const long long *ket_col, int nsp, long long rowlen, double *dst,
+                        cudaStream_t s);
+
+// GEMMs
+void gemm_fp64_nn_ragged(const double *A, long long lda, const double *B, long long ldb,
+                         double *C, long long ldc, long long M, long long N,
+                         const long long *ktile, int tileM, cudaStream_t s);
+void gemm_fp64_tn_sym(const double *A, long long lda, const double *B, long long ldb, double *C,
+                      long long N, long long K, double *partial, size_t partial_elems,
+                      cudaStream_t s);
+int gemm_fp64_tile_m();
+
+// packing
+void launch_pack(const double *O, long long ldo, int nKa, double *out, cudaStream_t s);
+void launch_unpack(const double *packed, int nKa, int gaunt_like, double *full, cudaStream_t s);
+void launch_zero(double *p, long long n, cudaStream_t s);
+
+}  // namespace qdt

@@ -1,0 +1,170 @@
+"""Thin Python binding of libqdt (include/qdt.h): argument marshalling only.
+
+Every step of a transformation runs in the library's CUDA kernels; PyTorch is
+used for device memory and streams.  There is no CPU fallback: if the
+extension is missing the import of the library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+COULOMB, GAUNT, GAUGE = 1, 2, 4
+FP64, SPLIT = 0, 1
+BLOCK_BITS = {"coulomb": COULOMB, "gaunt": GAUNT, "gauge": GAUGE}
+ERRORS = {-1: "QDT_ERR_ARG", -2: "QDT_ERR_OOM", -3: "QDT_ERR_CUDA", -4: "QDT_ERR_STATE",
+          -5: "QDT_ERR_UNIMPLEMENTED", -6: "QDT_ERR_TIMEOUT", -7: "QDT_ERR_ADMISSION"}
+
+EXPORTS = ["qdt_create", "qdt_destroy", "qdt_set_basis", "qdt_num_functions", "qdt_set_coefficients",
+           "qdt_packed_size", "qdt_transform", "qdt_unpack", "qdt_last_error", "qdt_version"]
+
+
+class QdtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "QDT_ERR"), code, msg))
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double), ("ms_density", ctypes.c_double),
+                ("ms_screen", ctypes.c_double), ("ms_eri", ctypes.c_double),
+                ("ms_half1", ctypes.c_double), ("ms_half2", ctypes.c_double),
+                ("ms_pack", ctypes.c_double), ("flops_half1", ctypes.c_double),
+                ("flops_half2", ctypes.c_double), ("quartets_total", ctypes.c_longlong * 3),
+                ("quartets_kept", ctypes.c_longlong * 3), ("eri_values", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_int), ("precision", ctypes.c_int),
+                ("slices", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+_LIB = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libqdt.so (building it in-tree with nvcc if absent)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError("libqdt.so is not built: run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    L.qdt_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp]
+    L.qdt_destroy.argtypes = [vp]
+    L.qdt_destroy.restype = None
+    L.qdt_set_basis.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, vp]
+    L.qdt_num_functions.argtypes = [vp]
+    L.qdt_set_coefficients.argtypes = [vp, ctypes.c_int, vp, vp]
+    L.qdt_packed_size.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int]
+    L.qdt_packed_size.restype = ctypes.c_size_t
+    L.qdt_transform.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_int, vp, ctypes.c_size_t, ctypes.POINTER(Stats)]
+    L.qdt_unpack.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint, vp]
+    L.qdt_last_error.argtypes = [vp]
+    L.qdt_last_error.restype = ctypes.c_char_p
+    L.qdt_version.restype = ctypes.c_char_p
+    _LIB = L
+    return L
+
+
+def _ptr(x):
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def blocks_mask(blocks):
+    if isinstance(blocks, int):
+        return blocks
+    m = 0
+    for b in blocks:
+        m |= BLOCK_BITS[b]
+    return m
+
+
+class Context:
+    """One qdt context on one CUDA device (and one stream)."""
+
+    def __init__(self, device=0, stream=None):
+        self.L = load()
+        h = ctypes.c_void_p()
+        sp = None
+        if stream is not None:
+            sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        rc = self.L.qdt_create(ctypes.byref(h), int(device), sp)
+        if rc != 0:
+            raise QdtError(rc, "qdt_create failed")
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.qdt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise QdtError(rc, self.L.qdt_last_error(self.h).decode())
+
+    def set_basis(self, basis):
+        arrs = [np.ascontiguousarray(basis.xyz, np.float64), np.ascontiguousarray(basis.shell_center, np.int32),
+                np.ascontiguousarray(basis.shell_l, np.int32), np.ascontiguousarray(basis.shell_nprim, np.int32),
+                np.ascontiguousarray(basis.exps, np.float64), np.ascontiguousarray(basis.coefs, np.float64)]
+        self._check(self.L.qdt_set_basis(self.h, int(arrs[0].shape[0]), _ptr(arrs[0]), int(arrs[1].shape[0]),
+                                         _ptr(arrs[1]), _ptr(arrs[2]), _ptr(arrs[3]), _ptr(arrs[4]),
+                                         _ptr(arrs[5])))
+
+    def num_functions(self):
+        return self.L.qdt_num_functions(self.h)
+
+    def set_coefficients(self, CL, CS):
+        """CL [nL, nK, 4], CS [3 nL, nK, 4] float64, numpy (host) or torch (host or cuda)."""
+        if isinstance(CL, np.ndarray):
+            CL = np.ascontiguousarray(CL, np.float64)
+            CS = np.ascontiguousarray(CS, np.float64)
+        nK = int(CL.shape[1])
+        self._check(self.L.qdt_set_coefficients(self.h, nK, _ptr(CL), _ptr(CS)))
+
+    def packed_size(self, blocks, k_begin, k_end):
+        return int(self.L.qdt_packed_size(self.h, blocks_mask(blocks), int(k_begin), int(k_end)))
+
+    def transform(self, blocks, k_begin, k_end, tau, precision, out):
+        """Packed (pq|rs) into `out` (numpy or torch float64, host or device);
+        returns the call's statistics as a dict."""
+        st = Stats()
+        nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+        self._check(self.L.qdt_transform(self.h, blocks_mask(blocks), int(k_begin), int(k_end), float(tau),
+                                         int(precision), _ptr(out), nbytes, ctypes.byref(st)))
+        return st.as_dict()
+
+    def unpack(self, packed, n_kramers, block, full):
+        """packed/full: torch cuda float64 tensors; full holds (2n)^4 complex values."""
+        self._check(self.L.qdt_unpack(self.h, _ptr(packed), int(n_kramers), blocks_mask([block]), _ptr(full)))
+
+
+def version():
+    return load().qdt_version().decode()
