@@ -1,0 +1,302 @@
+"""Benchmark of the quaternion Dirac-Coulomb(-Breit) AO->MO transformation.
+
+One step = one qdt_transform() over the whole hot path (density, screening,
+AO integral tiles, first and second half-transforms, packing) of the
+workload, with the basis and coefficients already resident on the GPU.
+
+Default workload: the 40-centre s+p chain (nL = 160, nS = 480, 40 Kramers
+pairs, Schwarz threshold 1e-12, seeded synthetic inputs standing in for the
+paper's Hg/Pu chains).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload chain40-sp] [--blocks coulomb[,gaunt,gauge]]
+                  [--precision split|fp64]
+Multi-GPU (torchrun): every rank transforms its own copy of the workload
+(independent problems, weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_04316_gb300 import synth  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+NOMINAL = {"bf16": 2250.0, "fp64": 1.25}     # dense TF/s, for dtype ratios
+
+
+def workload(name):
+    if name == "chain40-sp":
+        return synth.medium_dc()
+    if name == "tiny-6s":
+        return synth.tiny_dc()
+    if name == "cluster64-sp":
+        return synth.dcb_cluster()
+    if name.startswith("chain"):
+        n = int(name[5:].split("-")[0])
+        return synth.medium_dc(n_centers=n, nK=n)
+    raise SystemExit("unknown workload " + name)
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def mo_integrals(nK, nblocks):
+    return float((2 * nK) ** 4) * nblocks
+
+
+def run_reference(args, problem, blocks, rank):
+    """CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    if rank != 0:
+        return
+    res = cpu_oracle_rate(problem, blocks, budget_s=args.ref_budget)
+    line = {"metric": METRIC, "value": res["value"], "unit": "MO-integrals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": config_dict(args, problem, blocks),
+            "cpu_baseline": {"value": res["value"], "unit": "MO-integrals/s", "cores": res["cores"],
+                             "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": res["value"], "unit": "MO-integrals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_oracle_rate(problem, blocks, budget_s=20.0):
+    """Time the oracle on a reduced chain of the same recipe, grown until one
+    full transformation takes about budget_s / 2 seconds."""
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count()
+    n, last = 2, None
+    while True:
+        p = synth.chain_problem(n, n, seed=synth.SEED_BASE + 1, shells=(0, 1), nprim=3,
+                                blocks=blocks, tau=problem.tau, name="sample")
+        t0 = time.perf_counter()
+        tr = O.Transform(p)
+        for b in blocks:
+            tr.packed(b)
+        dt = time.perf_counter() - t0
+        last = (n, dt)
+        if dt > budget_s / 2 or n >= 12:
+            break
+        n += 2
+    n, dt = last
+    rate = mo_integrals(n, len(blocks)) / dt
+    return {"value": rate, "ms": dt * 1e3, "cores": cores,
+            "sample": "oracle, full transform of a %d-centre s+p chain (same recipe, nK=%d, blocks=%s) "
+                      "on %d host threads; %.1f s" % (n, n, "+".join(blocks), cores, dt)}
+
+
+METRIC = "DCB AO->MO transform MO-integrals/s (split vs FP64 @1e-10 Eh)"
+
+
+def config_dict(args, problem, blocks):
+    return {"workload": args.workload, "nL": problem.basis.nL, "nS": problem.basis.nS,
+            "n_kramers": problem.nK, "blocks": "+".join(blocks), "schwarz_tau": problem.tau,
+            "precision": args.precision, "l2": "inputs larger than L2 (densities, integral rows)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chain40-sp")
+    ap.add_argument("--blocks", default="coulomb")
+    ap.add_argument("--precision", default="fp64", choices=["split", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--stats", action="store_true", help="print per-phase statistics to stderr")
+    args = ap.parse_args()
+    blocks = args.blocks.split(",")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    problem = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, problem, blocks, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2606_04316_gb300 import qdt
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    ctx = qdt.Context(local, stream=stream)
+    ctx.set_basis(problem.basis)
+    CLd = torch.from_numpy(problem.CL).cuda()
+    CSd = torch.from_numpy(problem.CS).cuda()
+    ctx.set_coefficients(CLd, CSd)
+    nK = problem.nK
+    prec = qdt.SPLIT if args.precision == "split" else qdt.FP64
+    nout = ctx.packed_size(blocks, 0, nK) // 8
+    out = torch.zeros(nout, dtype=torch.float64, device="cuda")
+    tau = problem.tau
+
+    def step():
+        return ctx.transform(blocks, 0, nK, tau, prec, out)
+
+    for _ in range(args.warmup):
+        st = step()
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    phase = {k: 0.0 for k in ("ms_eri", "ms_half1", "ms_half2", "ms_density", "ms_screen", "ms_pack")}
+    launches = 0
+    for _ in range(args.steps):
+        st = step()
+        for k in phase:
+            phase[k] += st[k]
+        launches += st["kernel_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    n_mo = mo_integrals(nK, len(blocks))
+    value = n_mo * world / (ms / 1e3)
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        CLh = torch.from_numpy(problem.CL).pin_memory()
+        CSh = torch.from_numpy(problem.CS).pin_memory()
+        outh = torch.zeros(nout, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        ne = 1
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            ctx.set_coefficients(CLh, CSh)
+            ctx.transform(blocks, 0, nK, tau, prec, outh)
+        dt = (time.perf_counter() - t0) / ne
+        e2e = {"value": n_mo * world / dt, "unit": "MO-integrals/s",
+               "h2d_bytes_per_step": int(CLh.numel() * 8 + CSh.numel() * 8),
+               "d2h_bytes_per_step": int(outh.numel() * 8)}
+
+    pk, src = peaks()
+    avg = {k: v / args.steps for k, v in phase.items()}
+    dom = max(("ms_eri", "ms_half1", "ms_half2"), key=lambda k: avg[k])
+    fp64_peak = pk["bf16_tflops_sustained"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+    if dom == "ms_eri":
+        achieved = st["flops_eri"] / (avg[dom] / 1e3) / 1e12
+        roof = {"kernel": "eri_rows_kernel", "bound": "alu", "achieved": achieved,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": None,
+                "peak_note": "FP64 pipe: %s bf16 sustained x 1.25/2250 nominal ratio (%s)" % (src, src)}
+    else:
+        fl = st["flops_half1"] if dom == "ms_half1" else st["flops_half2"]
+        achieved = fl / (avg[dom] / 1e3) / 1e12
+        if prec == qdt.FP64:
+            peak, note = fp64_peak, "FP64: %s bf16 sustained x 1.25/2250 nominal ratio" % src
+        else:
+            peak, note = pk["bf16_tflops_sustained"], "%s bf16 sustained" % src
+        roof = {"kernel": "half1" if dom == "ms_half1" else "half2", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_note": note}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        try:
+            r = cpu_oracle_rate(problem, blocks)
+            cpu = {"value": r["value"], "unit": "MO-integrals/s", "cores": r["cores"], "kind": "oracle",
+                   "sample": r["sample"]}
+        except Exception as ex:  # keep the bench line even if the oracle fails
+            cpu = {"value": None, "unit": "MO-integrals/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": "failed: %s" % ex}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MO-integrals/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == qdt.FP64 else "bf16-slices/f64",
+                "data": "synthetic", "config": config_dict(args, problem, blocks), "clocks": clocks,
+                "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+                "phases_ms": avg, "quartets_kept": st["quartets_kept"], "quartets_total": st["quartets_total"]}
+        print(json.dumps(line), flush=True)
+        if args.stats:
+            print(json.dumps(st), file=sys.stderr)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -102,6 +102,7 @@ typedef struct {
     int kernel_launches;        /* library kernels launched by the call               */
     int precision;              /* QDT_FP64 or QDT_SPLIT                              */
     int slices;                 /* BF16 slices per operand in the split form          */
+    double flops_eri;           /* FP64 flops of the integral contractions (E R E)    */
 } qdt_stats;
 
 /*

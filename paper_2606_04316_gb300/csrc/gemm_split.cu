@@ -1,7 +1,61 @@
-// gemm_split.cu -- dispatch of the half-transform contractions.
+// gemm_split.cu -- the half-transform contractions (paper Eqs. firsthalf and
+// secondhalf) in two forms:
+//
+//  QDT_FP64:  plain FP64 GEMMs (gemm_fp64.cu).
+//  QDT_SPLIT: Ozaki-style split precision on the 5th-generation tensor cores.
+//    Every FP64 operand row (A) or column (B) gets a power-of-two scale 2^e
+//    with 2^e > max |x|; x = sign * 2^e * sum_{i=1..6} d_i 2^{-7 i} with 7-bit
+//    digits d_i (exact in BF16).  C = 2^{e_r + f_c} sum_{i+j<=7} 2^{-7(i+j)}
+//    sum_k a_i b_j.  Digit products are integers < 2^14; over a K chunk of 256
+//    the sums of diagonals i+j = 2, 3, 4 (at most 3 pairs) stay below 2^24 and
+//    are exact in the FP32 TMEM accumulators; after each chunk they are
+//    converted to integers and folded into a 64-bit integer accumulator.  The
+//    lighter diagonals 5, 6, 7 (weights <= 2^{-35}) accumulate in FP32 over the
+//    whole K.  The result is recombined in FP64.
+//
+//  Tensor-core kernel: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), M = 128,
+//  N = 64, operands K-major in shared memory with the 128-byte swizzle, staged
+//  by TMA (cp.async.bulk.tensor) through a 3-deep mbarrier pipeline; six FP32
+//  accumulators (384 TMEM columns) per CTA; every wait is bounded and reports
+//  a timeout through a device status word instead of hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "split.cuh"
 
 namespace qdt {
+
+constexpr int kSlices = 6;
+constexpr int kBits = 7;
+constexpr int kFrac = kSlices * kBits;       // 42 fractional bits
+constexpr int SBM = 128, SBN = 64, SBK = 64;
+constexpr int kChunkSub = 4;                  // 4 x 64 = 256 K per exact chunk
+constexpr int kStages = 3;
+constexpr int kATile = SBM * SBK * 2;         // 16 KB
+constexpr int kBTile = SBN * SBK * 2;         // 8 KB
+constexpr int kStageBytes = kATile + kSlices * kBTile;   // 64 KB
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr long long kWaitNs = 2000000000LL;   // 2 s bound on every wait
+
+// ------------------------------------------------------------ workspace
+enum { WS_A = 0, WS_B0 = 1, WS_B1 = 2, WS_EXP = 3, WS_KT = 4, WS_ERR = 5, WS_A2 = 6, WS_B2 = 7 };
+
+static void *ws_get(SplitWorkspace &w, int slot, size_t bytes) {
+    if (w.bytes[slot] >= bytes && w.buf[slot]) return w.buf[slot];
+    if (w.buf[slot]) cudaFree(w.buf[slot]);
+    w.buf[slot] = nullptr;
+    w.bytes[slot] = 0;
+    if (cudaMalloc(&w.buf[slot], bytes) != cudaSuccess) {
+        cudaGetLastError();
+        w.buf[slot] = nullptr;
+        throw Error{QDT_ERR_OOM, "split workspace allocation failed"};
+    }
+    w.bytes[slot] = bytes;
+    return w.buf[slot];
+}
 
 void split_release(SplitWorkspace &w) {
     for (int i = 0; i < 8; ++i) {
@@ -9,24 +63,473 @@ void split_release(SplitWorkspace &w) {
         w.buf[i] = nullptr;
         w.bytes[i] = 0;
     }
+    w.bkey[0] = w.bkey[1] = SplitKey();
+    w.bnext = 0;
 }
 
 int split_slices(const SplitWorkspace &w) { return w.slices; }
 
-void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B,
-                long long ldb, double *C, long long ldc, long long M, long long N,
-                const long long *d_ktile, const std::vector<long long> &h_ktile, cudaStream_t s) {
-    (void)w; (void)h_ktile;
-    if (precision == QDT_SPLIT) throw Error{QDT_ERR_UNIMPLEMENTED, "split form not built yet"};
-    gemm_fp64_nn_ragged(A, lda, B, ldb, C, ldc, M, N, d_ktile, gemm_fp64_tile_m(), s);
+void split_invalidate(SplitWorkspace &w) { w.bkey[0] = w.bkey[1] = SplitKey(); }
+
+static inline long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// ------------------------------------------------------------ digits
+__device__ inline int exp_of_max(double m) {
+    // smallest e with 2^e > m (m >= 0); 0 for m == 0
+    if (!(m > 0.0)) return 0;
+    long long bits = __double_as_longlong(m);
+    int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex == 0) return -1022;
+    return ex - 1023 + 1;
 }
 
-void gemm_half2(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B,
-                long long ldb, double *C, long long N, long long K, double *partial,
-                size_t partial_elems, cudaStream_t s) {
-    (void)w;
-    if (precision == QDT_SPLIT) throw Error{QDT_ERR_UNIMPLEMENTED, "split form not built yet"};
-    gemm_fp64_tn_sym(A, lda, B, ldb, C, N, K, partial, partial_elems, s);
+__device__ inline void digits7(double x, int e, __nv_bfloat16 *d, size_t plane) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    int ex = (int)((bits >> 52) & 0x7FF);
+    unsigned long long X = 0;
+    if (ex != 0) {
+        unsigned long long mant = (bits & ((1ULL << 52) - 1)) | (1ULL << 52);
+        int sh = ex - 1075 + kFrac - e;          // |x| 2^{42-e} = mant 2^sh
+        if (sh >= 0) X = (1ULL << kFrac) - 1;    // cannot happen when 2^e > |x|
+        else if (sh > -64) X = mant >> (-sh);
+        if (X >= (1ULL << kFrac)) X = (1ULL << kFrac) - 1;
+    }
+    bool neg = (bits >> 63) != 0;
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i) {
+        int v = (int)((X >> (kBits * (kSlices - 1 - i))) & 127);
+        d[i * plane] = __float2bfloat16_rn((float)(neg ? -v : v));
+    }
+}
+
+// A operand: rows of X (row-major, ld) scaled per row; out[i][r][k] for
+// r < Mpad, k < Kpad (zeros outside the matrix).  One CTA per row.
+__global__ void slice_rows_kernel(const double *X, long long ld, long long M, long long K,
+                                  long long Mpad, long long Kpad, __nv_bfloat16 *out, int *rowexp) {
+    long long r = blockIdx.x;
+    __shared__ double red[256];
+    double m = 0.0;
+    if (r < M)
+        for (long long k = threadIdx.x; k < K; k += blockDim.x) m = fmax(m, fabs(X[r * ld + k]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    int e = exp_of_max(red[0]);
+    if (threadIdx.x == 0) rowexp[r] = e;
+    size_t plane = (size_t)Mpad * Kpad;
+    for (long long k = threadIdx.x; k < Kpad; k += blockDim.x) {
+        double x = (r < M && k < K) ? X[r * ld + k] : 0.0;
+        digits7(x, e, out + (size_t)r * Kpad + k, plane);
+    }
+}
+
+// column maxima (as exponents) of X[rows][cols]
+__global__ void col_max_kernel(const double *X, long long ld, long long rows, long long cols,
+                               long long rows_per_block, unsigned long long *cmax) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    long long r0 = blockIdx.y * rows_per_block, r1 = min(rows, r0 + rows_per_block);
+    double m = 0.0;
+    for (long long r = r0; r < r1; ++r) m = fmax(m, fabs(X[r * ld + c]));
+    atomicMax(cmax + c, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void col_exp_kernel(const unsigned long long *cmax, long long cols, long long cols_pad, int *colexp) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= cols_pad) return;
+    colexp[c] = (c < cols) ? exp_of_max(__longlong_as_double((long long)cmax[c])) : 0;
+}
+
+// B operand (or a transposed A): columns of X scaled per column, written
+// transposed: out[i][c][r] for c < Cpad, r < Rpad.  Tile 64 rows x 32 cols.
+__global__ void slice_cols_t_kernel(const double *X, long long ld, long long rows, long long cols,
+                                    long long Rpad, long long Cpad, const int *colexp,
+                                    __nv_bfloat16 *out) {
+    __shared__ double t[64][33];
+    long long r0 = blockIdx.x * 64LL, c0 = blockIdx.y * 32LL;
+    for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
+        int rr = i / 32, cc = i % 32;
+        long long r = r0 + rr, c = c0 + cc;
+        t[rr][cc] = (r < rows && c < cols) ? X[r * ld + c] : 0.0;
+    }
+    __syncthreads();
+    size_t plane = (size_t)Cpad * Rpad;
+    for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
+        int cc = i / 64, rr = i % 64;
+        long long r = r0 + rr, c = c0 + cc;
+        if (r < Rpad && c < Cpad) digits7(t[rr][cc], colexp[c], out + (size_t)c * Rpad + r, plane);
+    }
+}
+
+// ------------------------------------------------------------ PTX helpers
+__device__ inline uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ inline void mbar_init(uint64_t *b, int cnt) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(cnt) : "memory");
+}
+
+__device__ inline void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+
+// bounded wait for phase `parity` of an mbarrier; false on timeout
+__device__ inline bool mbar_wait(uint64_t *b, uint32_t parity) {
+    uint32_t a = su32(b);
+    unsigned long long t0 = gtimer();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((long long)(gtimer() - t0) > kWaitNs) return false;
+    }
+}
+
+__device__ inline void tma_load(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            su32(dst)),
+        "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+__device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ inline uint64_t sdesc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor: D = F32, A = B = BF16, both K-major, N = 64, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SBN >> 3) << 17) |
+                            ((uint32_t)(SBM >> 4) << 24);
+
+__device__ inline void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ inline void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ inline void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------ GEMM kernel
+// C[M x N] (FP64, ld ldc) = sum of digit products of A slices (tmA rows
+// i*Mpad + m) and B slices (tmB rows j*Npad + n), K extent per 128-row tile.
+__global__ void __launch_bounds__(128, 1)
+    ozaki_umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      long long Mpad, long long Npad, const long long *__restrict__ ktile,
+                      const int *__restrict__ rowexp, const int *__restrict__ colexp, double *C, long long ldc,
+                      long long Mvalid, long long Nvalid, int upper_only, int *status) {
+    extern __shared__ uint8_t smem_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long m0 = (long long)blockIdx.y * SBM, n0 = (long long)blockIdx.x * SBN;
+    if (upper_only && (m0 / 4) > (n0 + SBN - 1) / 4) return;   // below the block diagonal: unused
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(base + kStages * kStageBytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *chunk_bar = empty + kStages;
+    uint32_t *tslot = (uint32_t *)(chunk_bar + 1);
+    __shared__ int abort_flag;
+
+    const long long K = ktile[blockIdx.y];
+    const int nk = (int)((K + SBK - 1) / SBK);
+    long long acc[SBN];
+#pragma unroll
+    for (int j = 0; j < SBN; ++j) acc[j] = 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+        mbar_init(chunk_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int total = nk * kSlices;                    // pipeline steps: (k subtile, A slice)
+    const int nchunks = (nk + kChunkSub - 1) / kChunkSub;
+
+    auto load_step = [&](int s) {
+        int st = s % kStages, kt = s / kSlices, i = s % kSlices;
+        uint8_t *sa = base + st * kStageBytes, *sb = sa + kATile;
+        int nb = kSlices - i;                          // B slices j with i + j <= 5 (0-based)
+        mbar_expect_tx(full + st, kATile + nb * kBTile);
+        tma_load(sa, &tmA, kt * SBK, (int)(i * Mpad + m0), full + st);
+        for (int j = 0; j < nb; ++j)
+            tma_load(sb + j * kBTile, &tmB, kt * SBK, (int)(j * Npad + n0), full + st);
+    };
+
+    bool ok = true;
+    if (tid == 0)
+        for (int s = 0; s < min(kStages, total); ++s) load_step(s);
+    for (int c = 0; c < nchunks; ++c) {
+        if (tid == 0 && ok) {
+            bool fresh[kSlices];
+            for (int a = 0; a < kSlices; ++a) fresh[a] = (a < 3) || (c == 0);
+            int s_begin = c * kChunkSub * kSlices, s_end = min(total, (c + 1) * kChunkSub * kSlices);
+            for (int s = s_begin; s < s_end && ok; ++s) {
+                int st = s % kStages;
+                if (!mbar_wait(full + st, (uint32_t)((s / kStages) & 1))) { ok = false; break; }
+                tc_fence_after();
+                int i = s % kSlices;
+                uint32_t sa = su32(base + st * kStageBytes), sb = sa + kATile;
+                for (int j = 0; j < kSlices - i; ++j) {
+                    int a = i + j;
+                    for (int k16 = 0; k16 < SBK / 16; ++k16) {
+                        umma(tmem + (uint32_t)(a * SBN), sdesc(sa + k16 * 32), sdesc(sb + j * kBTile + k16 * 32),
+                             fresh[a] ? 0u : 1u);
+                        fresh[a] = false;
+                    }
+                }
+                umma_commit(empty + st);
+                if (s >= 1) {
+                    int prev = s - 1;
+                    if (prev + kStages < total) {
+                        if (!mbar_wait(empty + prev % kStages, (uint32_t)((prev / kStages) & 1))) { ok = false; break; }
+                        load_step(prev + kStages);
+                    }
+                }
+            }
+            if (ok) umma_commit(chunk_bar);
+            if (!ok) abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        bool mine = mbar_wait(chunk_bar, (uint32_t)(c & 1));
+        if (__syncthreads_or(!mine)) { if (tid == 0) abort_flag = 1; break; }
+        tc_fence_after();
+        // fold the exact diagonals (accumulators 0, 1, 2) into the integer accumulator
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int q = 0; q < SBN / 16; ++q) {
+            float v0[16], v1[16], v2[16];
+            tmem_ld16(trow + 0 * SBN + q * 16, v0);
+            tmem_ld16(trow + 1 * SBN + q * 16, v1);
+            tmem_ld16(trow + 2 * SBN + q * 16, v2);
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                acc[q * 16 + t] += ((long long)__float2ll_rn(v0[t]) << 14) + ((long long)__float2ll_rn(v1[t]) << 7) +
+                                   (long long)__float2ll_rn(v2[t]);
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!abort_flag && nk > 0) {
+        tc_fence_after();
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        const long long m = m0 + warp * 32 + lane;
+        const int er = (m < Mpad) ? rowexp[m] : 0;
+#pragma unroll
+        for (int q = 0; q < SBN / 16; ++q) {
+            float v3[16], v4[16], v5[16];
+            tmem_ld16(trow + 3 * SBN + q * 16, v3);
+            tmem_ld16(trow + 4 * SBN + q * 16, v4);
+            tmem_ld16(trow + 5 * SBN + q * 16, v5);
+            if (m < Mvalid) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    long long n = n0 + q * 16 + t;
+                    if (n < Nvalid) {
+                        double v = ldexp((double)acc[q * 16 + t], -28) + ldexp((double)v3[t], -35) +
+                                   ldexp((double)v4[t], -42) + ldexp((double)v5[t], -49);
+                        C[m * ldc + n] = ldexp(v, er + colexp[n]);
+                    }
+                }
+            }
+        }
+    } else if (!abort_flag && nk == 0) {
+        const long long m = m0 + warp * 32 + lane;
+        if (m < Mvalid)
+            for (int t = 0; t < SBN; ++t)
+                if (n0 + t < Nvalid) C[m * ldc + n0 + t] = 0.0;
+    }
+    if (abort_flag && tid == 0) {
+        atomicExch(status, 1);
+        // let copies and MMAs in flight land before the CTA exits (bounded)
+        for (int s = 0; s < kStages; ++s) { mbar_wait(full + s, 0); mbar_wait(full + s, 1); }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    }
+}
+
+// ------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        QDT_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p) throw Error{QDT_ERR_CUDA, "cuTensorMapEncodeTiled unavailable"};
+        fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 2D BF16 map over [rows][cols] (row pitch cols*2 bytes), box {64, box_rows}, 128B swizzle
+static CUtensorMap make_map(void *ptr, long long rows, long long cols, int box_rows) {
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)SBK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error{QDT_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+    return m;
+}
+
+// Column-scaled, transposed slices of X[rows][cols] into slot; returns (Cpad, Rpad).
+static void slice_cols(SplitWorkspace &w, int slot, const double *X, long long ld, long long rows, long long cols,
+                       long long Rpad, long long Cpad, int *colexp, cudaStream_t s) {
+    unsigned long long *cmax = (unsigned long long *)ws_get(w, WS_ERR, std::max<size_t>(4096, (size_t)Cpad * 8 + 64));
+    QDT_CUDA_TRY(cudaMemsetAsync(cmax, 0, (size_t)Cpad * 8, s));
+    long long rpb = std::max<long long>(64, (rows + 1023) / 1024);
+    dim3 g1((unsigned)((cols + 255) / 256), (unsigned)((rows + rpb - 1) / rpb));
+    if (rows > 0 && cols > 0) col_max_kernel<<<g1, 256, 0, s>>>(X, ld, rows, cols, rpb, cmax);
+    col_exp_kernel<<<(unsigned)((Cpad + 255) / 256), 256, 0, s>>>(cmax, cols, Cpad, colexp);
+    __nv_bfloat16 *out = (__nv_bfloat16 *)ws_get(w, slot, (size_t)kSlices * Cpad * Rpad * 2 + (size_t)Cpad * sizeof(int));
+    dim3 g2((unsigned)(Rpad / 64), (unsigned)(Cpad / 32));
+    slice_cols_t_kernel<<<g2, 256, 0, s>>>(X, ld, rows, cols, Rpad, Cpad, colexp, out);
+    QDT_CHECK_LAUNCH();
+}
+
+static void run_umma(SplitWorkspace &w, void *Asl, long long Mpad, long long KpadA, void *Bsl, long long Npad,
+                     long long KpadB, const long long *d_kt128, const int *rowexp, const int *colexp, double *C,
+                     long long ldc, long long M, long long N, int upper, cudaStream_t s) {
+    CUtensorMap ta = make_map(Asl, kSlices * Mpad, KpadA, SBM);
+    CUtensorMap tb = make_map(Bsl, kSlices * Npad, KpadB, SBN);
+    int *status = (int *)((char *)ws_get(w, WS_KT, 0) + 0);  // status lives in front of the tile extents
+    QDT_CUDA_TRY(cudaFuncSetAttribute(ozaki_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    dim3 grid((unsigned)(Npad / SBN), (unsigned)(Mpad / SBM));
+    ozaki_umma_kernel<<<grid, 128, kSmemBytes, s>>>(ta, tb, Mpad, Npad, d_kt128, rowexp, colexp, C, ldc, M, N,
+                                                    upper, status);
+    QDT_CHECK_LAUNCH();
+    int h = 0;
+    QDT_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    QDT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) throw Error{QDT_ERR_TIMEOUT, "split contraction: a bounded tensor-core wait gave up"};
+}
+
+void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B, long long ldb,
+                double *C, long long ldc, long long M, long long N, const long long *d_ktile,
+                const std::vector<long long> &h_ktile, cudaStream_t s) {
+    if (precision != QDT_SPLIT) {
+        gemm_fp64_nn_ragged(A, lda, B, ldb, C, ldc, M, N, d_ktile, gemm_fp64_tile_m(), s);
+        return;
+    }
+    if (M <= 0 || N <= 0) return;
+    const int TMr = gemm_fp64_tile_m();
+    const long long Mpad = rup(M, SBM), Npad = rup(N, SBN);
+    std::vector<long long> kt((size_t)(Mpad / SBM), 0);
+    long long kmax = 0;
+    for (size_t t = 0; t < h_ktile.size(); ++t) {
+        long long r = (long long)t * TMr / SBM;
+        if (r < (long long)kt.size()) kt[r] = std::max(kt[r], h_ktile[t]);
+        kmax = std::max(kmax, h_ktile[t]);
+    }
+    const long long KpadA = std::max<long long>(SBK, rup(std::min(kmax, lda), SBK));
+    // tile extents + status word
+    char *ktb = (char *)ws_get(w, WS_KT, 256 + kt.size() * sizeof(long long));
+    QDT_CUDA_TRY(cudaMemsetAsync(ktb, 0, 256, s));
+    long long *d_kt = (long long *)(ktb + 256);
+    QDT_CUDA_TRY(cudaMemcpyAsync(d_kt, kt.data(), kt.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+    // A slices (row scaled)
+    int *rowexp = (int *)ws_get(w, WS_EXP, (size_t)(Mpad + Npad + 64) * sizeof(int) * 2);
+    __nv_bfloat16 *Asl = (__nv_bfloat16 *)ws_get(w, WS_A, (size_t)kSlices * Mpad * KpadA * 2);
+    slice_rows_kernel<<<(unsigned)Mpad, 256, 0, s>>>(A, lda, M, std::min(kmax, lda), Mpad, KpadA, Asl, rowexp);
+    QDT_CHECK_LAUNCH();
+    // B slices (column scaled, transposed), cached per (pointer, shape) until
+    // split_invalidate(): the densities are the same for every row batch.
+    const long long Krows = kmax;
+    long long KpadB = std::max<long long>(SBK, rup(Krows, SBK));
+    SplitKey key{B, ldb, N, KpadB};
+    int slot = -1;
+    for (int q = 0; q < 2; ++q)
+        if (w.bkey[q].ptr == B && w.bkey[q].ld == ldb && w.bkey[q].n == N && w.bkey[q].k >= KpadB) slot = q;
+    // the first (highest-Q) row batch has the longest ket prefix; later
+    // batches reuse its slices with the cached row pitch
+    if (slot >= 0) KpadB = w.bkey[slot].k;
+    const size_t bslice = (size_t)kSlices * Npad * KpadB * 2;
+    if (slot < 0) {
+        slot = w.bnext;
+        w.bnext ^= 1;
+        w.bkey[slot] = SplitKey();
+        char *bb = (char *)ws_get(w, WS_B0 + slot, bslice + (size_t)Npad * sizeof(int));
+        slice_cols(w, WS_B0 + slot, B, ldb, Krows, N, KpadB, Npad, (int *)(bb + bslice), s);
+        w.bkey[slot] = key;
+    }
+    char *bb = (char *)w.buf[WS_B0 + slot];
+    run_umma(w, Asl, Mpad, KpadA, bb, Npad, KpadB, d_kt, rowexp, (const int *)(bb + bslice), C, ldc, M, N, 0, s);
+}
+
+void gemm_half2(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B, long long ldb,
+                double *C, long long N, long long K, double *partial, size_t partial_elems, cudaStream_t s) {
+    if (precision != QDT_SPLIT) {
+        gemm_fp64_tn_sym(A, lda, B, ldb, C, N, K, partial, partial_elems, s);
+        return;
+    }
+    if (N <= 0) return;
+    const long long Mpad = rup(N, SBM), Npad = rup(N, SBN), Kpad = std::max<long long>(SBK, rup(K, SBK));
+    int *exps = (int *)ws_get(w, WS_EXP, (size_t)(Mpad + Npad + 64) * sizeof(int) * 2);
+    int *aexp = exps, *bexp = exps + Mpad + 32;
+    slice_cols(w, WS_A2, A, lda, K, N, Kpad, Mpad, aexp, s);
+    slice_cols(w, WS_B2, B, ldb, K, N, Kpad, Npad, bexp, s);
+    std::vector<long long> kt((size_t)(Mpad / SBM), K);
+    char *ktb = (char *)ws_get(w, WS_KT, 256 + kt.size() * sizeof(long long));
+    QDT_CUDA_TRY(cudaMemsetAsync(ktb, 0, 256, s));
+    long long *d_kt = (long long *)(ktb + 256);
+    QDT_CUDA_TRY(cudaMemcpyAsync(d_kt, kt.data(), kt.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+    // the split kernel overwrites C; C = A^T B is the whole second half here
+    run_umma(w, w.buf[WS_A2], Mpad, Kpad, w.buf[WS_B2], Npad, Kpad, d_kt, aexp, bexp, C, N, N, N, 1, s);
 }
 
 }  // namespace qdt

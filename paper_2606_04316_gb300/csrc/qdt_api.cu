@@ -229,6 +229,7 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
     for (int r = 0; r < nKa; ++r)
         for (int q = r; q < nKa; ++q) { hR.push_back(r); hS.push_back(q); }
     int *d_rsR = dcopy(ctx->rsR, hR, s), *d_rsS = dcopy(ctx->rsS, hS, s);
+    split_invalidate(ctx->split);
 
     // 1. density in bra order + Dmax
     int t0 = tm.n; tm.mark();
@@ -252,6 +253,8 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
     std::vector<long long> h_col(pc.nsp + 1);
     QDT_CUDA_TRY(cudaMemcpyAsync(h_prefix.data(), prefix, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
     QDT_CUDA_TRY(cudaMemcpyAsync(h_col.data(), ketcol, (pc.nsp + 1) * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    std::vector<int> h_ketsp(pc.nsp);
+    QDT_CUDA_TRY(cudaMemcpyAsync(h_ketsp.data(), ketsp, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
     // 3. ket-ordered density copy
     double *Dket = (double *)ctx->Dket.get(std::max<long long>(1, M * ncolD) * sizeof(double));
     launch_gather_rows(Dbra, pc.d_pairs, ketsp, ketcol, pc.nsp, ncolD, Dket, s);
@@ -333,11 +336,24 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
         ctx->launches += 2 + (Wc ? 1 : 0);
         if (st) {
             long long v = 0;
+            double fl = 0.0;
+            const int NC = prm.gauge ? 7 : 1;
             for (int k = b0; k < b1; ++k) {
                 int sp = pc.bra_order[k];
-                v += (long long)pc.h_pairs[sp].nfp * Krow_pair[sp];
+                const PairDev &ab = pc.h_pairs[sp];
+                v += (long long)ab.nfp * Krow_pair[sp];
+                // E R E contraction of every kept quartet: per primitive quartet
+                // 2 nha ncd nhc NC, per bra primitive pair 2 nab ncd nha NC.
+                const double nha = nherm(ab.Lab);
+                for (int q = 0; q < h_prefix[sp]; ++q) {
+                    const PairDev &cd = pc.h_pairs[h_ketsp[q]];
+                    const double ncd = cd.nfp, nhc = nherm(cd.Lab);
+                    fl += (double)ab.npp * cd.npp * 2.0 * nha * ncd * nhc * NC +
+                          (double)ab.npp * 2.0 * ab.nfp * ncd * nha * NC;
+                }
             }
             st->eri_values += v * (prm.gauge ? 6 : 1);
+            st->flops_eri += fl;
         }
         int th = tm.n; tm.mark();
         // per-tile K extents (rows in units of W rows)
@@ -393,6 +409,7 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
         QDT_CUDA_TRY(cudaStreamSynchronize(s));
         ms_eri += tm.ms(te, th);
         ms_h1 += tm.ms(th, tend);
+        tm.n = te;   // reuse the batch's events
         b0 = b1;
     }
     acc_ms[2] += ms_eri;

@@ -37,7 +37,7 @@ class Stats(ctypes.Structure):
                 ("flops_half2", ctypes.c_double), ("quartets_total", ctypes.c_longlong * 3),
                 ("quartets_kept", ctypes.c_longlong * 3), ("eri_values", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_int), ("precision", ctypes.c_int),
-                ("slices", ctypes.c_int)]
+                ("slices", ctypes.c_int), ("flops_eri", ctypes.c_double)]
 
     def as_dict(self):
         d = {}

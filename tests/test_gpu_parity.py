@@ -84,3 +84,28 @@ def test_screened_chain_matches_oracle(oracle, torch_cuda):
     assert st["quartets_kept"][1] == kept_or[1]
     for i, b in enumerate(["coulomb", "gaunt"]):
         assert np.abs(got[i] - tr.packed(b).reshape(-1)).max() <= TOL_FP64
+
+
+TOL_SPLIT = 1e-10
+
+
+@pytest.mark.parametrize("blocks", [("coulomb",), ("coulomb", "gaunt", "gauge")])
+def test_split_form_small(oracle, torch_cuda, blocks):
+    """Split (Ozaki BF16) form against the oracle within 1e-10."""
+    torch = torch_cuda
+    p = synth.chain_problem(3, 3, seed=202, shells=(0, 1), nprim=2, blocks=blocks, tau=0.0)
+    ctx, got, st = run_gpu(torch, p, list(blocks), 0, p.nK, 0.0, precision=1)
+    tr = oracle.Transform(p)
+    for i, b in enumerate(blocks):
+        ref = tr.packed(b).reshape(-1)
+        err = np.abs(got[i] - ref).max()
+        assert err <= TOL_SPLIT, (b, err)
+
+
+def test_split_form_tiny_config(oracle, torch_cuda):
+    torch = torch_cuda
+    p = synth.tiny_dc()
+    ctx, got, st = run_gpu(torch, p, ["coulomb"], 0, p.nK, 0.0, precision=1)
+    ref = oracle.Transform(p).packed("coulomb").reshape(-1)
+    assert np.abs(got[0] - ref).max() <= TOL_SPLIT
+    assert st["slices"] == 6
