@@ -160,8 +160,7 @@ __global__ void prim_pair_kernel(const ShellDev *shells, const PairDev *pairs, c
     int ip = pp_pair[ipp];
     PairDev pr = pairs[ip];
     ShellDev A = shells[pr.sa], B = shells[pr.sb];
-    int local = ipp - pr.ppoff;
-    int ia = local / B.nprim, ib = local % B.nprim;
+    int ia = pp[ipp].ia, ib = pp[ipp].ib;
     double a = exps[A.poff + ia], b = exps[B.poff + ib];
     double da = coefs[A.poff + ia], db = coefs[B.poff + ib];
     double p = a + b;
@@ -194,6 +193,8 @@ __global__ void prim_pair_kernel(const ShellDev *shells, const PairDev *pairs, c
             o.p = p;
             for (int d = 0; d < 3; ++d) o.P[d] = (a * A.A[d] + b * B.A[d]) / p;
             o.eoff = pp[ipp].eoff;
+            o.ia = ia;
+            o.ib = ib;
             pp[ipp] = o;
         }
     }

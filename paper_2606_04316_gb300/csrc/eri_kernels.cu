@@ -1,15 +1,22 @@
 // eri_kernels.cu -- AO two-electron integral tiles on the GPU (stage (i) of
 // the paper's Sec. 3.3.1 decomposition), McMurchie-Davidson in FP64:
 //
-//   (ab|K|cd) = sum_{ij in AB, kl in CD} sum_{h, h'} E^{ij}_{ab,h} (-1)^{|h'|}
-//               E^{kl}_{cd,h'} R^K_{h+h'}(rho, P - Q)
+//   (xy|K|zw) = sum_{ij in X, kl in Y} sum_{h, h'} E^{ij}_{xy,h} (-1)^{|h'|}
+//               E^{kl}_{zw,h'} R^K_{h+h'}(rho, P - Q)
 //
-//   1/r12 (Eq. Coulomb):   R^n_000 = (-2 rho)^n F_n(T) * 2 pi^{5/2} / (p q sqrt(p+q))
+//   1/r12 (Eq. Coulomb):    R^n_000 = (-2 rho)^n F_n(T) * 2 pi^{5/2} / (p q sqrt(p+q))
 //   r12 (for Eq. gaugeInt): R^n_000 = (-2 rho)^n (F_n - F_{n-1})(T) * pi^{5/2} sqrt(p+q) / (p q)^2,
-//                          F_{-1}(T) = -(2 T F_0 + e^{-T})  (Gaussian-smeared distance)
-//   gauge kernel:  (ab|r_I r_J/r^3|cd) = delta_IJ (ab|1/r|cd) - (ab|d_I d_J r|cd),
+//                           F_{-1}(T) = -(2 T F_0 + e^{-T})  (Gaussian-smeared distance)
+//   gauge kernel:  (xy|r_I r_J/r^3|zw) = delta_IJ (xy|1/r|zw) - (xy|d_I d_J r|zw),
 //                  the last term shifting the Hermite index of the r12 tensor by e_I + e_J,
 //   R^n_{t+1,u,v} = t R^{n+1}_{t-1,u,v} + X_PQ R^{n+1}_{t,u,v}  (same in u, v).
+//
+// Work layout: a CTA owns one bra shell pair and a run of ket shell pairs.
+// For every shell quartet the cheaper orientation is contracted (the pair
+// with more function pairs takes the outer, per-primitive-pair role), and for
+// every outer primitive pair all inner primitive pairs are processed together:
+// Boys values in parallel, one barrier per recursion level, then the
+// contraction T = R E' and the accumulation G += E T.
 #include <math.h>
 
 #include "qdt_internal.cuh"
@@ -49,182 +56,228 @@ __device__ void boys_eval(const double *tab, double T, int nmax, double *F) {
     }
 }
 
-struct BlockSmem {
-    double *G, *T, *RC[2], *RR[2], *F, *scal;
-    int *trA, *trC;
+// Shared-memory plan (sizes from the class maxima; must match eri_smem_bytes()).
+struct Plan {
+    int NC;         // 1 Coulomb, 7 gauge
+    int ach, cch;   // chunk of outer / inner function pairs
+    int nhMax;      // nherm(max Lab)
+    int LtC, LtR;   // top Hermite orders of the Coulomb and r12 tensors (LtR < 0: none)
+    int klg;        // inner primitive pairs per group
 };
 
-// Shared-memory plan of one block chunk (must match eri_smem_bytes()).
-__device__ inline BlockSmem carve(double *sm, int NC, int ach, int cch, int nhaMax, int LtC, int LtR) {
+struct BlockSmem {
+    double *G, *T, *RC, *RR, *F, *sc;
+    int *trX, *trY;
+};
+
+__host__ __device__ inline size_t smem_doubles(const Plan &p) {
+    size_t nrC = nherm(p.LtC), nrR = p.LtR >= 0 ? nherm(p.LtR) : 0;
+    return (size_t)p.NC * p.ach * p.cch + (size_t)p.NC * p.nhMax * p.cch + 2 * p.klg * nrC + 2 * p.klg * nrR +
+           (size_t)p.klg * (kBoysNMax + 3) + (size_t)p.klg * 8;
+}
+
+size_t eri_smem_bytes(const Plan &p) { return smem_doubles(p) * sizeof(double) + 6 * p.nhMax * sizeof(int) + 64; }
+
+__device__ inline BlockSmem carve(double *sm, const Plan &p) {
     BlockSmem b;
-    b.G = sm; sm += (size_t)NC * ach * cch;
-    b.T = sm; sm += (size_t)NC * nhaMax * cch;
-    b.RC[0] = sm; sm += nherm(LtC);
-    b.RC[1] = sm; sm += nherm(LtC);
-    b.RR[0] = sm; sm += (LtR >= 0 ? nherm(LtR) : 0);
-    b.RR[1] = sm; sm += (LtR >= 0 ? nherm(LtR) : 0);
-    b.F = sm; sm += kBoysNMax + 3;
-    b.scal = sm; sm += 8;
-    b.trA = (int *)sm;
-    b.trC = b.trA + 3 * nherm(kMaxLPair);
+    size_t nrC = nherm(p.LtC), nrR = p.LtR >= 0 ? nherm(p.LtR) : 0;
+    b.G = sm; sm += (size_t)p.NC * p.ach * p.cch;
+    b.T = sm; sm += (size_t)p.NC * p.nhMax * p.cch;
+    b.RC = sm; sm += 2 * p.klg * nrC;
+    b.RR = sm; sm += 2 * p.klg * nrR;
+    b.F = sm; sm += (size_t)p.klg * (kBoysNMax + 3);
+    b.sc = sm; sm += (size_t)p.klg * 8;
+    b.trX = (int *)sm;
+    b.trY = b.trX + 3 * p.nhMax;
     return b;
 }
 
-size_t eri_smem_bytes(int NC, int ach, int cch, int maxLab, bool gauge) {
-    int LtC = 2 * maxLab, LtR = gauge ? 2 * maxLab + 2 : -1;
-    size_t d = (size_t)NC * ach * cch + (size_t)NC * nherm(maxLab) * cch + 2 * nherm(LtC) +
-               (LtR >= 0 ? 2 * nherm(LtR) : 0) + kBoysNMax + 3 + 8;
-    return d * sizeof(double) + 6 * nherm(kMaxLPair) * sizeof(int);
+__host__ __device__ inline double orient_cost(const PairDev &X, const PairDev &Y) {
+    double nhx = nherm(X.Lab), nhy = nherm(Y.Lab);
+    return (double)X.npp * Y.npp * nhx * Y.nfp * nhy + (double)X.npp * X.nfp * Y.nfp * nhx;
 }
 
-// One chunk (ab in [a0,a1), cd in [c0,c1)) of the block (AB|CD); results in
-// b.G[comp][a][c].  NC = 1 (Coulomb) or 7 (gauge: [0] Coulomb, [1..6]
-// (ab|d_I d_J r|cd) for IJ = xx,xy,xz,yy,yz,zz).
+// One chunk (x in [x0,x1) of X, y in [y0,y1) of Y) of the block (X|Y);
+// results in b.G[comp][x][y].  NC = 1 (Coulomb) or 7 (gauge: [0] Coulomb,
+// [1..6] (xy|d_I d_J r|zw) for IJ = xx,xy,xz,yy,yz,zz).
 template <bool GAUGE>
-__device__ void block_chunk(const PrimPairDev *pp, const double *E, const double *boys,
-                            const PairDev &AB, const PairDev &CD, int a0, int a1, int c0, int c1,
-                            BlockSmem &b) {
+__device__ void block_chunk(const PrimPairDev *pp, const double *E, const double *boys, const PairDev &X,
+                            const PairDev &Y, int x0, int x1, int y0, int y1, const Plan &pl, BlockSmem &b) {
     constexpr int NC = GAUGE ? 7 : 1;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int La = AB.Lab, Lc = CD.Lab;
-    const int nha = nherm(La), nhc = nherm(Lc);
-    const int L = La + Lc, Lr = L + 2;
-    const int ach = a1 - a0, cch = c1 - c0;
-    for (int h = tid; h < nha; h += nt) htrip_d(h, b.trA[3 * h], b.trA[3 * h + 1], b.trA[3 * h + 2]);
-    for (int h = tid; h < nhc; h += nt) htrip_d(h, b.trC[3 * h], b.trC[3 * h + 1], b.trC[3 * h + 2]);
-    for (int i = tid; i < NC * ach * cch; i += nt) b.G[i] = 0.0;
+    const int Lx = X.Lab, Ly = Y.Lab;
+    const int nhx = nherm(Lx), nhy = nherm(Ly);
+    const int L = Lx + Ly, Lr = L + 2, Ltop = GAUGE ? Lr : L;
+    const int nrC = nherm(pl.LtC), nrR = GAUGE ? nherm(pl.LtR) : 0;
+    const int xch = x1 - x0, ych = y1 - y0;
+    for (int h = tid; h < nhx; h += nt) htrip_d(h, b.trX[3 * h], b.trX[3 * h + 1], b.trX[3 * h + 2]);
+    for (int h = tid; h < nhy; h += nt) htrip_d(h, b.trY[3 * h], b.trY[3 * h + 1], b.trY[3 * h + 2]);
+    for (int i = tid; i < NC * xch * ych; i += nt) b.G[i] = 0.0;
     __syncthreads();
-    for (int ij = 0; ij < AB.npp; ++ij) {
-        const PrimPairDev pa = pp[AB.ppoff + ij];
-        for (int i = tid; i < NC * nha * cch; i += nt) b.T[i] = 0.0;
-        for (int kl = 0; kl < CD.npp; ++kl) {
-            const PrimPairDev pc = pp[CD.ppoff + kl];
-            if (tid == 0) {
+    for (int ij = 0; ij < X.npp; ++ij) {
+        const PrimPairDev pa = pp[X.ppoff + ij];
+        for (int i = tid; i < NC * nhx * ych; i += nt) b.T[i] = 0.0;
+        for (int g0 = 0; g0 < Y.npp; g0 += pl.klg) {
+            const int ng = min(pl.klg, Y.npp - g0);
+            // Boys values and geometry of the group's primitive quartets
+            for (int g = tid; g < ng; g += nt) {
+                const PrimPairDev pc = pp[Y.ppoff + g0 + g];
                 double p = pa.p, q = pc.p, rho = p * q / (p + q);
-                double X = pa.P[0] - pc.P[0], Y = pa.P[1] - pc.P[1], Z = pa.P[2] - pc.P[2];
-                double T = rho * (X * X + Y * Y + Z * Z);
-                int nmax = GAUGE ? Lr : L;
-                boys_eval(boys, T, nmax, b.F + 1);
-                b.F[0] = -(2.0 * T * b.F[1] + exp(-T));        // F_{-1}
-                b.scal[0] = X; b.scal[1] = Y; b.scal[2] = Z;
-                b.scal[3] = -2.0 * rho;
-                b.scal[4] = 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p + q));
-                b.scal[5] = pow(M_PI, 2.5) * sqrt(p + q) / (p * p * q * q);
+                double Xq = pa.P[0] - pc.P[0], Yq = pa.P[1] - pc.P[1], Zq = pa.P[2] - pc.P[2];
+                double Tv = rho * (Xq * Xq + Yq * Yq + Zq * Zq);
+                double *F = b.F + g * (kBoysNMax + 3);
+                boys_eval(boys, Tv, Ltop, F + 1);
+                F[0] = -(2.0 * Tv * F[1] + exp(-Tv));       // F_{-1}
+                double *sc = b.sc + g * 8;
+                sc[0] = Xq; sc[1] = Yq; sc[2] = Zq; sc[3] = -2.0 * rho;
+                sc[4] = 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p + q));
+                sc[5] = pow(M_PI, 2.5) * sqrt(p + q) / (p * p * q * q);
             }
             __syncthreads();
-            const double X = b.scal[0], Y = b.scal[1], Z = b.scal[2], m2r = b.scal[3];
-            const int Ltop = GAUGE ? Lr : L;
+            // Hermite recursion, all primitive quartets of the group per level
             for (int n = Ltop; n >= 0; --n) {
-                double *dC = b.RC[n & 1], *sC = b.RC[(n + 1) & 1];
-                double *dR = b.RR[n & 1], *sR = b.RR[(n + 1) & 1];
-                int cntR = GAUGE ? nherm(Lr - n) : 0;
-                int cntC = (n <= L) ? nherm(L - n) : 0;
-                int cnt = cntR > cntC ? cntR : cntC;
-                for (int h = tid; h < cnt; h += nt) {
+                const int cntC = (n <= L) ? nherm(L - n) : 0;
+                const int cntR = GAUGE ? nherm(Lr - n) : 0;
+                const int cnt = cntR > cntC ? cntR : cntC;
+                for (int it = tid; it < ng * cnt; it += nt) {
+                    const int g = it / cnt, h = it - g * cnt;
+                    const double *sc = b.sc + g * 8;
+                    const double Xq = sc[0], Yq = sc[1], Zq = sc[2];
                     int t, u, v;
                     htrip_d(h, t, u, v);
-                    double base = 0.0;
-                    if (h == 0) base = pow(m2r, n);
-                    // Coulomb tensor
                     if (h < cntC) {
+                        double *d = b.RC + ((size_t)(n & 1) * pl.klg + g) * nrC;
+                        const double *s = b.RC + ((size_t)((n + 1) & 1) * pl.klg + g) * nrC;
                         double r;
-                        if (h == 0) r = base * b.F[n + 1] * b.scal[4];
-                        else if (t > 0) r = (t > 1 ? (t - 1) * sC[hidx(t - 2, u, v)] : 0.0) + X * sC[hidx(t - 1, u, v)];
-                        else if (u > 0) r = (u > 1 ? (u - 1) * sC[hidx(t, u - 2, v)] : 0.0) + Y * sC[hidx(t, u - 1, v)];
-                        else r = (v > 1 ? (v - 1) * sC[hidx(t, u, v - 2)] : 0.0) + Z * sC[hidx(t, u, v - 1)];
-                        dC[h] = r;
+                        if (h == 0) r = pow(sc[3], n) * b.F[g * (kBoysNMax + 3) + n + 1] * sc[4];
+                        else if (t > 0) r = (t > 1 ? (t - 1) * s[hidx(t - 2, u, v)] : 0.0) + Xq * s[hidx(t - 1, u, v)];
+                        else if (u > 0) r = (u > 1 ? (u - 1) * s[hidx(t, u - 2, v)] : 0.0) + Yq * s[hidx(t, u - 1, v)];
+                        else r = (v > 1 ? (v - 1) * s[hidx(t, u, v - 2)] : 0.0) + Zq * s[hidx(t, u, v - 1)];
+                        d[h] = r;
                     }
                     if (GAUGE && h < cntR) {
+                        double *d = b.RR + ((size_t)(n & 1) * pl.klg + g) * nrR;
+                        const double *s = b.RR + ((size_t)((n + 1) & 1) * pl.klg + g) * nrR;
+                        const double *F = b.F + g * (kBoysNMax + 3);
                         double r;
-                        if (h == 0) r = base * (b.F[n + 1] - b.F[n]) * b.scal[5];
-                        else if (t > 0) r = (t > 1 ? (t - 1) * sR[hidx(t - 2, u, v)] : 0.0) + X * sR[hidx(t - 1, u, v)];
-                        else if (u > 0) r = (u > 1 ? (u - 1) * sR[hidx(t, u - 2, v)] : 0.0) + Y * sR[hidx(t, u - 1, v)];
-                        else r = (v > 1 ? (v - 1) * sR[hidx(t, u, v - 2)] : 0.0) + Z * sR[hidx(t, u, v - 1)];
-                        dR[h] = r;
+                        if (h == 0) r = pow(sc[3], n) * (F[n + 1] - F[n]) * sc[5];
+                        else if (t > 0) r = (t > 1 ? (t - 1) * s[hidx(t - 2, u, v)] : 0.0) + Xq * s[hidx(t - 1, u, v)];
+                        else if (u > 0) r = (u > 1 ? (u - 1) * s[hidx(t, u - 2, v)] : 0.0) + Yq * s[hidx(t, u - 1, v)];
+                        else r = (v > 1 ? (v - 1) * s[hidx(t, u, v - 2)] : 0.0) + Zq * s[hidx(t, u, v - 1)];
+                        d[h] = r;
                     }
                 }
                 __syncthreads();
             }
-            const double *RC0 = b.RC[0], *RR0 = b.RR[0];
-            const double *Ekl = E + pc.eoff;
-            for (int idx = tid; idx < nha * cch; idx += nt) {
-                int h = idx / cch, c = idx - h * cch;
-                int t = b.trA[3 * h], u = b.trA[3 * h + 1], v = b.trA[3 * h + 2];
-                const double *e = Ekl + (size_t)(c0 + c) * nhc;
-                double sc = 0.0;
-                double sr[6] = {0, 0, 0, 0, 0, 0};
-                for (int hp = 0; hp < nhc; ++hp) {
-                    int tp = b.trC[3 * hp], up = b.trC[3 * hp + 1], vp = b.trC[3 * hp + 2];
-                    double ev = ((tp + up + vp) & 1) ? -e[hp] : e[hp];
-                    int T0 = t + tp, U0 = u + up, V0 = v + vp;
-                    sc += RC0[hidx(T0, U0, V0)] * ev;
-                    if (GAUGE) {
-                        sr[0] += RR0[hidx(T0 + 2, U0, V0)] * ev;
-                        sr[1] += RR0[hidx(T0 + 1, U0 + 1, V0)] * ev;
-                        sr[2] += RR0[hidx(T0 + 1, U0, V0 + 1)] * ev;
-                        sr[3] += RR0[hidx(T0, U0 + 2, V0)] * ev;
-                        sr[4] += RR0[hidx(T0, U0 + 1, V0 + 1)] * ev;
-                        sr[5] += RR0[hidx(T0, U0, V0 + 2)] * ev;
+            // T[c][h][y] += sum_{kl in group} sum_h' R[h+h'] (-1)^|h'| E^{kl}[y][h']
+            for (int idx = tid; idx < nhx * ych; idx += nt) {
+                const int h = idx / ych, yy = idx - h * ych;
+                const int t = b.trX[3 * h], u = b.trX[3 * h + 1], v = b.trX[3 * h + 2];
+                double sc0 = 0.0, sr[6] = {0, 0, 0, 0, 0, 0};
+                for (int g = 0; g < ng; ++g) {
+                    const double *e = E + pp[Y.ppoff + g0 + g].eoff + (size_t)(y0 + yy) * nhy;
+                    const double *RC0 = b.RC + (size_t)g * nrC;
+                    const double *RR0 = b.RR + (size_t)g * nrR;
+                    for (int hp = 0; hp < nhy; ++hp) {
+                        const int tp = b.trY[3 * hp], up = b.trY[3 * hp + 1], vp = b.trY[3 * hp + 2];
+                        const double ev = ((tp + up + vp) & 1) ? -__ldg(e + hp) : __ldg(e + hp);
+                        const int T0 = t + tp, U0 = u + up, V0 = v + vp;
+                        sc0 = fma(RC0[hidx(T0, U0, V0)], ev, sc0);
+                        if (GAUGE) {
+                            sr[0] = fma(RR0[hidx(T0 + 2, U0, V0)], ev, sr[0]);
+                            sr[1] = fma(RR0[hidx(T0 + 1, U0 + 1, V0)], ev, sr[1]);
+                            sr[2] = fma(RR0[hidx(T0 + 1, U0, V0 + 1)], ev, sr[2]);
+                            sr[3] = fma(RR0[hidx(T0, U0 + 2, V0)], ev, sr[3]);
+                            sr[4] = fma(RR0[hidx(T0, U0 + 1, V0 + 1)], ev, sr[4]);
+                            sr[5] = fma(RR0[hidx(T0, U0, V0 + 2)], ev, sr[5]);
+                        }
                     }
                 }
-                b.T[(size_t)h * cch + c] += sc;
+                b.T[(size_t)h * ych + yy] += sc0;
                 if (GAUGE)
-                    for (int k = 0; k < 6; ++k) b.T[((size_t)(k + 1) * nha + h) * cch + c] += sr[k];
+                    for (int k = 0; k < 6; ++k) b.T[((size_t)(k + 1) * nhx + h) * ych + yy] += sr[k];
             }
             __syncthreads();
         }
+        // G[c][x][y] += sum_h E^{ij}[x][h] T[c][h][y]
         const double *Eij = E + pa.eoff;
-        for (int idx = tid; idx < ach * cch; idx += nt) {
-            int a = idx / cch, c = idx - a * cch;
-            const double *e = Eij + (size_t)(a0 + a) * nha;
+        for (int idx = tid; idx < xch * ych; idx += nt) {
+            const int xx = idx / ych, yy = idx - xx * ych;
+            const double *e = Eij + (size_t)(x0 + xx) * nhx;
             double s[NC];
+#pragma unroll
             for (int k = 0; k < NC; ++k) s[k] = 0.0;
-            for (int h = 0; h < nha; ++h) {
-                double ev = e[h];
-                for (int k = 0; k < NC; ++k) s[k] += ev * b.T[((size_t)k * nha + h) * cch + c];
+            for (int h = 0; h < nhx; ++h) {
+                const double ev = __ldg(e + h);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) s[k] = fma(ev, b.T[((size_t)k * nhx + h) * ych + yy], s[k]);
             }
-            for (int k = 0; k < NC; ++k) b.G[((size_t)k * ach + a) * cch + c] += s[k];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) b.G[((size_t)k * xch + xx) * ych + yy] += s[k];
         }
         __syncthreads();
     }
 }
 
-struct ChunkCfg { int ach, cch; };
-
 // Screened rows: one CTA per task (bra shell pair x range of sorted ket positions).
 template <bool GAUGE>
-__global__ void __launch_bounds__(128) eri_rows_kernel(EriParams prm, const EriTask *tasks, ChunkCfg cfg) {
+__global__ void __launch_bounds__(256) eri_rows_kernel(EriParams prm, const EriTask *tasks, Plan pl) {
     extern __shared__ double sm[];
     const EriTask tk = tasks[blockIdx.x];
     const PairDev AB = prm.pairs[tk.bra_sp];
-    constexpr int NC = GAUGE ? 7 : 1;
-    BlockSmem b = carve(sm, NC, cfg.ach, cfg.cch, nherm(kMaxLPair), 2 * kMaxLPair,
-                        GAUGE ? 2 * kMaxLPair + 2 : -1);
+    BlockSmem b = carve(sm, pl);
+    const int ij_of[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
     for (int kp = tk.k0; kp < tk.k1; ++kp) {
-        const PairDev CD = prm.pairs[prm.ket_sp[kp]];
+        const int cd_id = prm.ket_sp[kp];
+        const PairDev CD = prm.pairs[cd_id];
         const long long col = prm.ket_col[kp];
-        for (int a0 = 0; a0 < AB.nfp; a0 += cfg.ach) {
-            int a1 = min(AB.nfp, a0 + cfg.ach);
-            for (int c0 = 0; c0 < CD.nfp; c0 += cfg.cch) {
-                int c1 = min(CD.nfp, c0 + cfg.cch);
-                block_chunk<GAUGE>(prm.pp, prm.E, prm.boys, AB, CD, a0, a1, c0, c1, b);
-                int ach = a1 - a0, cch = c1 - c0;
-                for (int idx = threadIdx.x; idx < ach * cch; idx += blockDim.x) {
-                    int a = idx / cch, c = idx - a * cch;
-                    long long row = AB.rowoff + a0 + a - prm.row0;
-                    long long cc = col + c0 + c;
+        // (CD|AB) also kept?  Then the lower pair id computes both blocks.
+        const bool rev = prm.sym && cd_id != tk.bra_sp && prm.ket_pos[tk.bra_sp] < prm.prefix[cd_id];
+        if (rev && cd_id < tk.bra_sp) continue;
+        const long long col_rev = rev ? prm.ket_col[prm.ket_pos[tk.bra_sp]] : 0;
+        // contract the orientation with the smaller cost; swapped -> G is (CD|AB)
+        const bool swap = orient_cost(CD, AB) < orient_cost(AB, CD);
+        const PairDev &X = swap ? CD : AB, &Y = swap ? AB : CD;
+        for (int x0 = 0; x0 < X.nfp; x0 += pl.ach) {
+            const int x1 = min(X.nfp, x0 + pl.ach);
+            for (int y0 = 0; y0 < Y.nfp; y0 += pl.cch) {
+                const int y1 = min(Y.nfp, y0 + pl.cch);
+                block_chunk<GAUGE>(prm.pp, prm.E, prm.boys, X, Y, x0, x1, y0, y1, pl, b);
+                const int xch = x1 - x0, ych = y1 - y0;
+                for (int idx = threadIdx.x; idx < xch * ych; idx += blockDim.x) {
+                    const int xx = idx / ych, yy = idx - xx * ych;
+                    const int a = swap ? y0 + yy : x0 + xx;      // bra function pair
+                    const int c = swap ? x0 + xx : y0 + yy;      // ket function pair
+                    const long long row = AB.rowoff + a - prm.row0;
+                    const long long cc = col + c;
                     if (!GAUGE) {
                         prm.W[row * prm.ldw + cc] = b.G[idx];
                     } else {
-                        double C = b.G[idx];
-                        const double *H = b.G + (size_t)ach * cch;
-                        const int ij_of[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+                        const double C = b.G[idx];
+                        const double *H = b.G + (size_t)xch * ych;
                         for (int I = 0; I < 3; ++I)
                             for (int J = 0; J < 3; ++J) {
-                                double h = H[(size_t)ij_of[I][J] * ach * cch + idx];
+                                // K_IJ is symmetric, so the swapped block needs no index change
+                                const double h = H[(size_t)ij_of[I][J] * xch * ych + idx];
                                 prm.W[(row * 3 + I) * prm.ldw + cc * 3 + J] = (I == J ? C : 0.0) - h;
                             }
                         if (prm.with_coulomb) prm.Wc[row * prm.ldwc + cc] = C;
+                    }
+                    if (rev) {    // the same integrals at (cd, ab): rows of CD, columns of AB
+                        const long long row2 = CD.rowoff + c - prm.row0;
+                        const long long cc2 = col_rev + a;
+                        if (!GAUGE) {
+                            prm.W[row2 * prm.ldw + cc2] = b.G[idx];
+                        } else {
+                            const double C = b.G[idx];
+                            const double *H = b.G + (size_t)xch * ych;
+                            for (int I = 0; I < 3; ++I)
+                                for (int J = 0; J < 3; ++J) {
+                                    const double h = H[(size_t)ij_of[I][J] * xch * ych + idx];
+                                    prm.W[(row2 * 3 + I) * prm.ldw + cc2 * 3 + J] = (I == J ? C : 0.0) - h;
+                                }
+                            if (prm.with_coulomb) prm.Wc[row2 * prm.ldwc + cc2] = C;
+                        }
                     }
                 }
                 __syncthreads();
@@ -233,46 +286,49 @@ __global__ void __launch_bounds__(128) eri_rows_kernel(EriParams prm, const EriT
     }
 }
 
-ChunkCfg eri_chunks(int maxnfp, int maxLab, bool gauge, size_t *smem) {
-    int NC = gauge ? 7 : 1;
-    ChunkCfg c;
-    c.ach = c.cch = maxnfp < 96 ? maxnfp : 96;
-    const size_t budget = 200 * 1024;
-    while (eri_smem_bytes(NC, c.ach, c.cch, kMaxLPair, gauge) > budget && c.ach > 8) {
-        c.ach = (c.ach + 1) / 2;
-        c.cch = (c.cch + 1) / 2;
+Plan eri_plan(int maxnfp, int maxLab, int maxnpp, bool gauge, size_t *smem) {
+    Plan p;
+    p.NC = gauge ? 7 : 1;
+    p.ach = p.cch = maxnfp;
+    p.nhMax = nherm(maxLab);
+    p.LtC = 2 * maxLab;
+    p.LtR = gauge ? 2 * maxLab + 2 : -1;
+    p.klg = maxnpp < 16 ? (maxnpp > 0 ? maxnpp : 1) : 16;
+    const size_t budget = 110 * 1024;          // two CTAs per SM
+    while (eri_smem_bytes(p) > budget && (p.ach > 16 || p.klg > 2)) {
+        if (p.klg > 4) p.klg = (p.klg + 1) / 2;
+        else { p.ach = (p.ach + 1) / 2; p.cch = (p.cch + 1) / 2; }
     }
-    *smem = eri_smem_bytes(NC, c.ach, c.cch, kMaxLPair, gauge);
-    return c;
+    *smem = eri_smem_bytes(p);
+    return p;
 }
 
-void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxnfp, int maxLab,
+void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxnfp, int maxLab, int maxnpp,
                 cudaStream_t s) {
     if (ntasks <= 0) return;
     size_t smem;
-    ChunkCfg cfg = eri_chunks(maxnfp, maxLab, prm.gauge != 0, &smem);
+    Plan pl = eri_plan(maxnfp, maxLab, maxnpp, prm.gauge != 0, &smem);
     if (prm.gauge) {
         QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        eri_rows_kernel<true><<<ntasks, 128, smem, s>>>(prm, tasks, cfg);
+        eri_rows_kernel<true><<<ntasks, 256, smem, s>>>(prm, tasks, pl);
     } else {
         QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        eri_rows_kernel<false><<<ntasks, 128, smem, s>>>(prm, tasks, cfg);
+        eri_rows_kernel<false><<<ntasks, 256, smem, s>>>(prm, tasks, pl);
     }
     QDT_CHECK_LAUNCH();
 }
 
 // Schwarz diagonals: Q[AB] = max over ab of sqrt(|(ab|ab)|), Coulomb kernel.
-__global__ void __launch_bounds__(128) schwarz_kernel(const PrimPairDev *pp, const PairDev *pairs,
-                                                      const double *E, const double *boys,
-                                                      ChunkCfg cfg, double *Q) {
+__global__ void __launch_bounds__(256) schwarz_kernel(const PrimPairDev *pp, const PairDev *pairs, const double *E,
+                                                      const double *boys, Plan pl, double *Q) {
     extern __shared__ double sm[];
     const PairDev AB = pairs[blockIdx.x];
-    BlockSmem b = carve(sm, 1, cfg.ach, cfg.cch, nherm(kMaxLPair), 2 * kMaxLPair, -1);
+    BlockSmem b = carve(sm, pl);
     double qmax = 0.0;
-    for (int a0 = 0; a0 < AB.nfp; a0 += cfg.ach) {
-        int a1 = min(AB.nfp, a0 + cfg.ach);
-        block_chunk<false>(pp, E, boys, AB, AB, a0, a1, a0, a1, b);
-        int ach = a1 - a0;
+    for (int a0 = 0; a0 < AB.nfp; a0 += pl.ach) {
+        const int a1 = min(AB.nfp, a0 + pl.ach);
+        block_chunk<false>(pp, E, boys, AB, AB, a0, a1, a0, a1, pl, b);
+        const int ach = a1 - a0;
         if (threadIdx.x == 0)
             for (int a = 0; a < ach; ++a) qmax = fmax(qmax, sqrt(fabs(b.G[(size_t)a * ach + a])));
         __syncthreads();
@@ -280,16 +336,16 @@ __global__ void __launch_bounds__(128) schwarz_kernel(const PrimPairDev *pp, con
     if (threadIdx.x == 0) Q[blockIdx.x] = qmax;
 }
 
-void launch_schwarz(const ShellDev *shells, const PairDev *pairs, const PrimPairDev *pp,
-                    const double *E, const double *boys, int npairs, int maxnfp, int maxLab,
-                    double *Q, double *scratch, cudaStream_t s) {
-    (void)shells; (void)scratch;
+void launch_schwarz(const ShellDev *shells, const PairDev *pairs, const PrimPairDev *pp, const double *E,
+                    const double *boys, int npairs, int maxnfp, int maxLab, int maxnpp, double *Q,
+                    cudaStream_t s) {
+    (void)shells;
     if (npairs <= 0) return;
     size_t smem;
-    ChunkCfg cfg = eri_chunks(maxnfp, maxLab, false, &smem);
-    cfg.cch = cfg.ach;
+    Plan pl = eri_plan(maxnfp, maxLab, maxnpp, false, &smem);
+    pl.cch = pl.ach;
     QDT_CUDA_TRY(cudaFuncSetAttribute(schwarz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    schwarz_kernel<<<npairs, 128, smem, s>>>(pp, pairs, E, boys, cfg, Q);
+    schwarz_kernel<<<npairs, 256, smem, s>>>(pp, pairs, E, boys, pl, Q);
     QDT_CHECK_LAUNCH();
 }
 

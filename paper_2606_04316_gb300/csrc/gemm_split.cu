@@ -435,11 +435,13 @@ static void slice_cols(SplitWorkspace &w, int slot, const double *X, long long l
     long long rpb = std::max<long long>(64, (rows + 1023) / 1024);
     dim3 g1((unsigned)((cols + 255) / 256), (unsigned)((rows + rpb - 1) / rpb));
     if (rows > 0 && cols > 0) col_max_kernel<<<g1, 256, 0, s>>>(X, ld, rows, cols, rpb, cmax);
+    QDT_CHECK_KERNEL("col_max_kernel");
     col_exp_kernel<<<(unsigned)((Cpad + 255) / 256), 256, 0, s>>>(cmax, cols, Cpad, colexp);
+    QDT_CHECK_KERNEL("col_exp_kernel");
     __nv_bfloat16 *out = (__nv_bfloat16 *)ws_get(w, slot, (size_t)kSlices * Cpad * Rpad * 2 + (size_t)Cpad * sizeof(int));
     dim3 g2((unsigned)(Rpad / 64), (unsigned)(Cpad / 32));
     slice_cols_t_kernel<<<g2, 256, 0, s>>>(X, ld, rows, cols, Rpad, Cpad, colexp, out);
-    QDT_CHECK_LAUNCH();
+    QDT_CHECK_KERNEL("slice_cols_t_kernel");
 }
 
 static void run_umma(SplitWorkspace &w, void *Asl, long long Mpad, long long KpadA, void *Bsl, long long Npad,
@@ -452,7 +454,7 @@ static void run_umma(SplitWorkspace &w, void *Asl, long long Mpad, long long Kpa
     dim3 grid((unsigned)(Npad / SBN), (unsigned)(Mpad / SBM));
     ozaki_umma_kernel<<<grid, 128, kSmemBytes, s>>>(ta, tb, Mpad, Npad, d_kt128, rowexp, colexp, C, ldc, M, N,
                                                     upper, status);
-    QDT_CHECK_LAUNCH();
+    QDT_CHECK_KERNEL("ozaki_umma_kernel");
     int h = 0;
     QDT_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     QDT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -486,7 +488,7 @@ void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda
     int *rowexp = (int *)ws_get(w, WS_EXP, (size_t)(Mpad + Npad + 64) * sizeof(int) * 2);
     __nv_bfloat16 *Asl = (__nv_bfloat16 *)ws_get(w, WS_A, (size_t)kSlices * Mpad * KpadA * 2);
     slice_rows_kernel<<<(unsigned)Mpad, 256, 0, s>>>(A, lda, M, std::min(kmax, lda), Mpad, KpadA, Asl, rowexp);
-    QDT_CHECK_LAUNCH();
+    QDT_CHECK_KERNEL("slice_rows_kernel");
     // B slices (column scaled, transposed), cached per (pointer, shape) until
     // split_invalidate(): the densities are the same for every row batch.
     const long long Krows = kmax;

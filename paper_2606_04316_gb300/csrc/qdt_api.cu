@@ -82,6 +82,7 @@ struct qdt_ctx {
     bool has_basis = false;
     int nL = 0, nS = 0, nshL = 0;
     std::vector<ShellDev> h_shells;
+    std::vector<double> h_exps;
     DBuf shells, exps, coefs, norms, boys;
     PairClass cls[2];
     ClassBufs cb[2];
@@ -91,7 +92,7 @@ struct qdt_ctx {
     DBuf Cq;
     // per-transform workspace
     DBuf Dbra, Dket, V, Vg, W, Wc, Dmax, wsort, ketsp, ketcol, prefix, ktile, tasks, O, partial,
-        stage, rsR, rsS;
+        stage, rsR, rsS, kpos;
     SplitWorkspace split;
     cudaEvent_t ev[16];
     int launches = 0;
@@ -114,6 +115,13 @@ bool is_device_ptr(const void *p) {
 }
 
 int lcart(int l) { return (l + 1) * (l + 2) / 2; }
+
+// FP64 multiply-adds of the E R E contraction of one shell quartet with X as
+// the outer (per primitive pair) side.
+double orient_cost_h(const PairDev &X, const PairDev &Y) {
+    double nhx = nherm(X.Lab), nhy = nherm(Y.Lab);
+    return (double)X.npp * Y.npp * nhx * Y.nfp * nhy + (double)X.npp * X.nfp * Y.nfp * nhx;
+}
 
 // Build the shell-pair tables of class `c` (0: LL+SS, 1: LS); pairs in natural
 // order, primitive pairs and E offsets.
@@ -141,16 +149,24 @@ void build_class(qdt_ctx *ctx, int c) {
         pr.sb = sp[i].second;
         pr.nfp = (pr.sa == pr.sb) ? A.nfunc * (A.nfunc + 1) / 2 : A.nfunc * B.nfunc;
         pr.Lab = (A.l + A.isS) + (B.l + B.isS);
-        pr.npp = A.nprim * B.nprim;
         pr.ppoff = (int)hpp.size();
         pr.rowoff = 0;
-        for (int k = 0; k < pr.npp; ++k) {
-            PrimPairDev q{};
-            q.eoff = eoff;
-            eoff += (long long)pr.nfp * nherm(pr.Lab);
-            hpp.push_back(q);
-            pp_pair.push_back(i);
-        }
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) r2 += (A.A[d] - B.A[d]) * (A.A[d] - B.A[d]);
+        for (int ia = 0; ia < A.nprim; ++ia)
+            for (int ib = 0; ib < B.nprim; ++ib) {
+                double a = ctx->h_exps[A.poff + ia], bb = ctx->h_exps[B.poff + ib];
+                if (std::exp(-a * bb / (a + bb) * r2) < kPrimPairTol) continue;
+                PrimPairDev q{};
+                q.eoff = eoff;
+                q.ia = ia;
+                q.ib = ib;
+                eoff += (long long)pr.nfp * nherm(pr.Lab);
+                hpp.push_back(q);
+                pp_pair.push_back(i);
+            }
+        pr.npp = (int)hpp.size() - pr.ppoff;
+        pc.maxnpp = std::max(pc.maxnpp, pr.npp);
         M += pr.nfp;
         pc.maxnfp = std::max(pc.maxnfp, pr.nfp);
         pc.maxLab = std::max(pc.maxLab, pr.Lab);
@@ -172,7 +188,7 @@ void build_class(qdt_ctx *ctx, int c) {
     // Schwarz diagonals, then the bra order (Q descending, ties by id)
     pc.d_Q = (double *)b.Q.get(std::max(1, pc.nsp) * sizeof(double));
     launch_schwarz((const ShellDev *)ctx->shells.p, pc.d_pairs, pc.d_pp, pc.d_E,
-                   (const double *)ctx->boys.p, pc.nsp, pc.maxnfp, pc.maxLab, pc.d_Q, nullptr, s);
+                   (const double *)ctx->boys.p, pc.nsp, pc.maxnfp, pc.maxLab, pc.maxnpp, pc.d_Q, s);
     ctx->launches++;
     pc.h_Q.resize(pc.nsp);
     QDT_CUDA_TRY(cudaMemcpyAsync(pc.h_Q.data(), pc.d_Q, pc.nsp * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -284,7 +300,19 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
     if (ls && cr.gauge) Vg = (double *)ctx->Vg.get(std::max<long long>(1, 3 * M * N4) * sizeof(double));
     const long long Kfull = h_col[pc.nsp];
     const int mult = (ls && cr.gauge) ? 3 : 1;          // gauge rows/cols are (pair, I)
-    const size_t wbudget = (size_t)6 << 30;              // bytes of integral rows per batch
+    // one batch (and bra-ket symmetry) when all integral rows fit comfortably,
+    // else batches of at most 6 GB
+    size_t wall = 0;
+    {
+        long long kmax_all = 0;
+        for (int i = 0; i < pc.nsp; ++i) kmax_all = std::max(kmax_all, Krow_pair[i]);
+        wall = (size_t)M * mult * (size_t)std::max<long long>(kmax_all, 1) * mult * sizeof(double);
+    }
+    const bool one_batch = wall <= ((size_t)24 << 30);
+    const size_t wbudget = one_batch ? wall : ((size_t)6 << 30);
+    std::vector<int> h_kpos(pc.nsp);
+    for (int q = 0; q < pc.nsp; ++q) h_kpos[h_ketsp[q]] = q;
+    int *d_kpos = one_batch ? dcopy(ctx->kpos, h_kpos, s) : nullptr;
     int b0 = 0;
     double ms_eri = 0, ms_h1 = 0;
     while (b0 < pc.nsp) {
@@ -332,7 +360,10 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
         prm.with_coulomb = Wc ? 1 : 0;
         prm.Wc = Wc;
         prm.ldwc = ldwc;
-        launch_eri(prm, d_tk, (int)tk.size(), pc.maxnfp, pc.maxLab, s);
+        prm.sym = one_batch ? 1 : 0;
+        prm.ket_pos = d_kpos;
+        prm.prefix = prefix;
+        launch_eri(prm, d_tk, (int)tk.size(), pc.maxnfp, pc.maxLab, pc.maxnpp, s);
         ctx->launches += 2 + (Wc ? 1 : 0);
         if (st) {
             long long v = 0;
@@ -344,12 +375,11 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
                 v += (long long)ab.nfp * Krow_pair[sp];
                 // E R E contraction of every kept quartet: per primitive quartet
                 // 2 nha ncd nhc NC, per bra primitive pair 2 nab ncd nha NC.
-                const double nha = nherm(ab.Lab);
                 for (int q = 0; q < h_prefix[sp]; ++q) {
-                    const PairDev &cd = pc.h_pairs[h_ketsp[q]];
-                    const double ncd = cd.nfp, nhc = nherm(cd.Lab);
-                    fl += (double)ab.npp * cd.npp * 2.0 * nha * ncd * nhc * NC +
-                          (double)ab.npp * 2.0 * ab.nfp * ncd * nha * NC;
+                    const int cid = h_ketsp[q];
+                    const PairDev &cd = pc.h_pairs[cid];
+                    if (one_batch && cid < sp && h_kpos[sp] < h_prefix[cid]) continue;
+                    fl += 2.0 * NC * std::min(orient_cost_h(ab, cd), orient_cost_h(cd, ab));
                 }
             }
             st->eri_values += v * (prm.gauge ? 6 : 1);
@@ -548,6 +578,7 @@ int qdt_set_basis(qdt_ctx *c, int n_centers, const double *xyz, int n_shells, co
         cudaStream_t st = c->stream;
         dcopy(c->shells, c->h_shells, st);
         dcopy(c->exps, he, st);
+        c->h_exps = he;
         dcopy(c->coefs, hk, st);
         c->norms.get(std::max(1, noff) * sizeof(double));
         launch_shell_norms((const ShellDev *)c->shells.p, n_shells, (const double *)c->exps.p,

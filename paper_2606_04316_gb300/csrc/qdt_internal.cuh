@@ -45,7 +45,16 @@ struct Error {
             throw ::qdt::Error{QDT_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)}; \
     } while (0)
 
-#define QDT_CHECK_LAUNCH() QDT_CUDA_TRY(cudaGetLastError())
+#define QDT_STR2(x) #x
+#define QDT_STR(x) QDT_STR2(x)
+#define QDT_CHECK_LAUNCH() QDT_CHECK_KERNEL(__FILE__ ":" QDT_STR(__LINE__))
+// launch check naming the kernel
+#define QDT_CHECK_KERNEL(name)                                                         \
+    do {                                                                               \
+        cudaError_t _e = cudaGetLastError();                                           \
+        if (_e != cudaSuccess)                                                         \
+            throw ::qdt::Error{QDT_ERR_CUDA, std::string("launch of ") + (name) + ": " + cudaGetErrorString(_e)}; \
+    } while (0)
 
 inline void arg_check(bool ok, const std::string &m) {
     if (!ok) throw Error{QDT_ERR_ARG, m};
@@ -79,7 +88,12 @@ struct PrimPairDev {
     double p;
     double P[3];
     long long eoff; // offset of this primitive pair's E matrix [nfp][nherm(Lab)]
+    int ia, ib;     // primitives of the two shells
 };
+
+// Primitive pairs with exp(-a b / (a+b) |A-B|^2) below this are dropped at
+// set-up (their integrals are below 1e-24 of the pair's leading terms).
+constexpr double kPrimPairTol = 1e-24;
 
 // Host + device tables of one pair class.
 struct PairClass {
@@ -94,7 +108,7 @@ struct PairClass {
     double *d_Q = nullptr;
     int *d_bra_order = nullptr;
     long long npp_total = 0, e_total = 0;
-    int maxnfp = 0, maxLab = 0;
+    int maxnfp = 0, maxLab = 0, maxnpp = 0;
 };
 
 // ------------------------------------------------------------------ kernels
@@ -113,6 +127,11 @@ struct EriParams {
     int with_coulomb;           // gauge mode: also write the plain Coulomb block
     double *Wc;                 // gauge mode: Coulomb block output (may be null)
     long long ldwc;
+    // bra-ket symmetry (all rows in one batch): (CD|AB) is written from the
+    // (AB|CD) block when both survive; the task of the lower pair id computes it
+    int sym;
+    const int *ket_pos;         // sorted ket position of every pair id
+    const int *prefix;          // kept ket prefix length of every pair id
 };
 
 struct EriTask {                // one CTA: bra shell pair x range of ket positions
@@ -124,10 +143,10 @@ void launch_boys_table(double *d_tab, cudaStream_t s);
 void launch_shell_norms(const ShellDev *shells, int nL_shells, const double *exps,
                         const double *coefs, double *norms, cudaStream_t s);
 void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxnfp, int maxLab,
-                cudaStream_t s);
+                int maxnpp, cudaStream_t s);
 void launch_schwarz(const ShellDev *shells, const PairDev *pairs, const PrimPairDev *pp,
                     const double *E, const double *boys, int npairs, int maxnfp, int maxLab,
-                    double *Q, double *scratch, cudaStream_t s);
+                    int maxnpp, double *Q, cudaStream_t s);
 
 void launch_ket_order(const double *Q, const double *Dmax, int nsp, double *w, int *ket_sp,
                       cudaStream_t s);
