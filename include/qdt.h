@@ -158,6 +158,58 @@ int qdt_transform(qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end, double 
  */
 int qdt_unpack(qdt_ctx *ctx, const double *packed, int n_kramers, unsigned block, double *full);
 
+/* ------------------------------------------------------------------ serving
+ * A server runs transformation requests of different basis and active-space
+ * sizes on one GPU with continuous batching: `n_slots` contexts, each with its
+ * own stream, execute admitted requests concurrently (their kernels overlap on
+ * the device); a request waiting in the queue is admitted as soon as a slot is
+ * free and its estimated device footprint (qdt_footprint) fits in what is left
+ * of `pool_bytes`.  A slot keeps its basis tables resident and reuses them when
+ * the next request carries the same basis.  All pointers of a request are
+ * caller-owned and must stay valid until qdt_wait/qdt_poll reports it done.
+ */
+typedef struct qdt_server qdt_server;
+
+typedef struct {
+    int n_centers;                  /* basis, as for qdt_set_basis            */
+    const double *xyz;
+    int n_shells;
+    const int *shell_center, *shell_l, *shell_nprim;
+    const double *exps, *coefs;
+    int nK;                         /* coefficients, as qdt_set_coefficients  */
+    const double *CL, *CS;
+    unsigned blocks;                /* as qdt_transform                       */
+    int k_begin, k_end;
+    double schwarz_tau;
+    int precision;
+    double *out;                    /* host or device, qdt_packed_size bytes  */
+    size_t out_bytes;
+} qdt_request;
+
+/* Estimated peak device bytes of one request (integrals, densities, partial
+   results, split-form digit planes); used for admission. */
+size_t qdt_footprint(const qdt_request *req);
+
+/* Create a server on `device` with `n_slots` (1..16) concurrent contexts and a
+   device memory budget of `pool_bytes` (0: 80 % of the free memory). */
+int qdt_server_create(qdt_server **srv, int device, int n_slots, size_t pool_bytes);
+
+/* Finish queued and running requests, then release everything (NULL allowed). */
+void qdt_server_destroy(qdt_server *srv);
+
+/* Queue a request (copied; its arrays are not).  QDT_ERR_ADMISSION if its
+   footprint exceeds the whole pool; QDT_ERR_ARG on bad sizes. */
+int qdt_submit(qdt_server *srv, const qdt_request *req, uint64_t *handle);
+
+/* *done = 1 once the request has finished (successfully or not). */
+int qdt_poll(qdt_server *srv, uint64_t handle, int *done);
+
+/* Wait up to timeout_s seconds (< 0: forever).  Returns the request's own
+   status (QDT_OK or its error), or QDT_ERR_TIMEOUT.  latency_s (nullable)
+   receives completion minus submission time; stats (nullable) the call's
+   statistics.  A finished request's record is released by this call. */
+int qdt_wait(qdt_server *srv, uint64_t handle, double timeout_s, double *latency_s, qdt_stats *stats);
+
 /* Text of the last error of this context ("" if none); valid until the next call. */
 const char *qdt_last_error(const qdt_ctx *ctx);
 

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <vector>
 
 #include "split.cuh"
@@ -454,7 +455,23 @@ static void run_umma(SplitWorkspace &w, void *Asl, long long Mpad, long long Kpa
     dim3 grid((unsigned)(Npad / SBN), (unsigned)(Mpad / SBM));
     ozaki_umma_kernel<<<grid, 128, kSmemBytes, s>>>(ta, tb, Mpad, Npad, d_kt128, rowexp, colexp, C, ldc, M, N,
                                                     upper, status);
-    QDT_CHECK_KERNEL("ozaki_umma_kernel");
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) {
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, ozaki_umma_kernel);
+        int dev = 0, optin = 0, perblock = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&perblock, cudaDevAttrMaxSharedMemoryPerBlock, dev);
+        cudaGetLastError();
+        char msg[512];
+        snprintf(msg, sizeof msg,
+                 "launch of ozaki_umma_kernel: %s (grid %u x %u, dyn smem %d, static %zu, max dyn attr %d, "
+                 "regs %d, max threads %d, optin %d, per block %d, param %zu)",
+                 cudaGetErrorString(le), grid.x, grid.y, kSmemBytes, fa.sharedSizeBytes, fa.maxDynamicSharedSizeBytes,
+                 fa.numRegs, fa.maxThreadsPerBlock, optin, perblock, sizeof(CUtensorMap));
+        throw Error{QDT_ERR_CUDA, msg};
+    }
     int h = 0;
     QDT_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     QDT_CUDA_TRY(cudaStreamSynchronize(s));

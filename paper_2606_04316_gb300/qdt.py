@@ -20,7 +20,8 @@ ERRORS = {-1: "QDT_ERR_ARG", -2: "QDT_ERR_OOM", -3: "QDT_ERR_CUDA", -4: "QDT_ERR
           -5: "QDT_ERR_UNIMPLEMENTED", -6: "QDT_ERR_TIMEOUT", -7: "QDT_ERR_ADMISSION"}
 
 EXPORTS = ["qdt_create", "qdt_destroy", "qdt_set_basis", "qdt_num_functions", "qdt_set_coefficients",
-           "qdt_packed_size", "qdt_transform", "qdt_unpack", "qdt_last_error", "qdt_version"]
+           "qdt_packed_size", "qdt_transform", "qdt_unpack", "qdt_last_error", "qdt_version",
+           "qdt_footprint", "qdt_server_create", "qdt_server_destroy", "qdt_submit", "qdt_poll", "qdt_wait"]
 
 
 class QdtError(RuntimeError):
@@ -45,6 +46,15 @@ class Stats(ctypes.Structure):
             v = getattr(self, name)
             d[name] = list(v) if hasattr(v, "__len__") else v
         return d
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n_centers", ctypes.c_int), ("xyz", ctypes.c_void_p), ("n_shells", ctypes.c_int),
+                ("shell_center", ctypes.c_void_p), ("shell_l", ctypes.c_void_p), ("shell_nprim", ctypes.c_void_p),
+                ("exps", ctypes.c_void_p), ("coefs", ctypes.c_void_p), ("nK", ctypes.c_int),
+                ("CL", ctypes.c_void_p), ("CS", ctypes.c_void_p), ("blocks", ctypes.c_uint),
+                ("k_begin", ctypes.c_int), ("k_end", ctypes.c_int), ("schwarz_tau", ctypes.c_double),
+                ("precision", ctypes.c_int), ("out", ctypes.c_void_p), ("out_bytes", ctypes.c_size_t)]
 
 
 _LIB = None
@@ -80,6 +90,15 @@ def load(build_if_missing=True):
     L.qdt_last_error.argtypes = [vp]
     L.qdt_last_error.restype = ctypes.c_char_p
     L.qdt_version.restype = ctypes.c_char_p
+    L.qdt_footprint.argtypes = [ctypes.POINTER(Request)]
+    L.qdt_footprint.restype = ctypes.c_size_t
+    L.qdt_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_size_t]
+    L.qdt_server_destroy.argtypes = [vp]
+    L.qdt_server_destroy.restype = None
+    L.qdt_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.qdt_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
+    L.qdt_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(Stats)]
     _LIB = L
     return L
 
@@ -168,3 +187,71 @@ class Context:
 
 def version():
     return load().qdt_version().decode()
+
+
+class Server:
+    """Continuous-batching request server (qdt_server_*): n_slots concurrent
+    contexts on one GPU, admission by device-memory footprint."""
+
+    def __init__(self, device=0, n_slots=4, pool_bytes=0):
+        self.L = load()
+        h = ctypes.c_void_p()
+        rc = self.L.qdt_server_create(ctypes.byref(h), int(device), int(n_slots), int(pool_bytes))
+        if rc != 0:
+            raise QdtError(rc, "qdt_server_create failed")
+        self.h = h
+        self._keep = {}
+
+    def make_request(self, problem, blocks, k_begin, k_end, tau, precision, out, CL=None, CS=None):
+        b = problem.basis
+        arrs = [np.ascontiguousarray(b.xyz, np.float64), np.ascontiguousarray(b.shell_center, np.int32),
+                np.ascontiguousarray(b.shell_l, np.int32), np.ascontiguousarray(b.shell_nprim, np.int32),
+                np.ascontiguousarray(b.exps, np.float64), np.ascontiguousarray(b.coefs, np.float64),
+                np.ascontiguousarray(problem.CL if CL is None else CL, np.float64),
+                np.ascontiguousarray(problem.CS if CS is None else CS, np.float64)]
+        nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+        r = Request(int(arrs[0].shape[0]), _ptr(arrs[0]), int(arrs[1].shape[0]), _ptr(arrs[1]), _ptr(arrs[2]),
+                    _ptr(arrs[3]), _ptr(arrs[4]), _ptr(arrs[5]), int(arrs[6].shape[1]), _ptr(arrs[6]),
+                    _ptr(arrs[7]), blocks_mask(blocks), int(k_begin), int(k_end), float(tau), int(precision),
+                    _ptr(out), nbytes)
+        return r, arrs + [out]
+
+    def footprint(self, req):
+        return int(self.L.qdt_footprint(ctypes.byref(req)))
+
+    def submit(self, req, keep):
+        hd = ctypes.c_uint64()
+        rc = self.L.qdt_submit(self.h, ctypes.byref(req), ctypes.byref(hd))
+        if rc != 0:
+            raise QdtError(rc, "qdt_submit")
+        self._keep[hd.value] = (req, keep)
+        return hd.value
+
+    def poll(self, handle):
+        d = ctypes.c_int()
+        rc = self.L.qdt_poll(self.h, ctypes.c_uint64(handle), ctypes.byref(d))
+        if rc != 0:
+            raise QdtError(rc, "qdt_poll")
+        return bool(d.value)
+
+    def wait(self, handle, timeout=-1.0):
+        lat = ctypes.c_double()
+        st = Stats()
+        rc = self.L.qdt_wait(self.h, ctypes.c_uint64(handle), float(timeout), ctypes.byref(lat), ctypes.byref(st))
+        if rc == -6 and timeout >= 0:
+            raise TimeoutError("request %d still running" % handle)
+        self._keep.pop(handle, None)
+        if rc != 0:
+            raise QdtError(rc, "request %d failed" % handle)
+        return lat.value, st.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.qdt_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

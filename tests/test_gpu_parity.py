@@ -109,3 +109,40 @@ def test_split_form_tiny_config(oracle, torch_cuda):
     ref = oracle.Transform(p).packed("coulomb").reshape(-1)
     assert np.abs(got[0] - ref).max() <= TOL_SPLIT
     assert st["slices"] == 6
+
+
+@pytest.mark.slow
+def test_multi_tile_screened_chain_both_forms(oracle, torch_cuda):
+    """10-centre s+p chain, 6 Kramers pairs: ~8000 rows (63 row tiles of 128,
+    ragged tail), 84 columns, Schwarz threshold 1e-9 (screening active);
+    FP64 form <= 1e-12 and split form <= 1e-10 against the oracle."""
+    torch = torch_cuda
+    p = synth.chain_problem(10, 6, seed=303, shells=(0, 1), nprim=3, blocks=("coulomb",), tau=1e-9)
+    tr = oracle.Transform(p)
+    ref = tr.packed("coulomb").reshape(-1)
+    assert tr.mask("coulomb").mean() < 1.0
+    for prec, tol in ((0, TOL_FP64), (1, TOL_SPLIT)):
+        ctx, got, st = run_gpu(torch, p, ["coulomb"], 0, p.nK, p.tau, precision=prec)
+        assert np.abs(got[0] - ref).max() <= tol, (prec, np.abs(got[0] - ref).max())
+
+
+@pytest.mark.slow
+def test_full_size_chain40_properties(torch_cuda):
+    """The 40-centre chain at full size (the benchmark's workload): the split
+    form agrees with the FP64 form within 1e-10, and the Coulomb output, a
+    Gram matrix of a positive-definite kernel, is positive semidefinite."""
+    torch = torch_cuda
+    from oracle import oracle as O
+    p = synth.medium_dc()
+    _, f64, st64 = run_gpu(torch, p, ["coulomb"], 0, p.nK, p.tau, precision=0)
+    _, spl, stsp = run_gpu(torch, p, ["coulomb"], 0, p.nK, p.tau, precision=1)
+    assert st64["quartets_kept"] == stsp["quartets_kept"]
+    assert np.abs(f64 - spl).max() <= TOL_SPLIT
+    nP = p.nK * (p.nK + 1) // 2
+    full = np.zeros((nP, 4, nP, 4))
+    iu, ju = np.triu_indices(nP)
+    blk = f64[0].reshape(-1, 4, 4)
+    full[iu, :, ju, :] = blk
+    full[ju, :, iu, :] = blk.transpose(0, 2, 1)
+    w = np.linalg.eigvalsh(full.reshape(4 * nP, 4 * nP))
+    assert w.min() >= -1e-10 * w.max()
