@@ -172,7 +172,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chain40-sp")
     ap.add_argument("--blocks", default="coulomb")
-    ap.add_argument("--precision", default="fp64", choices=["split", "fp64"])
+    ap.add_argument("--precision", default="split", choices=["split", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 form (0: skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
@@ -252,6 +253,26 @@ def main():
                "h2d_bytes_per_step": int(CLh.numel() * 8 + CSh.numel() * 8),
                "d2h_bytes_per_step": int(outh.numel() * 8)}
 
+    # the FP64 form on the same workload, and the agreement of the two forms
+    other = None
+    if prec == qdt.SPLIT and args.fp64_steps > 0:
+        out64 = torch.zeros_like(out)
+        ctx.set_coefficients(CLd, CSd)
+        ctx.transform(blocks, 0, nK, tau, qdt.FP64, out64)
+        ctx.transform(blocks, 0, nK, tau, prec, out)
+        torch.cuda.synchronize()
+        diff = float((out - out64).abs().max().item())
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            st64 = ctx.transform(blocks, 0, nK, tau, qdt.FP64, out64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / args.fp64_steps
+        other = {"value": n_mo * world / (ms64 / 1e3), "ms_per_step": ms64, "steps": args.fp64_steps,
+                 "phases_ms": {k: st64[k] for k in phase}, "max_abs_diff_split_vs_fp64": diff}
+
     pk, src = peaks()
     avg = {k: v / args.steps for k, v in phase.items()}
     dom = max(("ms_eri", "ms_half1", "ms_half2"), key=lambda k: avg[k])
@@ -289,7 +310,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == qdt.FP64 else "bf16-slices/f64",
                 "data": "synthetic", "config": config_dict(args, problem, blocks), "clocks": clocks,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
-                "phases_ms": avg, "quartets_kept": st["quartets_kept"], "quartets_total": st["quartets_total"]}
+                "phases_ms": avg, "quartets_kept": st["quartets_kept"], "quartets_total": st["quartets_total"],
+                "fp64_form": other}
         print(json.dumps(line), flush=True)
         if args.stats:
             print(json.dumps(st), file=sys.stderr)

@@ -218,7 +218,10 @@ struct Timer {
     }
     double ms(int a, int b) {
         float t = 0.f;
-        if (a < n && b < n) cudaEventElapsedTime(&t, c->ev[a], c->ev[b]);
+        if (a < n && b < n && cudaEventElapsedTime(&t, c->ev[a], c->ev[b]) != cudaSuccess) {
+            cudaGetLastError();   // a timing failure must not surface as a later launch error
+            t = 0.f;
+        }
         return t;
     }
 };
@@ -628,6 +631,7 @@ int qdt_transform(qdt_ctx *c, unsigned blocks, int k_begin, int k_end, double ta
                   double *out, size_t out_bytes, qdt_stats *st) {
     if (!c) return QDT_ERR_ARG;
     try {
+        cudaGetLastError();      // start from a clean error state
         QDT_CUDA_TRY(cudaSetDevice(c->device));
         if (!c->has_basis || !c->has_coef) throw Error{QDT_ERR_STATE, "qdt_transform: basis or coefficients not set"};
         arg_check(blocks != 0 && (blocks & ~7u) == 0, "qdt_transform: blocks must be a non-empty subset of COULOMB|GAUNT|GAUGE");
