@@ -210,6 +210,37 @@ int qdt_poll(qdt_server *srv, uint64_t handle, int *done);
    statistics.  A finished request's record is released by this call. */
 int qdt_wait(qdt_server *srv, uint64_t handle, double timeout_s, double *latency_s, qdt_stats *stats);
 
+/* ------------------------------------------------------------ no allocation
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot allocate device memory -- a host framework that owns all device memory
+ * through its own pool allocator, or a latency-critical service that must not
+ * take the implicit synchronisation of a fresh cudaMalloc.  It computes the
+ * FP64 second-half contraction O = Dq^T V (Eq. secondhalf in real quaternion
+ * form) like qdt_transform does internally, but keeps its split-K partial sums
+ * in a fixed device array of the library (32 MiB of doubles, held on every GPU
+ * that loads the library until the process exits) and calls no allocator.
+ *
+ *   Dq, V  device pointers, [K][N] row-major doubles (rows: AO pairs, in any
+ *          order as long as both use the same; columns: Kramers-pair column x
+ *          quaternion part); K >= 0.
+ *   O      device pointer, [N][N] row-major; receives Dq^T V in every 64 x 64
+ *          tile on or above the diagonal (tile row <= tile column); entries of
+ *          the tiles below hold unspecified values.  Caller-owned.
+ *   N      1 <= N and N * N <= 4 * 2^20 (N <= 2048); larger N returns
+ *          QDT_ERR_ARG without launching anything.
+ *   cuda_stream  cudaStream_t to order the work on (NULL: legacy stream); the
+ *          call returns after queueing, without synchronising.
+ *   msg    optional buffer (msg_len bytes) for an error description.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (it must be the current device); make that first call before any
+ * stream capture.  Every call shares the one array: calls whose work overlaps
+ * on the GPU (different streams, or host threads) race and must be serialised
+ * by the caller.  Returns QDT_OK, QDT_ERR_ARG or QDT_ERR_CUDA.
+ */
+int qdt_second_half_noalloc(const double *Dq, const double *V, long long K, long long N, double *O,
+                            void *cuda_stream, char *msg, size_t msg_len);
+
 /* Text of the last error of this context ("" if none); valid until the next call. */
 const char *qdt_last_error(const qdt_ctx *ctx);
 

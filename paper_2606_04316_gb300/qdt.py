@@ -21,7 +21,8 @@ ERRORS = {-1: "QDT_ERR_ARG", -2: "QDT_ERR_OOM", -3: "QDT_ERR_CUDA", -4: "QDT_ERR
 
 EXPORTS = ["qdt_create", "qdt_destroy", "qdt_set_basis", "qdt_num_functions", "qdt_set_coefficients",
            "qdt_packed_size", "qdt_transform", "qdt_unpack", "qdt_last_error", "qdt_version",
-           "qdt_footprint", "qdt_server_create", "qdt_server_destroy", "qdt_submit", "qdt_poll", "qdt_wait"]
+           "qdt_footprint", "qdt_server_create", "qdt_server_destroy", "qdt_submit", "qdt_poll", "qdt_wait",
+           "qdt_second_half_noalloc"]
 
 
 class QdtError(RuntimeError):
@@ -99,6 +100,8 @@ def load(build_if_missing=True):
     L.qdt_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
     L.qdt_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(Stats)]
+    L.qdt_second_half_noalloc.argtypes = [vp, vp, ctypes.c_longlong, ctypes.c_longlong, vp, vp,
+                                          ctypes.c_char_p, ctypes.c_size_t]
     _LIB = L
     return L
 
@@ -255,3 +258,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def second_half_noalloc(Dq, V, O, stream=None):
+    """O = Dq^T V (FP64, upper 64x64 tiles) through qdt_second_half_noalloc:
+    no device allocation.  Dq, V: cuda float64 [K, N]; O: cuda float64 [N, N]."""
+    L = load()
+    buf = ctypes.create_string_buffer(512)
+    sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    rc = L.qdt_second_half_noalloc(_ptr(Dq), _ptr(V), int(Dq.shape[0]), int(Dq.shape[1]), _ptr(O), sp,
+                                   buf, 512)
+    if rc != 0:
+        raise QdtError(rc, buf.value.decode())
