@@ -171,6 +171,16 @@ class OracleBasis:
         # shell of every L function and every S function
         self.shell_of_L = np.repeat(np.arange(self.nsh), nc)
         self.shell_of_S = np.repeat(self.shell_of_L, 3)
+        # d/dr_K chi_i and d/dr_i chi_K of one p shell are the same function
+        # (delta_iK g - 2 a x_i x_K g): canonical S index of every S function
+        canon = np.arange(self.nS)
+        for s_ in range(self.nsh):
+            if int(basis.shell_l[s_]) == 1:
+                mu0 = int(self.Loff[s_])
+                for i in range(3):
+                    for K in range(3):
+                        canon[3 * (mu0 + i) + K] = 3 * (mu0 + min(i, K)) + max(i, K)
+        self.s_canonical = canon
         self._pairs = {}
 
     def __del__(self):
@@ -332,11 +342,27 @@ def schwarz_q(ob, cls):
 
 
 def density_max(ob, cls, Dq):
-    """Dmax per shell pair: max |entry| of the density rows of its pairs."""
-    _, _, sp = ob.pairs(cls)
-    row = np.abs(Dq.reshape(Dq.shape[0], -1)).max(axis=1) if Dq.size else np.zeros(Dq.shape[0])
+    """Dmax per shell pair: max |entry| of the density over the pair's distinct
+    functions.  Rows of identical derivative functions (d_K chi_i = d_i chi_K of
+    a p shell) are summed first, so the density is that of the actual basis
+    functions (Eq. SchwarzDen)."""
+    a, b, sp = ob.pairs(cls)
+    nL = ob.nL
+    X = Dq.reshape(Dq.shape[0], -1)
+    ca = np.where(a >= nL, nL + ob.s_canonical[np.clip(a - nL, 0, None)], a)
+    cb = np.where(b >= nL, nL + ob.s_canonical[np.clip(b - nL, 0, None)], b)
+    if cls == 0:
+        lo, hi = np.minimum(ca, cb), np.maximum(ca, cb)
+    else:
+        lo, hi = ca, cb
+    nF = nL + ob.nS
+    key = lo.astype(np.int64) * nF + hi
+    uk, inv = np.unique(key, return_inverse=True)
+    merged = np.zeros((uk.shape[0], X.shape[1]))
+    np.add.at(merged, inv, X)
+    kmax = np.abs(merged).max(axis=1) if X.size else np.zeros(uk.shape[0])
     Dm = np.zeros(ob.n_shell_pairs(cls))
-    np.maximum.at(Dm, sp, row)
+    np.maximum.at(Dm, sp, kmax[inv])
     return Dm
 
 

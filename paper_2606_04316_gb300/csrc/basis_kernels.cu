@@ -111,6 +111,23 @@ __device__ inline void func_terms(const ShellDev &sh, int f, double a, double d,
         t.w[0] = norms[sh.noff + f] * d;
         return;
     }
+    if (sh.red) {
+        // p shell: d/dr_K (x_i g) = delta_iK g - 2a x_i x_K g is symmetric in (i, K);
+        // function f is the pair i <= K in the order of the Cartesian d components
+        int pw2[3];
+        cart_triple(2, f, pw2[0], pw2[1], pw2[2]);
+        int i = pw2[0] ? 0 : (pw2[1] ? 1 : 2);           // first axis of the pair
+        double N = norms[sh.noff + i] * d;               // the three p components share N
+        t.pw[0][0] = pw2[0]; t.pw[0][1] = pw2[1]; t.pw[0][2] = pw2[2];
+        t.w[0] = -2.0 * a * N;
+        t.n = 1;
+        if (pw2[i] == 2) {                               // i == K: the delta_iK g term
+            t.pw[1][0] = t.pw[1][1] = t.pw[1][2] = 0;
+            t.w[1] = N;
+            t.n = 2;
+        }
+        return;
+    }
     // d/dr_K of N (x-A)^i.. e^{-a r^2} = N (i (x-A)^{i-1} - 2 a (x-A)^{i+1}) ..
     int c = f / 3, K = f % 3, pw[3];
     cart_triple(sh.l, c, pw[0], pw[1], pw[2]);
@@ -151,7 +168,8 @@ __device__ inline void htrip(int h, int &t, int &u, int &v) {
 }
 
 // One CTA per primitive pair: 1D tables in shared memory, then the E matrix
-// E[fp][h] over the pair's function pairs and Hermite functions h of order <= Lab.
+// E[h][fp] over the pair's Hermite functions h of order <= Lab and its
+// function pairs fp (function pairs contiguous, for coalesced reads).
 __global__ void prim_pair_kernel(const ShellDev *shells, const PairDev *pairs, const int *pp_pair,
                                  const double *exps, const double *coefs, const double *norms,
                                  PrimPairDev *pp, double *E) {
@@ -218,7 +236,7 @@ __global__ void prim_pair_kernel(const ShellDev *shells, const PairDev *pairs, c
                     s += ta.w[x] * tb.w[y] * Ex[0][pa[0]][pb[0]][t] * Ex[1][pa[1]][pb[1]][u] *
                          Ex[2][pa[2]][pb[2]][v];
                 }
-            Eo[(size_t)fp * nh + h] = s;
+            Eo[(size_t)h * pr.nfp + fp] = s;          // [h][fp]: function pairs contiguous
         }
     }
 }

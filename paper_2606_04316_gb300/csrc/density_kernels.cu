@@ -251,6 +251,23 @@ void launch_gather_rows(const double *src, const PairDev *pairs, const int *ket_
     QDT_CHECK_LAUNCH();
 }
 
+__global__ void merge_rows_kernel(const double *in, const int *m0, const int *m1, int nrows, int rowlen,
+                                  double *out) {
+    int r = blockIdx.x;
+    if (r >= nrows) return;
+    const double *a = in + (size_t)m0[r] * rowlen;
+    const double *b = m1[r] >= 0 ? in + (size_t)m1[r] * rowlen : nullptr;
+    double *o = out + (size_t)r * rowlen;
+    for (int i = threadIdx.x; i < rowlen; i += blockDim.x) o[i] = b ? a[i] + b[i] : a[i];
+}
+
+void launch_merge_rows(const double *in, const int *m0, const int *m1, int nrows, int rowlen, double *out,
+                       cudaStream_t s) {
+    if (nrows <= 0) return;
+    merge_rows_kernel<<<nrows, 128, 0, s>>>(in, m0, m1, nrows, rowlen, out);
+    QDT_CHECK_LAUNCH();
+}
+
 __global__ void zero_kernel(double *p, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)

@@ -153,7 +153,7 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
                         else if (t > 0) r = (t > 1 ? (t - 1) * s[hidx(t - 2, u, v)] : 0.0) + Xq * s[hidx(t - 1, u, v)];
                         else if (u > 0) r = (u > 1 ? (u - 1) * s[hidx(t, u - 2, v)] : 0.0) + Yq * s[hidx(t, u - 1, v)];
                         else r = (v > 1 ? (v - 1) * s[hidx(t, u, v - 2)] : 0.0) + Zq * s[hidx(t, u, v - 1)];
-                        d[h] = r;
+                        d[h] = (n == 0 && ((t + u + v) & 1)) ? -r : r;   // level 0 keeps (-1)^|k| R_k
                     }
                     if (GAUGE && h < cntR) {
                         double *d = b.RR + ((size_t)(n & 1) * pl.klg + g) * nrR;
@@ -164,23 +164,24 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
                         else if (t > 0) r = (t > 1 ? (t - 1) * s[hidx(t - 2, u, v)] : 0.0) + Xq * s[hidx(t - 1, u, v)];
                         else if (u > 0) r = (u > 1 ? (u - 1) * s[hidx(t, u - 2, v)] : 0.0) + Yq * s[hidx(t, u - 1, v)];
                         else r = (v > 1 ? (v - 1) * s[hidx(t, u, v - 2)] : 0.0) + Zq * s[hidx(t, u, v - 1)];
-                        d[h] = r;
+                        d[h] = (n == 0 && ((t + u + v) & 1)) ? -r : r;
                     }
                 }
                 __syncthreads();
             }
             // T[c][h][y] += sum_{kl in group} sum_h' R[h+h'] (-1)^|h'| E^{kl}[y][h']
+            //            = (-1)^|h| sum_h' Rs[h+h'] E^{kl}[y][h'],  Rs_k = (-1)^|k| R_k
             for (int idx = tid; idx < nhx * ych; idx += nt) {
                 const int h = idx / ych, yy = idx - h * ych;
                 const int t = b.trX[3 * h], u = b.trX[3 * h + 1], v = b.trX[3 * h + 2];
                 double sc0 = 0.0, sr[6] = {0, 0, 0, 0, 0, 0};
                 for (int g = 0; g < ng; ++g) {
-                    const double *e = E + pp[Y.ppoff + g0 + g].eoff + (size_t)(y0 + yy) * nhy;
+                    const double *e = E + pp[Y.ppoff + g0 + g].eoff + (y0 + yy);   // E[h'][y], stride nfp
                     const double *RC0 = b.RC + (size_t)g * nrC;
                     const double *RR0 = b.RR + (size_t)g * nrR;
                     for (int hp = 0; hp < nhy; ++hp) {
                         const int tp = b.trY[3 * hp], up = b.trY[3 * hp + 1], vp = b.trY[3 * hp + 2];
-                        const double ev = ((tp + up + vp) & 1) ? -__ldg(e + hp) : __ldg(e + hp);
+                        const double ev = __ldg(e + (size_t)hp * Y.nfp);
                         const int T0 = t + tp, U0 = u + up, V0 = v + vp;
                         sc0 = fma(RC0[hidx(T0, U0, V0)], ev, sc0);
                         if (GAUGE) {
@@ -193,9 +194,10 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
                         }
                     }
                 }
-                b.T[(size_t)h * ych + yy] += sc0;
+                const bool odd = (t + u + v) & 1;
+                b.T[(size_t)h * ych + yy] += odd ? -sc0 : sc0;
                 if (GAUGE)
-                    for (int k = 0; k < 6; ++k) b.T[((size_t)(k + 1) * nhx + h) * ych + yy] += sr[k];
+                    for (int k = 0; k < 6; ++k) b.T[((size_t)(k + 1) * nhx + h) * ych + yy] += odd ? -sr[k] : sr[k];
             }
             __syncthreads();
         }
@@ -203,12 +205,12 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
         const double *Eij = E + pa.eoff;
         for (int idx = tid; idx < xch * ych; idx += nt) {
             const int xx = idx / ych, yy = idx - xx * ych;
-            const double *e = Eij + (size_t)(x0 + xx) * nhx;
+            const double *e = Eij + (x0 + xx);                                 // E[h][x], stride nfp
             double s[NC];
 #pragma unroll
             for (int k = 0; k < NC; ++k) s[k] = 0.0;
             for (int h = 0; h < nhx; ++h) {
-                const double ev = __ldg(e + h);
+                const double ev = __ldg(e + (size_t)h * X.nfp);
 #pragma unroll
                 for (int k = 0; k < NC; ++k) s[k] = fma(ev, b.T[((size_t)k * nhx + h) * ych + yy], s[k]);
             }
@@ -308,12 +310,15 @@ void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxn
     if (ntasks <= 0) return;
     size_t smem;
     Plan pl = eri_plan(maxnfp, maxLab, maxnpp, prm.gauge != 0, &smem);
+    // small plans run as 128-thread CTAs, four per SM, so that a CTA waiting at
+    // a recursion barrier leaves the FP64 pipe to the others
+    const int threads = smem <= 56 * 1024 ? 128 : 256;
     if (prm.gauge) {
         QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        eri_rows_kernel<true><<<ntasks, 256, smem, s>>>(prm, tasks, pl);
+        eri_rows_kernel<true><<<ntasks, threads, smem, s>>>(prm, tasks, pl);
     } else {
         QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        eri_rows_kernel<false><<<ntasks, 256, smem, s>>>(prm, tasks, pl);
+        eri_rows_kernel<false><<<ntasks, threads, smem, s>>>(prm, tasks, pl);
     }
     QDT_CHECK_LAUNCH();
 }

@@ -70,6 +70,12 @@ void split_release(SplitWorkspace &w) {
 
 int split_slices(const SplitWorkspace &w) { return w.slices; }
 
+size_t split_held_bytes(const SplitWorkspace &w) {
+    size_t b = 0;
+    for (int i = 0; i < 8; ++i) b += w.bytes[i];
+    return b;
+}
+
 void split_invalidate(SplitWorkspace &w) { w.bkey[0] = w.bkey[1] = SplitKey(); }
 
 static inline long long rup(long long x, long long m) { return (x + m - 1) / m * m; }

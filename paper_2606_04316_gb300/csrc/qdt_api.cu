@@ -86,10 +86,11 @@ struct qdt_ctx {
     DBuf shells, exps, coefs, norms, boys;
     PairClass cls[2];
     ClassBufs cb[2];
-    // coefficients
+    // coefficients (internal rows: L functions, then the distinct derivative functions)
     bool has_coef = false;
     int nK = 0;
-    DBuf Cq;
+    DBuf Cq, Craw, dsmap0, dsmap1;
+    std::vector<int> smap0, smap1;
     // per-transform workspace
     DBuf Dbra, Dket, V, Vg, W, Wc, Dmax, wsort, ketsp, ketcol, prefix, ktile, tasks, O, partial,
         stage, rsR, rsS, kpos;
@@ -311,7 +312,13 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
         for (int i = 0; i < pc.nsp; ++i) kmax_all = std::max(kmax_all, Krow_pair[i]);
         wall = (size_t)M * mult * (size_t)std::max<long long>(kmax_all, 1) * mult * sizeof(double);
     }
-    const bool one_batch = wall <= ((size_t)24 << 30);
+    // all rows at once (bra-ket symmetry) when the integral block and its digit
+    // planes fit in 70 % of the device memory this context can use
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
+    const size_t usable = (size_t)(0.7 * (double)(fr + ctx->W.n + ctx->Wc.n + split_held_bytes(ctx->split)));
+    const double wfac = (precision == QDT_SPLIT ? 2.5 : 1.0) * ((ls && cr.gauge && cr.gaunt) ? 1.12 : 1.0);
+    const bool one_batch = (double)wall * wfac <= (double)usable;
     const size_t wbudget = one_batch ? wall : ((size_t)6 << 30);
     std::vector<int> h_kpos(pc.nsp);
     for (int q = 0; q < pc.nsp; ++q) h_kpos[h_ketsp[q]] = q;
@@ -517,7 +524,8 @@ void qdt_destroy(qdt_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    DBuf *bufs[] = {&c->shells, &c->exps, &c->coefs, &c->norms, &c->boys, &c->Cq, &c->Dbra, &c->Dket,
+    DBuf *bufs[] = {&c->shells, &c->exps, &c->coefs, &c->norms, &c->boys, &c->Cq, &c->Craw, &c->dsmap0,
+                    &c->dsmap1, &c->Dbra, &c->Dket,
                     &c->V, &c->Vg, &c->W, &c->Wc, &c->Dmax, &c->wsort, &c->ketsp, &c->ketcol,
                     &c->prefix, &c->ktile, &c->tasks, &c->O, &c->partial, &c->stage, &c->rsR, &c->rsS};
     for (DBuf *b : bufs) b->release();
@@ -572,12 +580,33 @@ int qdt_set_basis(qdt_ctx *c, int n_centers, const double *xyz, int n_shells, co
             c->h_shells.push_back(sh);
             foff += sh.nfunc; poff += hn[s]; noff += sh.nfunc;
         }
-        c->nL = foff; c->nS = 3 * foff; c->nshL = n_shells;
+        c->nL = foff; c->nshL = n_shells;
+        // derivative shells; those of p shells keep the 6 distinct functions
+        // d_K chi_i = d_i chi_K (i <= K), whose coefficient rows are merged
+        c->smap0.clear(); c->smap1.clear();
+        int soff = 0;
         for (int s = 0; s < n_shells; ++s) {
             ShellDev sh = c->h_shells[s];
-            sh.isS = 1; sh.nfunc = 3 * lcart(sh.l); sh.foff = c->nL + 3 * sh.foff;
+            sh.isS = 1;
+            sh.red = (sh.l == 1) ? 1 : 0;
+            sh.nfunc = sh.red ? 6 : 3 * lcart(sh.l);
+            const int mu0 = sh.foff;                       // first L function of the parent
+            sh.foff = c->nL + soff;
+            if (sh.red) {
+                const int pi[6] = {0, 0, 0, 1, 1, 2}, pk[6] = {0, 1, 2, 1, 2, 2};
+                for (int f = 0; f < 6; ++f) {
+                    c->smap0.push_back(3 * (mu0 + pi[f]) + pk[f]);
+                    c->smap1.push_back(pi[f] == pk[f] ? -1 : 3 * (mu0 + pk[f]) + pi[f]);
+                }
+            } else {
+                for (int f = 0; f < sh.nfunc; ++f) { c->smap0.push_back(3 * mu0 + f); c->smap1.push_back(-1); }
+            }
+            soff += sh.nfunc;
             c->h_shells.push_back(sh);
         }
+        c->nS = soff;
+        dcopy(c->dsmap0, c->smap0, c->stream);
+        dcopy(c->dsmap1, c->smap1, c->stream);
         cudaStream_t st = c->stream;
         dcopy(c->shells, c->h_shells, st);
         dcopy(c->exps, he, st);
@@ -605,10 +634,13 @@ int qdt_set_coefficients(qdt_ctx *c, int nK, const double *CL, const double *CS)
         QDT_CUDA_TRY(cudaSetDevice(c->device));
         if (!c->has_basis) throw Error{QDT_ERR_STATE, "qdt_set_coefficients: no basis"};
         arg_check(nK > 0 && CL && CS, "qdt_set_coefficients: nK must be positive");
-        size_t nl = (size_t)c->nL * nK * 4, ns = (size_t)c->nS * nK * 4;
+        // CL as given; CS (3 nL rows) merged onto the internal derivative functions
+        size_t nl = (size_t)c->nL * nK * 4, ns_in = (size_t)3 * c->nL * nK * 4, ns = (size_t)c->nS * nK * 4;
         double *d = (double *)c->Cq.get((nl + ns) * sizeof(double));
+        double *raw = (double *)c->Craw.get(ns_in * sizeof(double));
         QDT_CUDA_TRY(cudaMemcpyAsync(d, CL, nl * sizeof(double), cudaMemcpyDefault, c->stream));
-        QDT_CUDA_TRY(cudaMemcpyAsync(d + nl, CS, ns * sizeof(double), cudaMemcpyDefault, c->stream));
+        QDT_CUDA_TRY(cudaMemcpyAsync(raw, CS, ns_in * sizeof(double), cudaMemcpyDefault, c->stream));
+        launch_merge_rows(raw, (const int *)c->dsmap0.p, (const int *)c->dsmap1.p, c->nS, nK * 4, d + nl, c->stream);
         QDT_CUDA_TRY(cudaStreamSynchronize(c->stream));
         c->nK = nK;
         c->has_coef = true;

@@ -71,6 +71,7 @@ struct ShellDev {
     int nprim;
     int poff;       // first primitive in the exponent/coefficient arrays
     int noff;       // first normalisation constant (per Cartesian component)
+    int red;        // derivative shell of a p shell kept as its 6 distinct functions
 };
 
 // Shell pair of a class.  Class 0 (Coulomb): LL pairs A<=B then SS pairs A<=B;
@@ -87,7 +88,7 @@ struct PairDev {
 struct PrimPairDev {
     double p;
     double P[3];
-    long long eoff; // offset of this primitive pair's E matrix [nfp][nherm(Lab)]
+    long long eoff; // offset of this primitive pair's E matrix [nherm(Lab)][nfp]
     int ia, ib;     // primitives of the two shells
 };
 
@@ -171,5 +172,8 @@ int gemm_fp64_tile_m();
 void launch_pack(const double *O, long long ldo, int nKa, double *out, cudaStream_t s);
 void launch_unpack(const double *packed, int nKa, int gaunt_like, double *full, cudaStream_t s);
 void launch_zero(double *p, long long n, cudaStream_t s);
+// coefficient rows of the internal small-component basis: row r = in[m0[r]] (+ in[m1[r]])
+void launch_merge_rows(const double *in, const int *m0, const int *m1, int nrows, int rowlen, double *out,
+                       cudaStream_t s);
 
 }  // namespace qdt

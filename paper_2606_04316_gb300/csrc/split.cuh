@@ -24,6 +24,8 @@ struct SplitWorkspace {
 
 void split_release(SplitWorkspace &w);
 int split_slices(const SplitWorkspace &w);
+// Device bytes currently held by the workspace.
+size_t split_held_bytes(const SplitWorkspace &w);
 // Drop cached operand slices (call whenever the densities change).
 void split_invalidate(SplitWorkspace &w);
 
