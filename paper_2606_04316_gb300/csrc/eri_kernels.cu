@@ -171,51 +171,72 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
             }
             // T[c][h][y] += sum_{kl in group} sum_h' R[h+h'] (-1)^|h'| E^{kl}[y][h']
             //            = (-1)^|h| sum_h' Rs[h+h'] E^{kl}[y][h'],  Rs_k = (-1)^|k| R_k
-            for (int idx = tid; idx < nhx * ych; idx += nt) {
-                const int h = idx / ych, yy = idx - h * ych;
+            // two output columns per thread: one R load feeds two FMAs
+            const int ych2 = (ych + 1) >> 1;
+            for (int idx = tid; idx < nhx * ych2; idx += nt) {
+                const int h = idx / ych2, y1 = idx - h * ych2, y2 = y1 + ych2;
+                const bool two = y2 < ych;
                 const int t = b.trX[3 * h], u = b.trX[3 * h + 1], v = b.trX[3 * h + 2];
-                double sc0 = 0.0, sr[6] = {0, 0, 0, 0, 0, 0};
+                double sc1 = 0.0, sc2 = 0.0, sr1[6] = {0, 0, 0, 0, 0, 0}, sr2[6] = {0, 0, 0, 0, 0, 0};
                 for (int g = 0; g < ng; ++g) {
-                    const double *e = E + pp[Y.ppoff + g0 + g].eoff + (y0 + yy);   // E[h'][y], stride nfp
+                    const double *e = E + pp[Y.ppoff + g0 + g].eoff + (y0 + y1);   // E[h'][y], stride nfp
                     const double *RC0 = b.RC + (size_t)g * nrC;
                     const double *RR0 = b.RR + (size_t)g * nrR;
                     for (int hp = 0; hp < nhy; ++hp) {
                         const int tp = b.trY[3 * hp], up = b.trY[3 * hp + 1], vp = b.trY[3 * hp + 2];
-                        const double ev = __ldg(e + (size_t)hp * Y.nfp);
+                        const double e1 = __ldg(e + (size_t)hp * Y.nfp);
+                        const double e2 = two ? __ldg(e + (size_t)hp * Y.nfp + ych2) : 0.0;
                         const int T0 = t + tp, U0 = u + up, V0 = v + vp;
-                        sc0 = fma(RC0[hidx(T0, U0, V0)], ev, sc0);
+                        const double rc = RC0[hidx(T0, U0, V0)];
+                        sc1 = fma(rc, e1, sc1);
+                        sc2 = fma(rc, e2, sc2);
                         if (GAUGE) {
-                            sr[0] = fma(RR0[hidx(T0 + 2, U0, V0)], ev, sr[0]);
-                            sr[1] = fma(RR0[hidx(T0 + 1, U0 + 1, V0)], ev, sr[1]);
-                            sr[2] = fma(RR0[hidx(T0 + 1, U0, V0 + 1)], ev, sr[2]);
-                            sr[3] = fma(RR0[hidx(T0, U0 + 2, V0)], ev, sr[3]);
-                            sr[4] = fma(RR0[hidx(T0, U0 + 1, V0 + 1)], ev, sr[4]);
-                            sr[5] = fma(RR0[hidx(T0, U0, V0 + 2)], ev, sr[5]);
+                            const double r[6] = {RR0[hidx(T0 + 2, U0, V0)], RR0[hidx(T0 + 1, U0 + 1, V0)],
+                                                 RR0[hidx(T0 + 1, U0, V0 + 1)], RR0[hidx(T0, U0 + 2, V0)],
+                                                 RR0[hidx(T0, U0 + 1, V0 + 1)], RR0[hidx(T0, U0, V0 + 2)]};
+#pragma unroll
+                            for (int k = 0; k < 6; ++k) {
+                                sr1[k] = fma(r[k], e1, sr1[k]);
+                                sr2[k] = fma(r[k], e2, sr2[k]);
+                            }
                         }
                     }
                 }
                 const bool odd = (t + u + v) & 1;
-                b.T[(size_t)h * ych + yy] += odd ? -sc0 : sc0;
+                b.T[(size_t)h * ych + y1] += odd ? -sc1 : sc1;
+                if (two) b.T[(size_t)h * ych + y2] += odd ? -sc2 : sc2;
                 if (GAUGE)
-                    for (int k = 0; k < 6; ++k) b.T[((size_t)(k + 1) * nhx + h) * ych + yy] += odd ? -sr[k] : sr[k];
+                    for (int k = 0; k < 6; ++k) {
+                        b.T[((size_t)(k + 1) * nhx + h) * ych + y1] += odd ? -sr1[k] : sr1[k];
+                        if (two) b.T[((size_t)(k + 1) * nhx + h) * ych + y2] += odd ? -sr2[k] : sr2[k];
+                    }
             }
             __syncthreads();
         }
-        // G[c][x][y] += sum_h E^{ij}[x][h] T[c][h][y]
+        // G[c][x][y] += sum_h E^{ij}[x][h] T[c][h][y], two columns per thread
         const double *Eij = E + pa.eoff;
-        for (int idx = tid; idx < xch * ych; idx += nt) {
-            const int xx = idx / ych, yy = idx - xx * ych;
+        const int ych2 = (ych + 1) >> 1;
+        for (int idx = tid; idx < xch * ych2; idx += nt) {
+            const int xx = idx / ych2, y1 = idx - xx * ych2, y2 = y1 + ych2;
+            const bool two = y2 < ych;
             const double *e = Eij + (x0 + xx);                                 // E[h][x], stride nfp
-            double s[NC];
+            double s1[NC], s2[NC];
 #pragma unroll
-            for (int k = 0; k < NC; ++k) s[k] = 0.0;
+            for (int k = 0; k < NC; ++k) s1[k] = s2[k] = 0.0;
             for (int h = 0; h < nhx; ++h) {
                 const double ev = __ldg(e + (size_t)h * X.nfp);
 #pragma unroll
-                for (int k = 0; k < NC; ++k) s[k] = fma(ev, b.T[((size_t)k * nhx + h) * ych + yy], s[k]);
+                for (int k = 0; k < NC; ++k) {
+                    const double *Tk = b.T + ((size_t)k * nhx + h) * ych;
+                    s1[k] = fma(ev, Tk[y1], s1[k]);
+                    if (two) s2[k] = fma(ev, Tk[y2], s2[k]);
+                }
             }
 #pragma unroll
-            for (int k = 0; k < NC; ++k) b.G[((size_t)k * xch + xx) * ych + yy] += s[k];
+            for (int k = 0; k < NC; ++k) {
+                b.G[((size_t)k * xch + xx) * ych + y1] += s1[k];
+                if (two) b.G[((size_t)k * xch + xx) * ych + y2] += s2[k];
+            }
         }
         __syncthreads();
     }
