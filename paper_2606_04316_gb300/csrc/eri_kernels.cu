@@ -242,15 +242,177 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
     }
 }
 
-// Screened rows: one CTA per task (bra shell pair x range of sorted ket positions).
+// ------------------------------------------------------------------ warp engine
+// Each warp owns whole shell quartets: its phases synchronise with __syncwarp
+// only, so a warp in the Hermite recursion never waits for another warp.
+constexpr int kWGroup = 16;   // primitive quartets whose Boys values a warp evaluates at once
+
+struct WPlan {
+    int NC, ach, cch, nhMax, LtC, LtR;
+    int nwarps;           // warps per CTA
+    int warp_doubles;     // shared doubles per warp
+};
+
+__host__ __device__ inline int wplan_doubles(int NC, int ach, int cch, int nhMax, int LtC, int LtR) {
+    int nrC = nherm(LtC), nrR = LtR >= 0 ? nherm(LtR) : 0;
+    return NC * ach * cch + NC * nhMax * cch + 2 * nrC + 2 * nrR + kWGroup * (kBoysNMax + 3) + kWGroup * 8 +
+           (3 * nhMax * 2 + 1) / 2 + 2;
+}
+
+struct WSmem {
+    double *G, *T, *RC, *RR, *F, *sc;
+    int *trX, *trY;
+};
+
+__device__ inline WSmem wcarve(double *sm, const WPlan &p) {
+    WSmem b;
+    int nrC = nherm(p.LtC), nrR = p.LtR >= 0 ? nherm(p.LtR) : 0;
+    b.G = sm; sm += p.NC * p.ach * p.cch;
+    b.T = sm; sm += p.NC * p.nhMax * p.cch;
+    b.RC = sm; sm += 2 * nrC;
+    b.RR = sm; sm += 2 * nrR;
+    b.F = sm; sm += kWGroup * (kBoysNMax + 3);
+    b.sc = sm; sm += kWGroup * 8;
+    b.trX = (int *)sm;
+    b.trY = b.trX + 3 * p.nhMax;
+    return b;
+}
+
+// One chunk of the block (X|Y) by one warp; results in b.G[comp][x][y].
 template <bool GAUGE>
-__global__ void __launch_bounds__(256) eri_rows_kernel(EriParams prm, const EriTask *tasks, Plan pl) {
+__device__ void warp_chunk(const PrimPairDev *pp, const double *E, const double *boys, const PairDev &X,
+                           const PairDev &Y, int x0, int x1, int y0, int y1, const WPlan &pl, WSmem &b) {
+    constexpr int NC = GAUGE ? 7 : 1;
+    const int lane = threadIdx.x & 31;
+    const int Lx = X.Lab, Ly = Y.Lab;
+    const int nhx = nherm(Lx), nhy = nherm(Ly);
+    const int L = Lx + Ly, Lr = L + 2, Ltop = GAUGE ? Lr : L;
+    const int xch = x1 - x0, ych = y1 - y0;
+    for (int h = lane; h < nhx; h += 32) htrip_d(h, b.trX[3 * h], b.trX[3 * h + 1], b.trX[3 * h + 2]);
+    for (int h = lane; h < nhy; h += 32) htrip_d(h, b.trY[3 * h], b.trY[3 * h + 1], b.trY[3 * h + 2]);
+    for (int i = lane; i < NC * xch * ych; i += 32) b.G[i] = 0.0;
+    __syncwarp();
+    for (int ij = 0; ij < X.npp; ++ij) {
+        const PrimPairDev pa = pp[X.ppoff + ij];
+        for (int i = lane; i < NC * nhx * ych; i += 32) b.T[i] = 0.0;
+        for (int g0 = 0; g0 < Y.npp; g0 += kWGroup) {
+            const int ng = min(kWGroup, Y.npp - g0);
+            // Boys values of up to kWGroup primitive quartets, one per lane
+            if (lane < ng) {
+                const PrimPairDev pc = pp[Y.ppoff + g0 + lane];
+                double p = pa.p, q = pc.p, rho = p * q / (p + q);
+                double Xq = pa.P[0] - pc.P[0], Yq = pa.P[1] - pc.P[1], Zq = pa.P[2] - pc.P[2];
+                double Tv = rho * (Xq * Xq + Yq * Yq + Zq * Zq);
+                double *F = b.F + lane * (kBoysNMax + 3);
+                boys_eval(boys, Tv, Ltop, F + 1);
+                F[0] = -(2.0 * Tv * F[1] + exp(-Tv));
+                double *sc = b.sc + lane * 8;
+                sc[0] = Xq; sc[1] = Yq; sc[2] = Zq; sc[3] = -2.0 * rho;
+                double pw = 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p + q));
+                sc[4] = pw;
+                sc[5] = pow(M_PI, 2.5) * sqrt(p + q) / (p * p * q * q);
+            }
+            __syncwarp();
+            for (int g = 0; g < ng; ++g) {
+                const double *sc = b.sc + g * 8;
+                const double *F = b.F + g * (kBoysNMax + 3);
+                const double Xq = sc[0], Yq = sc[1], Zq = sc[2], m2r = sc[3];
+                const int nrC = nherm(pl.LtC), nrR = GAUGE ? nherm(pl.LtR) : 0;
+                for (int n = Ltop; n >= 0; --n) {
+                    const int cntC = (n <= L) ? nherm(L - n) : 0;
+                    const int cntR = GAUGE ? nherm(Lr - n) : 0;
+                    const int cnt = cntR > cntC ? cntR : cntC;
+                    double *dC = b.RC + (n & 1) * nrC, *sC = b.RC + ((n + 1) & 1) * nrC;
+                    double *dR = b.RR + (n & 1) * nrR, *sR = b.RR + ((n + 1) & 1) * nrR;
+                    for (int h = lane; h < cnt; h += 32) {
+                        int t, u, v;
+                        htrip_d(h, t, u, v);
+                        const bool flip = (n == 0) && ((t + u + v) & 1);   // level 0 keeps (-1)^|k| R_k
+                        if (h < cntC) {
+                            double r;
+                            if (h == 0) {
+                                double mp = 1.0;                 // (-2 rho)^n
+                                for (int k = 0; k < n; ++k) mp *= m2r;
+                                r = mp * F[n + 1] * sc[4];
+                            }
+                            else if (t > 0) r = (t > 1 ? (t - 1) * sC[hidx(t - 2, u, v)] : 0.0) + Xq * sC[hidx(t - 1, u, v)];
+                            else if (u > 0) r = (u > 1 ? (u - 1) * sC[hidx(t, u - 2, v)] : 0.0) + Yq * sC[hidx(t, u - 1, v)];
+                            else r = (v > 1 ? (v - 1) * sC[hidx(t, u, v - 2)] : 0.0) + Zq * sC[hidx(t, u, v - 1)];
+                            dC[h] = flip ? -r : r;
+                        }
+                        if (GAUGE && h < cntR) {
+                            double r;
+                            if (h == 0) {
+                                double mp = 1.0;
+                                for (int k = 0; k < n; ++k) mp *= m2r;
+                                r = mp * (F[n + 1] - F[n]) * sc[5];
+                            }
+                            else if (t > 0) r = (t > 1 ? (t - 1) * sR[hidx(t - 2, u, v)] : 0.0) + Xq * sR[hidx(t - 1, u, v)];
+                            else if (u > 0) r = (u > 1 ? (u - 1) * sR[hidx(t, u - 2, v)] : 0.0) + Yq * sR[hidx(t, u - 1, v)];
+                            else r = (v > 1 ? (v - 1) * sR[hidx(t, u, v - 2)] : 0.0) + Zq * sR[hidx(t, u, v - 1)];
+                            dR[h] = flip ? -r : r;
+                        }
+                    }
+                    __syncwarp();
+                }
+                // T[c][h][y] += (-1)^|h| sum_h' Rs[h+h'] E^{kl}[h'][y]
+                const double *e = E + pp[Y.ppoff + g0 + g].eoff + y0;
+                const double *RC0 = b.RC, *RR0 = b.RR;
+                for (int idx = lane; idx < nhx * ych; idx += 32) {
+                    const int h = idx / ych, yy = idx - h * ych;
+                    const int t = b.trX[3 * h], u = b.trX[3 * h + 1], v = b.trX[3 * h + 2];
+                    double s0 = 0.0, s6[6] = {0, 0, 0, 0, 0, 0};
+                    for (int hp = 0; hp < nhy; ++hp) {
+                        const int T0 = t + b.trY[3 * hp], U0 = u + b.trY[3 * hp + 1], V0 = v + b.trY[3 * hp + 2];
+                        const double ev = __ldg(e + (size_t)hp * Y.nfp + yy);
+                        s0 = fma(RC0[hidx(T0, U0, V0)], ev, s0);
+                        if (GAUGE) {
+                            s6[0] = fma(RR0[hidx(T0 + 2, U0, V0)], ev, s6[0]);
+                            s6[1] = fma(RR0[hidx(T0 + 1, U0 + 1, V0)], ev, s6[1]);
+                            s6[2] = fma(RR0[hidx(T0 + 1, U0, V0 + 1)], ev, s6[2]);
+                            s6[3] = fma(RR0[hidx(T0, U0 + 2, V0)], ev, s6[3]);
+                            s6[4] = fma(RR0[hidx(T0, U0 + 1, V0 + 1)], ev, s6[4]);
+                            s6[5] = fma(RR0[hidx(T0, U0, V0 + 2)], ev, s6[5]);
+                        }
+                    }
+                    const bool odd = (t + u + v) & 1;
+                    b.T[(size_t)h * ych + yy] += odd ? -s0 : s0;
+                    if (GAUGE)
+                        for (int k = 0; k < 6; ++k) b.T[((size_t)(k + 1) * nhx + h) * ych + yy] += odd ? -s6[k] : s6[k];
+                }
+                __syncwarp();
+            }
+        }
+        // G[c][x][y] += sum_h E^{ij}[h][x] T[c][h][y]
+        const double *Eij = E + pa.eoff + x0;
+        for (int idx = lane; idx < xch * ych; idx += 32) {
+            const int xx = idx / ych, yy = idx - xx * ych;
+            double s[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) s[k] = 0.0;
+            for (int h = 0; h < nhx; ++h) {
+                const double ev = __ldg(Eij + (size_t)h * X.nfp + xx);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) s[k] = fma(ev, b.T[((size_t)k * nhx + h) * ych + yy], s[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < NC; ++k) b.G[((size_t)k * xch + xx) * ych + yy] += s[k];
+        }
+        __syncwarp();
+    }
+}
+
+// Screened rows: one CTA per task (bra shell pair x range of sorted ket
+// positions); the CTA's warps take the ket positions round robin.
+template <bool GAUGE>
+__global__ void __launch_bounds__(128) eri_rows_kernel(EriParams prm, const EriTask *tasks, WPlan pl) {
     extern __shared__ double sm[];
     const EriTask tk = tasks[blockIdx.x];
     const PairDev AB = prm.pairs[tk.bra_sp];
-    BlockSmem b = carve(sm, pl);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WSmem b = wcarve(sm + (size_t)warp * pl.warp_doubles, pl);
     const int ij_of[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-    for (int kp = tk.k0; kp < tk.k1; ++kp) {
+    for (int kp = tk.k0 + warp; kp < tk.k1; kp += pl.nwarps) {
         const int cd_id = prm.ket_sp[kp];
         const PairDev CD = prm.pairs[cd_id];
         const long long col = prm.ket_col[kp];
@@ -258,82 +420,74 @@ __global__ void __launch_bounds__(256) eri_rows_kernel(EriParams prm, const EriT
         const bool rev = prm.sym && cd_id != tk.bra_sp && prm.ket_pos[tk.bra_sp] < prm.prefix[cd_id];
         if (rev && cd_id < tk.bra_sp) continue;
         const long long col_rev = rev ? prm.ket_col[prm.ket_pos[tk.bra_sp]] : 0;
-        // contract the orientation with the smaller cost; swapped -> G is (CD|AB)
         const bool swap = orient_cost(CD, AB) < orient_cost(AB, CD);
         const PairDev &X = swap ? CD : AB, &Y = swap ? AB : CD;
         for (int x0 = 0; x0 < X.nfp; x0 += pl.ach) {
             const int x1 = min(X.nfp, x0 + pl.ach);
             for (int y0 = 0; y0 < Y.nfp; y0 += pl.cch) {
                 const int y1 = min(Y.nfp, y0 + pl.cch);
-                block_chunk<GAUGE>(prm.pp, prm.E, prm.boys, X, Y, x0, x1, y0, y1, pl, b);
+                warp_chunk<GAUGE>(prm.pp, prm.E, prm.boys, X, Y, x0, x1, y0, y1, pl, b);
                 const int xch = x1 - x0, ych = y1 - y0;
-                for (int idx = threadIdx.x; idx < xch * ych; idx += blockDim.x) {
+                for (int idx = lane; idx < xch * ych; idx += 32) {
                     const int xx = idx / ych, yy = idx - xx * ych;
                     const int a = swap ? y0 + yy : x0 + xx;      // bra function pair
                     const int c = swap ? x0 + xx : y0 + yy;      // ket function pair
                     const long long row = AB.rowoff + a - prm.row0;
                     const long long cc = col + c;
+                    const double C = b.G[idx];
                     if (!GAUGE) {
-                        prm.W[row * prm.ldw + cc] = b.G[idx];
+                        prm.W[row * prm.ldw + cc] = C;
+                        if (rev) prm.W[(CD.rowoff + c - prm.row0) * prm.ldw + col_rev + a] = C;
                     } else {
-                        const double C = b.G[idx];
                         const double *H = b.G + (size_t)xch * ych;
                         for (int I = 0; I < 3; ++I)
                             for (int J = 0; J < 3; ++J) {
-                                // K_IJ is symmetric, so the swapped block needs no index change
-                                const double h = H[(size_t)ij_of[I][J] * xch * ych + idx];
-                                prm.W[(row * 3 + I) * prm.ldw + cc * 3 + J] = (I == J ? C : 0.0) - h;
+                                // K_IJ is symmetric in I, J and in the two electrons
+                                const double v = (I == J ? C : 0.0) - H[(size_t)ij_of[I][J] * xch * ych + idx];
+                                prm.W[(row * 3 + I) * prm.ldw + cc * 3 + J] = v;
+                                if (rev) prm.W[((CD.rowoff + c - prm.row0) * 3 + I) * prm.ldw + (col_rev + a) * 3 + J] = v;
                             }
-                        if (prm.with_coulomb) prm.Wc[row * prm.ldwc + cc] = C;
-                    }
-                    if (rev) {    // the same integrals at (cd, ab): rows of CD, columns of AB
-                        const long long row2 = CD.rowoff + c - prm.row0;
-                        const long long cc2 = col_rev + a;
-                        if (!GAUGE) {
-                            prm.W[row2 * prm.ldw + cc2] = b.G[idx];
-                        } else {
-                            const double C = b.G[idx];
-                            const double *H = b.G + (size_t)xch * ych;
-                            for (int I = 0; I < 3; ++I)
-                                for (int J = 0; J < 3; ++J) {
-                                    const double h = H[(size_t)ij_of[I][J] * xch * ych + idx];
-                                    prm.W[(row2 * 3 + I) * prm.ldw + cc2 * 3 + J] = (I == J ? C : 0.0) - h;
-                                }
-                            if (prm.with_coulomb) prm.Wc[row2 * prm.ldwc + cc2] = C;
+                        if (prm.with_coulomb) {
+                            prm.Wc[row * prm.ldwc + cc] = C;
+                            if (rev) prm.Wc[(CD.rowoff + c - prm.row0) * prm.ldwc + col_rev + a] = C;
                         }
                     }
                 }
-                __syncthreads();
+                __syncwarp();
             }
         }
     }
 }
 
-Plan eri_plan(int maxnfp, int maxLab, int maxnpp, bool gauge, size_t *smem) {
-    Plan p;
+WPlan eri_wplan(int maxnfp, int maxLab, bool gauge, size_t *smem) {
+    WPlan p;
     p.NC = gauge ? 7 : 1;
     p.ach = p.cch = maxnfp;
     p.nhMax = nherm(maxLab);
     p.LtC = 2 * maxLab;
     p.LtR = gauge ? 2 * maxLab + 2 : -1;
-    p.klg = maxnpp < 16 ? (maxnpp > 0 ? maxnpp : 1) : 16;
-    const size_t budget = 110 * 1024;          // two CTAs per SM
-    while (eri_smem_bytes(p) > budget && (p.ach > 16 || p.klg > 2)) {
-        if (p.klg > 4) p.klg = (p.klg + 1) / 2;
-        else { p.ach = (p.ach + 1) / 2; p.cch = (p.cch + 1) / 2; }
+    // doubles per warp: Coulomb 18 KB (3 CTAs of 4 warps per SM); the gauge
+    // kernel's seven components get 24 KB so its chunks stay large enough that
+    // the Hermite recursion is not repeated too often
+    const int per_warp_budget = (gauge ? 24 : 18) * 1024 / 8;
+    while (wplan_doubles(p.NC, p.ach, p.cch, p.nhMax, p.LtC, p.LtR) > per_warp_budget && p.ach > 4) {
+        p.ach = (p.ach + 1) / 2;
+        p.cch = (p.cch + 1) / 2;
     }
-    *smem = eri_smem_bytes(p);
+    p.warp_doubles = (wplan_doubles(p.NC, p.ach, p.cch, p.nhMax, p.LtC, p.LtR) + 31) & ~31;
+    p.nwarps = 4;
+    while (p.nwarps > 1 && (size_t)p.nwarps * p.warp_doubles * 8 > 200 * 1024) --p.nwarps;
+    *smem = (size_t)p.nwarps * p.warp_doubles * 8;
     return p;
 }
 
 void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxnfp, int maxLab, int maxnpp,
                 cudaStream_t s) {
+    (void)maxnpp;
     if (ntasks <= 0) return;
     size_t smem;
-    Plan pl = eri_plan(maxnfp, maxLab, maxnpp, prm.gauge != 0, &smem);
-    // small plans run as 128-thread CTAs, four per SM, so that a CTA waiting at
-    // a recursion barrier leaves the FP64 pipe to the others
-    const int threads = smem <= 56 * 1024 ? 128 : 256;
+    WPlan pl = eri_wplan(maxnfp, maxLab, prm.gauge != 0, &smem);
+    const int threads = 32 * pl.nwarps;
     if (prm.gauge) {
         QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         eri_rows_kernel<true><<<ntasks, threads, smem, s>>>(prm, tasks, pl);
@@ -342,6 +496,24 @@ void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxn
         eri_rows_kernel<false><<<ntasks, threads, smem, s>>>(prm, tasks, pl);
     }
     QDT_CHECK_LAUNCH();
+}
+
+// CTA-level plan of block_chunk (used by the Schwarz kernel).
+Plan eri_plan(int maxnfp, int maxLab, int maxnpp, bool gauge, size_t *smem) {
+    Plan p;
+    p.NC = gauge ? 7 : 1;
+    p.ach = p.cch = maxnfp;
+    p.nhMax = nherm(maxLab);
+    p.LtC = 2 * maxLab;
+    p.LtR = gauge ? 2 * maxLab + 2 : -1;
+    p.klg = maxnpp < 16 ? (maxnpp > 0 ? maxnpp : 1) : 16;
+    const size_t budget = 110 * 1024;
+    while (eri_smem_bytes(p) > budget && (p.ach > 16 || p.klg > 2)) {
+        if (p.klg > 4) p.klg = (p.klg + 1) / 2;
+        else { p.ach = (p.ach + 1) / 2; p.cch = (p.cch + 1) / 2; }
+    }
+    *smem = eri_smem_bytes(p);
+    return p;
 }
 
 // Schwarz diagonals: Q[AB] = max over ab of sqrt(|(ab|ab)|), Coulomb kernel.
