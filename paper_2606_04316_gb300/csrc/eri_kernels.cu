@@ -18,6 +18,7 @@
 // Boys values in parallel, one barrier per recursion level, then the
 // contraction T = R E' and the accumulation G += E T.
 #include <math.h>
+#include <stdlib.h>
 
 #include "qdt_internal.cuh"
 
@@ -402,6 +403,277 @@ __device__ void warp_chunk(const PrimPairDev *pp, const double *E, const double 
     }
 }
 
+// ------------------------------------------------------------------ DMMA engine
+// For Hermite orders <= 4 per pair (s and p shells and their derivatives) the
+// two contractions of a block are small dense matrix products and run on the
+// FP64 tensor instruction mma.sync.m8n8k4 (256 multiply-adds per warp
+// instruction):  T[h][y] += Rt[h][h'] E^{kl}[h'][y]  with Rt[h][h'] = Rs[h+h']
+// built once per primitive quartet, and  G[x][y] += E^{ij}[h][x] T[h][y].  T and
+// G live in registers as 8x8 accumulator fragments.  The gauge kernel runs its
+// seven components one after the other.
+constexpr int kDM = 4;          // Hermite order limit of a pair for this engine (nherm 35)
+constexpr int kDTile = 32;      // function pairs per chunk side (4 tiles of 8)
+constexpr int kDH = 40;         // nherm(4) = 35 padded to tiles of 8
+constexpr int kDK = 36;         // nherm(4) padded to steps of 4
+
+__device__ inline void dmma884(double &c0, double &c1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(c0), "+d"(c1)
+                 : "d"(a), "d"(b));
+}
+
+struct DSmem {
+    double *Rt;      // [kDH][kDK]
+    double *T;       // [kDH][kDTile]
+    double *RC, *RR; // recursion ping-pong buffers
+    double *F, *sc;
+    int *trX, *trY;
+};
+
+__host__ __device__ inline int dsmem_doubles(int LtC, int LtR) {
+    const int Lt = LtR > LtC ? LtR : LtC;           // one recursion buffer serves both tensors
+    return kDH * kDK + kDH * kDTile + 2 * nherm(Lt) + kWGroup * (kBoysNMax + 3) + kWGroup * 8 + (6 * 35 + 1) / 2 + 2;
+}
+
+__device__ inline DSmem dcarve(double *sm, int LtC, int LtR) {
+    DSmem b;
+    b.Rt = sm; sm += kDH * kDK;
+    b.T = sm; sm += kDH * kDTile;
+    const int Lt = LtR > LtC ? LtR : LtC;
+    b.RC = b.RR = sm; sm += 2 * nherm(Lt);
+    b.F = sm; sm += kWGroup * (kBoysNMax + 3);
+    b.sc = sm; sm += kWGroup * 8;
+    b.trX = (int *)sm;
+    b.trY = b.trX + 3 * 35;
+    return b;
+}
+
+// G accumulators of one chunk (x0.., y0..): 4 x 4 tiles of 8 x 8, 2 doubles per lane each.
+struct DAcc {
+    double g[4][4][2];
+};
+
+// Contract component `comp` of the block chunk; comp 0 is the 1/r12 tensor,
+// comp 1..6 the r12 tensor shifted by e_I + e_J (IJ = xx,xy,xz,yy,yz,zz).
+template <bool GAUGE>
+__device__ void dmma_chunk(const PrimPairDev *pp, const double *E, const double *boys, const PairDev &X,
+                           const PairDev &Y, int x0, int x1, int y0, int y1, int LtC, int LtR, int comp, DSmem &b,
+                           DAcc &acc) {
+    const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    const int Lx = X.Lab, Ly = Y.Lab;
+    const int nhx = nherm(Lx), nhy = nherm(Ly);
+    const int L = Lx + Ly, Lr = L + 2;
+    const bool useR = GAUGE && comp > 0;
+    const int Ltop = useR ? Lr : L;
+    const int xch = x1 - x0, ych = y1 - y0;
+    const int ntX = (xch + 7) >> 3, ntY = (ych + 7) >> 3, ntH = (nhx + 7) >> 3;
+    const int ksT = (nhy + 3) >> 2, ksG = (nhx + 3) >> 2;
+    int sI = 0, sJ = 0;                           // Hermite shift of the gauge component
+    if (useR) {
+        const int IJ[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+        sI = IJ[comp - 1][0];
+        sJ = IJ[comp - 1][1];
+    }
+    const int nr = nherm(LtR > LtC ? LtR : LtC);
+    double *RB = b.RC;
+    for (int h = lane; h < nhx; h += 32) htrip_d(h, b.trX[3 * h], b.trX[3 * h + 1], b.trX[3 * h + 2]);
+    for (int h = lane; h < nhy; h += 32) htrip_d(h, b.trY[3 * h], b.trY[3 * h + 1], b.trY[3 * h + 2]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc.g[i][j][0] = acc.g[i][j][1] = 0.0;
+    __syncwarp();
+    for (int ij = 0; ij < X.npp; ++ij) {
+        const PrimPairDev pa = pp[X.ppoff + ij];
+        double t[5][4][2];
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) t[i][j][0] = t[i][j][1] = 0.0;
+        for (int g0 = 0; g0 < Y.npp; g0 += kWGroup) {
+            const int ng = min(kWGroup, Y.npp - g0);
+            if (lane < ng) {
+                const PrimPairDev pc = pp[Y.ppoff + g0 + lane];
+                double p = pa.p, q = pc.p, rho = p * q / (p + q);
+                double Xq = pa.P[0] - pc.P[0], Yq = pa.P[1] - pc.P[1], Zq = pa.P[2] - pc.P[2];
+                double Tv = rho * (Xq * Xq + Yq * Yq + Zq * Zq);
+                double *F = b.F + lane * (kBoysNMax + 3);
+                boys_eval(boys, Tv, Ltop, F + 1);
+                F[0] = -(2.0 * Tv * F[1] + exp(-Tv));
+                double *sc = b.sc + lane * 8;
+                sc[0] = Xq; sc[1] = Yq; sc[2] = Zq; sc[3] = -2.0 * rho;
+                sc[4] = useR ? pow(M_PI, 2.5) * sqrt(p + q) / (p * p * q * q) : 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p + q));
+            }
+            __syncwarp();
+            for (int g = 0; g < ng; ++g) {
+                const double *sc = b.sc + g * 8;
+                const double *F = b.F + g * (kBoysNMax + 3);
+                const double Xq = sc[0], Yq = sc[1], Zq = sc[2], m2r = sc[3];
+                for (int n = Ltop; n >= 0; --n) {
+                    const int cnt = nherm(Ltop - n);
+                    double *d = RB + (n & 1) * nr, *s = RB + ((n + 1) & 1) * nr;
+                    for (int h = lane; h < cnt; h += 32) {
+                        int tt, u, v;
+                        htrip_d(h, tt, u, v);
+                        double r;
+                        if (h == 0) {
+                            double mp = 1.0;
+                            for (int k = 0; k < n; ++k) mp *= m2r;
+                            r = mp * (useR ? F[n + 1] - F[n] : F[n + 1]) * sc[4];
+                        } else if (tt > 0) r = (tt > 1 ? (tt - 1) * s[hidx(tt - 2, u, v)] : 0.0) + Xq * s[hidx(tt - 1, u, v)];
+                        else if (u > 0) r = (u > 1 ? (u - 1) * s[hidx(tt, u - 2, v)] : 0.0) + Yq * s[hidx(tt, u - 1, v)];
+                        else r = (v > 1 ? (v - 1) * s[hidx(tt, u, v - 2)] : 0.0) + Zq * s[hidx(tt, u, v - 1)];
+                        d[h] = (n == 0 && ((tt + u + v) & 1)) ? -r : r;     // level 0 keeps (-1)^|k| R_k
+                    }
+                    __syncwarp();
+                }
+                // Rt[h][h'] = Rs[h + h' + shift], zero padded
+                for (int i = lane; i < kDH * kDK; i += 32) {
+                    const int h = i / kDK, hp = i - h * kDK;
+                    double v = 0.0;
+                    if (h < nhx && hp < nhy) {
+                        const int dx = useR ? (sI == 0) + (sJ == 0) : 0;
+                        const int dy = useR ? (sI == 1) + (sJ == 1) : 0;
+                        const int dz = useR ? (sI == 2) + (sJ == 2) : 0;
+                        const int T0 = b.trX[3 * h] + b.trY[3 * hp] + dx;
+                        const int U0 = b.trX[3 * h + 1] + b.trY[3 * hp + 1] + dy;
+                        const int V0 = b.trX[3 * h + 2] + b.trY[3 * hp + 2] + dz;
+                        v = RB[hidx(T0, U0, V0)];          // level 0 lives in the first half
+                    }
+                    b.Rt[i] = v;
+                }
+                __syncwarp();
+                // T += Rt E^{kl}
+                const double *e = E + pp[Y.ppoff + g0 + g].eoff;
+                for (int ks = 0; ks < ksT; ++ks) {
+                    const int hp = ks * 4 + tq;
+                    double bf[4];
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt) {
+                        const int y = nt * 8 + gq;
+                        bf[nt] = (nt < ntY && hp < nhy && y < ych) ? __ldg(e + (size_t)hp * Y.nfp + y0 + y) : 0.0;
+                    }
+#pragma unroll
+                    for (int mt = 0; mt < 5; ++mt) {
+                        if (mt >= ntH) break;
+                        const double a = b.Rt[(mt * 8 + gq) * kDK + ks * 4 + tq];
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt)
+                            if (nt < ntY) dmma884(t[mt][nt][0], t[mt][nt][1], a, bf[nt]);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // store T (rows h, with the sign (-1)^|h|) for the second product
+#pragma unroll
+        for (int mt = 0; mt < 5; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int h = mt * 8 + gq;
+                const bool odd = h < nhx && ((b.trX[3 * h] + b.trX[3 * h + 1] + b.trX[3 * h + 2]) & 1);
+                const int y = nt * 8 + 2 * tq;
+                if (mt < ntH && nt < ntY) {
+                    b.T[h * kDTile + y] = odd ? -t[mt][nt][0] : t[mt][nt][0];
+                    b.T[h * kDTile + y + 1] = odd ? -t[mt][nt][1] : t[mt][nt][1];
+                }
+            }
+        __syncwarp();
+        // G += E^{ij}^T T
+        const double *ea = E + pa.eoff;
+        for (int ks = 0; ks < ksG; ++ks) {
+            const int h = ks * 4 + tq;
+            double bf[4];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) bf[nt] = (nt < ntY && h < nhx) ? b.T[(ks * 4 + tq) * kDTile + nt * 8 + gq] : 0.0;
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) {
+                if (mt >= ntX) break;
+                const int x = mt * 8 + gq;
+                const double a = (h < nhx && x < xch) ? __ldg(ea + (size_t)h * X.nfp + x0 + x) : 0.0;
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+                    if (nt < ntY) dmma884(acc.g[mt][nt][0], acc.g[mt][nt][1], a, bf[nt]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <bool GAUGE>
+__global__ void __launch_bounds__(128) eri_rows_dmma_kernel(EriParams prm, const EriTask *tasks, int LtC, int LtR,
+                                                            int wdoubles, int nwarps) {
+    extern __shared__ double sm[];
+    const EriTask tk = tasks[blockIdx.x];
+    const PairDev AB = prm.pairs[tk.bra_sp];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    DSmem b = dcarve(sm + (size_t)warp * wdoubles, LtC, LtR);
+    const int IJ[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int kp = tk.k0 + warp; kp < tk.k1; kp += nwarps) {
+        const int cd_id = prm.ket_sp[kp];
+        const PairDev CD = prm.pairs[cd_id];
+        const long long col = prm.ket_col[kp];
+        const bool rev = prm.sym && cd_id != tk.bra_sp && prm.ket_pos[tk.bra_sp] < prm.prefix[cd_id];
+        if (rev && cd_id < tk.bra_sp) continue;
+        const long long col_rev = rev ? prm.ket_col[prm.ket_pos[tk.bra_sp]] : 0;
+        const bool swap = orient_cost(CD, AB) < orient_cost(AB, CD);
+        const PairDev &X = swap ? CD : AB, &Y = swap ? AB : CD;
+        for (int x0 = 0; x0 < X.nfp; x0 += kDTile) {
+            const int x1 = min(X.nfp, x0 + kDTile);
+            for (int y0 = 0; y0 < Y.nfp; y0 += kDTile) {
+                const int y1 = min(Y.nfp, y0 + kDTile);
+                const int ncomp = GAUGE ? 7 : 1;
+                for (int comp = 0; comp < ncomp; ++comp) {
+                    DAcc acc;
+                    dmma_chunk<GAUGE>(prm.pp, prm.E, prm.boys, X, Y, x0, x1, y0, y1, LtC, LtR, comp, b, acc);
+#pragma unroll
+                    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                const int xx = mt * 8 + gq, yy = nt * 8 + 2 * tq + q;
+                                if (x0 + xx >= x1 || y0 + yy >= y1) continue;
+                                const int a = swap ? y0 + yy : x0 + xx;
+                                const int c = swap ? x0 + xx : y0 + yy;
+                                const long long row = AB.rowoff + a - prm.row0, cc = col + c;
+                                const long long row2 = rev ? CD.rowoff + c - prm.row0 : 0, cc2 = col_rev + a;
+                                const double v = acc.g[mt][nt][q];
+                                if (!GAUGE) {
+                                    prm.W[row * prm.ldw + cc] = v;
+                                    if (rev) prm.W[row2 * prm.ldw + cc2] = v;
+                                } else if (comp == 0) {
+                                    // Coulomb part: Gaunt block and the delta_IJ term of the gauge kernel
+                                    for (int I = 0; I < 3; ++I)
+                                        for (int J = 0; J < 3; ++J) {
+                                            const double w = I == J ? v : 0.0;
+                                            prm.W[(row * 3 + I) * prm.ldw + cc * 3 + J] = w;
+                                            if (rev) prm.W[(row2 * 3 + I) * prm.ldw + cc2 * 3 + J] = w;
+                                        }
+                                    if (prm.with_coulomb) {
+                                        prm.Wc[row * prm.ldwc + cc] = v;
+                                        if (rev) prm.Wc[row2 * prm.ldwc + cc2] = v;
+                                    }
+                                } else {
+                                    // - (xy|d_I d_J r|zw), symmetric in I, J and in the electrons
+                                    const int I = IJ[comp - 1][0], J = IJ[comp - 1][1];
+                                    prm.W[(row * 3 + I) * prm.ldw + cc * 3 + J] -= v;
+                                    if (I != J) prm.W[(row * 3 + J) * prm.ldw + cc * 3 + I] -= v;
+                                    if (rev) {
+                                        prm.W[(row2 * 3 + I) * prm.ldw + cc2 * 3 + J] -= v;
+                                        if (I != J) prm.W[(row2 * 3 + J) * prm.ldw + cc2 * 3 + I] -= v;
+                                    }
+                                }
+                            }
+                    __syncwarp();
+                }
+            }
+        }
+    }
+}
+
+bool eri_dmma_fits(int maxLab) { return maxLab <= kDM; }
+
 // Screened rows: one CTA per task (bra shell pair x range of sorted ket
 // positions); the CTA's warps take the ket positions round robin.
 template <bool GAUGE>
@@ -485,6 +757,21 @@ void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxn
                 cudaStream_t s) {
     (void)maxnpp;
     if (ntasks <= 0) return;
+    if (eri_dmma_fits(maxLab) && !getenv("QDT_ERI_DFMA")) {
+        const int LtC = 2 * maxLab, LtR = prm.gauge ? 2 * maxLab + 2 : -1;
+        const int wd = (dsmem_doubles(LtC, LtR) + 31) & ~31;
+        const int nwarps = 4;
+        const size_t smem = (size_t)nwarps * wd * 8;
+        if (prm.gauge) {
+            QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_dmma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            eri_rows_dmma_kernel<true><<<ntasks, 32 * nwarps, smem, s>>>(prm, tasks, LtC, LtR, wd, nwarps);
+        } else {
+            QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_dmma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            eri_rows_dmma_kernel<false><<<ntasks, 32 * nwarps, smem, s>>>(prm, tasks, LtC, LtR, wd, nwarps);
+        }
+        QDT_CHECK_LAUNCH();
+        return;
+    }
     size_t smem;
     WPlan pl = eri_wplan(maxnfp, maxLab, prm.gauge != 0, &smem);
     const int threads = 32 * pl.nwarps;

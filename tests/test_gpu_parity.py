@@ -146,3 +146,49 @@ def test_full_size_chain40_properties(torch_cuda):
     full[ju, :, iu, :] = blk.transpose(0, 2, 1)
     w = np.linalg.eigvalsh(full.reshape(4 * nP, 4 * nP))
     assert w.min() >= -1e-10 * w.max()
+
+
+def test_d_shells_all_blocks(oracle, torch_cuda):
+    """s, p and d shells (derivative functions up to f): both forms, all blocks."""
+    torch = torch_cuda
+    p = synth.chain_problem(2, 2, seed=601, shells=(0, 1, 2), nprim=2,
+                            blocks=("coulomb", "gaunt", "gauge"), tau=0.0)
+    tr = oracle.Transform(p)
+    for prec, tol in ((0, TOL_FP64), (1, TOL_SPLIT)):
+        ctx, got, st = run_gpu(torch, p, list(p.blocks), 0, p.nK, 0.0, precision=prec)
+        for i, b in enumerate(p.blocks):
+            err = np.abs(got[i] - tr.packed(b).reshape(-1)).max()
+            assert err <= tol, (prec, b, err)
+
+
+def test_single_kramers_pair_and_s_only(oracle, torch_cuda):
+    torch = torch_cuda
+    p = synth.chain_problem(4, 1, seed=602, shells=(0,), nprim=2, blocks=("coulomb", "gaunt"), tau=0.0)
+    ctx, got, st = run_gpu(torch, p, ["coulomb", "gaunt"], 0, 1, 0.0)
+    tr = oracle.Transform(p)
+    for i, b in enumerate(["coulomb", "gaunt"]):
+        assert np.abs(got[i] - tr.packed(b).reshape(-1)).max() <= TOL_FP64
+
+
+def test_argument_errors(torch_cuda):
+    torch = torch_cuda
+    from paper_2606_04316_gb300 import qdt
+    p = synth.chain_problem(2, 2, seed=603, shells=(0,), nprim=1, blocks=("coulomb",), tau=0.0)
+    ctx = qdt.Context(0)
+    out = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(qdt.QdtError) as e:            # no basis yet
+        ctx.transform(["coulomb"], 0, 1, 0.0, 0, out)
+    assert e.value.code == -4
+    ctx.set_basis(p.basis)
+    ctx.set_coefficients(p.CL, p.CS)
+    for args in [(0, 0, 0.0, 0), (1, 3, 0.0, 0), (0, 2, -1.0, 0), (0, 2, 0.0, 7)]:
+        with pytest.raises(qdt.QdtError) as e:
+            ctx.transform(["coulomb"], args[0], args[1], args[2], args[3], out)
+        assert e.value.code == -1
+    small = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(qdt.QdtError):
+        ctx.transform(["coulomb"], 0, 2, 0.0, 0, small)
+    bad = synth.chain_problem(1, 1, seed=604, shells=(3,), nprim=1, blocks=("coulomb",), tau=0.0)
+    with pytest.raises(qdt.QdtError) as e:
+        ctx.set_basis(bad.basis)                        # f shells are not accepted
+    assert e.value.code == -1
