@@ -403,44 +403,39 @@ __device__ void warp_chunk(const PrimPairDev *pp, const double *E, const double 
     }
 }
 
-// ------------------------------------------------------------------ DMMA engine
+// ------------------------------------------------------------------ GEMM engine
 // For Hermite orders <= 4 per pair (s and p shells and their derivatives) the
-// two contractions of a block are small dense matrix products and run on the
-// FP64 tensor instruction mma.sync.m8n8k4 (256 multiply-adds per warp
-// instruction):  T[h][y] += Rt[h][h'] E^{kl}[h'][y]  with Rt[h][h'] = Rs[h+h']
-// built once per primitive quartet, and  G[x][y] += E^{ij}[h][x] T[h][y].  T and
-// G live in registers as 8x8 accumulator fragments.  The gauge kernel runs its
-// seven components one after the other.
+// two contractions of a block are dense register-blocked FP64 micro-GEMMs:
+//   T[h][y] += Rt[h][h'] E^{kl}[h'][y],   Rt[h][h'] = Rs[h + h'] (one primitive quartet)
+//   G[x][y] += E^{ij}[h][x] T[h][y]
+// Each of 128 threads owns a 4 x 4 block of T and of G in registers; Rt and E
+// are staged k-major in shared memory so one k step is 8 loads for 16 FMAs.
+// The gauge kernel runs its seven components one after the other.
 constexpr int kDM = 4;          // Hermite order limit of a pair for this engine (nherm 35)
-constexpr int kDTile = 32;      // function pairs per chunk side (4 tiles of 8)
-constexpr int kDH = 40;         // nherm(4) = 35 padded to tiles of 8
-constexpr int kDK = 36;         // nherm(4) padded to steps of 4
+constexpr int kGT = 36;         // function pairs per chunk side (9 blocks of 4)
+constexpr int kGH = 36;         // nherm(4) = 35 padded to blocks of 4
 
-__device__ inline void dmma884(double &c0, double &c1, double a, double b) {
-    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
-                 : "+d"(c0), "+d"(c1)
-                 : "d"(a), "d"(b));
-}
-
-struct DSmem {
-    double *Rt;      // [kDH][kDK]
-    double *T;       // [kDH][kDTile]
-    double *RC, *RR; // recursion ping-pong buffers
+struct GSmem {
+    double *Rt;      // [kGH (h')][kGH (h)]  k-major
+    double *Ek;      // [kGH (h')][kGT (y)]
+    double *T;       // [kGH (h)][kGT (y)]
+    double *Ei;      // [kGH (h)][kGT (x)]
+    double *RB;      // recursion ping-pong
     double *F, *sc;
     int *trX, *trY;
 };
 
-__host__ __device__ inline int dsmem_doubles(int LtC, int LtR) {
-    const int Lt = LtR > LtC ? LtR : LtC;           // one recursion buffer serves both tensors
-    return kDH * kDK + kDH * kDTile + 2 * nherm(Lt) + kWGroup * (kBoysNMax + 3) + kWGroup * 8 + (6 * 35 + 1) / 2 + 2;
+__host__ __device__ inline int gsmem_doubles(int Lt) {
+    return kGH * kGH + 3 * kGH * kGT + 2 * nherm(Lt) + kWGroup * (kBoysNMax + 3) + kWGroup * 8 + 105 + 2;
 }
 
-__device__ inline DSmem dcarve(double *sm, int LtC, int LtR) {
-    DSmem b;
-    b.Rt = sm; sm += kDH * kDK;
-    b.T = sm; sm += kDH * kDTile;
-    const int Lt = LtR > LtC ? LtR : LtC;
-    b.RC = b.RR = sm; sm += 2 * nherm(Lt);
+__device__ inline GSmem gcarve(double *sm, int Lt) {
+    GSmem b;
+    b.Rt = sm; sm += kGH * kGH;
+    b.Ek = sm; sm += kGH * kGT;
+    b.T = sm; sm += kGH * kGT;
+    b.Ei = sm; sm += kGH * kGT;
+    b.RB = sm; sm += 2 * nherm(Lt);
     b.F = sm; sm += kWGroup * (kBoysNMax + 3);
     b.sc = sm; sm += kWGroup * 8;
     b.trX = (int *)sm;
@@ -448,71 +443,66 @@ __device__ inline DSmem dcarve(double *sm, int LtC, int LtR) {
     return b;
 }
 
-// G accumulators of one chunk (x0.., y0..): 4 x 4 tiles of 8 x 8, 2 doubles per lane each.
-struct DAcc {
-    double g[4][4][2];
-};
-
-// Contract component `comp` of the block chunk; comp 0 is the 1/r12 tensor,
-// comp 1..6 the r12 tensor shifted by e_I + e_J (IJ = xx,xy,xz,yy,yz,zz).
+// One chunk of block (X|Y), component comp (0: 1/r12; 1..6: r12 shifted by
+// e_I + e_J); returns this thread's 4 x 4 block of G (rows x = 4 bi + r,
+// columns y = 4 bj + c with bi = tid / 9, bj = tid % 9; tid >= 81 idle).
 template <bool GAUGE>
-__device__ void dmma_chunk(const PrimPairDev *pp, const double *E, const double *boys, const PairDev &X,
-                           const PairDev &Y, int x0, int x1, int y0, int y1, int LtC, int LtR, int comp, DSmem &b,
-                           DAcc &acc) {
-    const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+__device__ void gemm_chunk(const PrimPairDev *pp, const double *E, const double *boys, const PairDev &X,
+                           const PairDev &Y, int x0, int x1, int y0, int y1, int Lt, int comp, GSmem &b,
+                           double g[4][4]) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int bi = tid / 9, bj = tid - 9 * bi;
+    const bool act = tid < 81;
     const int Lx = X.Lab, Ly = Y.Lab;
     const int nhx = nherm(Lx), nhy = nherm(Ly);
-    const int L = Lx + Ly, Lr = L + 2;
+    const int L = Lx + Ly;
     const bool useR = GAUGE && comp > 0;
-    const int Ltop = useR ? Lr : L;
+    const int Ltop = useR ? L + 2 : L;
     const int xch = x1 - x0, ych = y1 - y0;
-    const int ntX = (xch + 7) >> 3, ntY = (ych + 7) >> 3, ntH = (nhx + 7) >> 3;
-    const int ksT = (nhy + 3) >> 2, ksG = (nhx + 3) >> 2;
-    int sI = 0, sJ = 0;                           // Hermite shift of the gauge component
+    const int nr = nherm(Lt);
+    int dx = 0, dy = 0, dz = 0;
     if (useR) {
         const int IJ[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-        sI = IJ[comp - 1][0];
-        sJ = IJ[comp - 1][1];
+        const int I = IJ[comp - 1][0], J = IJ[comp - 1][1];
+        dx = (I == 0) + (J == 0); dy = (I == 1) + (J == 1); dz = (I == 2) + (J == 2);
     }
-    const int nr = nherm(LtR > LtC ? LtR : LtC);
-    double *RB = b.RC;
-    for (int h = lane; h < nhx; h += 32) htrip_d(h, b.trX[3 * h], b.trX[3 * h + 1], b.trX[3 * h + 2]);
-    for (int h = lane; h < nhy; h += 32) htrip_d(h, b.trY[3 * h], b.trY[3 * h + 1], b.trY[3 * h + 2]);
+    for (int h = tid; h < nhx; h += nt) htrip_d(h, b.trX[3 * h], b.trX[3 * h + 1], b.trX[3 * h + 2]);
+    for (int h = tid; h < nhy; h += nt) htrip_d(h, b.trY[3 * h], b.trY[3 * h + 1], b.trY[3 * h + 2]);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc.g[i][j][0] = acc.g[i][j][1] = 0.0;
-    __syncwarp();
+        for (int c = 0; c < 4; ++c) g[r][c] = 0.0;
+    __syncthreads();
     for (int ij = 0; ij < X.npp; ++ij) {
         const PrimPairDev pa = pp[X.ppoff + ij];
-        double t[5][4][2];
+        double t[4][4];
 #pragma unroll
-        for (int i = 0; i < 5; ++i)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) t[i][j][0] = t[i][j][1] = 0.0;
+            for (int c = 0; c < 4; ++c) t[r][c] = 0.0;
         for (int g0 = 0; g0 < Y.npp; g0 += kWGroup) {
             const int ng = min(kWGroup, Y.npp - g0);
-            if (lane < ng) {
-                const PrimPairDev pc = pp[Y.ppoff + g0 + lane];
+            if (tid < ng) {
+                const PrimPairDev pc = pp[Y.ppoff + g0 + tid];
                 double p = pa.p, q = pc.p, rho = p * q / (p + q);
                 double Xq = pa.P[0] - pc.P[0], Yq = pa.P[1] - pc.P[1], Zq = pa.P[2] - pc.P[2];
                 double Tv = rho * (Xq * Xq + Yq * Yq + Zq * Zq);
-                double *F = b.F + lane * (kBoysNMax + 3);
+                double *F = b.F + tid * (kBoysNMax + 3);
                 boys_eval(boys, Tv, Ltop, F + 1);
                 F[0] = -(2.0 * Tv * F[1] + exp(-Tv));
-                double *sc = b.sc + lane * 8;
+                double *sc = b.sc + tid * 8;
                 sc[0] = Xq; sc[1] = Yq; sc[2] = Zq; sc[3] = -2.0 * rho;
                 sc[4] = useR ? pow(M_PI, 2.5) * sqrt(p + q) / (p * p * q * q) : 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p + q));
             }
-            __syncwarp();
+            __syncthreads();
             for (int g = 0; g < ng; ++g) {
                 const double *sc = b.sc + g * 8;
                 const double *F = b.F + g * (kBoysNMax + 3);
                 const double Xq = sc[0], Yq = sc[1], Zq = sc[2], m2r = sc[3];
                 for (int n = Ltop; n >= 0; --n) {
                     const int cnt = nherm(Ltop - n);
-                    double *d = RB + (n & 1) * nr, *s = RB + ((n + 1) & 1) * nr;
-                    for (int h = lane; h < cnt; h += 32) {
+                    double *d = b.RB + (n & 1) * nr, *s = b.RB + ((n + 1) & 1) * nr;
+                    for (int h = tid; h < cnt; h += nt) {
                         int tt, u, v;
                         htrip_d(h, tt, u, v);
                         double r;
@@ -525,91 +515,81 @@ __device__ void dmma_chunk(const PrimPairDev *pp, const double *E, const double 
                         else r = (v > 1 ? (v - 1) * s[hidx(tt, u, v - 2)] : 0.0) + Zq * s[hidx(tt, u, v - 1)];
                         d[h] = (n == 0 && ((tt + u + v) & 1)) ? -r : r;     // level 0 keeps (-1)^|k| R_k
                     }
-                    __syncwarp();
+                    __syncthreads();
                 }
-                // Rt[h][h'] = Rs[h + h' + shift], zero padded
-                for (int i = lane; i < kDH * kDK; i += 32) {
-                    const int h = i / kDK, hp = i - h * kDK;
+                // stage Rt (k-major) and E^{kl}, zero padded
+                const double *ekl = E + pp[Y.ppoff + g0 + g].eoff;
+                for (int i = tid; i < kGH * kGH; i += nt) {
+                    const int hp = i / kGH, h = i - hp * kGH;
                     double v = 0.0;
-                    if (h < nhx && hp < nhy) {
-                        const int dx = useR ? (sI == 0) + (sJ == 0) : 0;
-                        const int dy = useR ? (sI == 1) + (sJ == 1) : 0;
-                        const int dz = useR ? (sI == 2) + (sJ == 2) : 0;
-                        const int T0 = b.trX[3 * h] + b.trY[3 * hp] + dx;
-                        const int U0 = b.trX[3 * h + 1] + b.trY[3 * hp + 1] + dy;
-                        const int V0 = b.trX[3 * h + 2] + b.trY[3 * hp + 2] + dz;
-                        v = RB[hidx(T0, U0, V0)];          // level 0 lives in the first half
-                    }
+                    if (h < nhx && hp < nhy)
+                        v = b.RB[hidx(b.trX[3 * h] + b.trY[3 * hp] + dx, b.trX[3 * h + 1] + b.trY[3 * hp + 1] + dy,
+                                      b.trX[3 * h + 2] + b.trY[3 * hp + 2] + dz)];
                     b.Rt[i] = v;
                 }
-                __syncwarp();
-                // T += Rt E^{kl}
-                const double *e = E + pp[Y.ppoff + g0 + g].eoff;
-                for (int ks = 0; ks < ksT; ++ks) {
-                    const int hp = ks * 4 + tq;
-                    double bf[4];
+                for (int i = tid; i < kGH * kGT; i += nt) {
+                    const int hp = i / kGT, y = i - hp * kGT;
+                    b.Ek[i] = (hp < nhy && y < ych) ? __ldg(ekl + (size_t)hp * Y.nfp + y0 + y) : 0.0;
+                }
+                __syncthreads();
+                if (act) {
+                    for (int k = 0; k < nhy; ++k) {
+                        const double2 a01 = *reinterpret_cast<const double2 *>(b.Rt + k * kGH + 4 * bi);
+                        const double2 a23 = *reinterpret_cast<const double2 *>(b.Rt + k * kGH + 4 * bi + 2);
+                        const double2 e01 = *reinterpret_cast<const double2 *>(b.Ek + k * kGT + 4 * bj);
+                        const double2 e23 = *reinterpret_cast<const double2 *>(b.Ek + k * kGT + 4 * bj + 2);
+                        const double a[4] = {a01.x, a01.y, a23.x, a23.y}, ev[4] = {e01.x, e01.y, e23.x, e23.y};
 #pragma unroll
-                    for (int nt = 0; nt < 4; ++nt) {
-                        const int y = nt * 8 + gq;
-                        bf[nt] = (nt < ntY && hp < nhy && y < ych) ? __ldg(e + (size_t)hp * Y.nfp + y0 + y) : 0.0;
-                    }
+                        for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int mt = 0; mt < 5; ++mt) {
-                        if (mt >= ntH) break;
-                        const double a = b.Rt[(mt * 8 + gq) * kDK + ks * 4 + tq];
-#pragma unroll
-                        for (int nt = 0; nt < 4; ++nt)
-                            if (nt < ntY) dmma884(t[mt][nt][0], t[mt][nt][1], a, bf[nt]);
+                            for (int c = 0; c < 4; ++c) t[r][c] = fma(a[r], ev[c], t[r][c]);
                     }
                 }
-                __syncwarp();
+                __syncthreads();
             }
         }
-        // store T (rows h, with the sign (-1)^|h|) for the second product
+        // T with the sign (-1)^|h| of its row, and E^{ij}, into shared memory
+        if (act) {
 #pragma unroll
-        for (int mt = 0; mt < 5; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const int h = mt * 8 + gq;
+            for (int r = 0; r < 4; ++r) {
+                const int h = 4 * bi + r;
                 const bool odd = h < nhx && ((b.trX[3 * h] + b.trX[3 * h + 1] + b.trX[3 * h + 2]) & 1);
-                const int y = nt * 8 + 2 * tq;
-                if (mt < ntH && nt < ntY) {
-                    b.T[h * kDTile + y] = odd ? -t[mt][nt][0] : t[mt][nt][0];
-                    b.T[h * kDTile + y + 1] = odd ? -t[mt][nt][1] : t[mt][nt][1];
-                }
-            }
-        __syncwarp();
-        // G += E^{ij}^T T
-        const double *ea = E + pa.eoff;
-        for (int ks = 0; ks < ksG; ++ks) {
-            const int h = ks * 4 + tq;
-            double bf[4];
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) bf[nt] = (nt < ntY && h < nhx) ? b.T[(ks * 4 + tq) * kDTile + nt * 8 + gq] : 0.0;
-#pragma unroll
-            for (int mt = 0; mt < 4; ++mt) {
-                if (mt >= ntX) break;
-                const int x = mt * 8 + gq;
-                const double a = (h < nhx && x < xch) ? __ldg(ea + (size_t)h * X.nfp + x0 + x) : 0.0;
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
-                    if (nt < ntY) dmma884(acc.g[mt][nt][0], acc.g[mt][nt][1], a, bf[nt]);
+                for (int c = 0; c < 4; ++c) b.T[h * kGT + 4 * bj + c] = odd ? -t[r][c] : t[r][c];
             }
         }
-        __syncwarp();
+        const double *eij = E + pa.eoff;
+        for (int i = tid; i < kGH * kGT; i += nt) {
+            const int h = i / kGT, x = i - h * kGT;
+            b.Ei[i] = (h < nhx && x < xch) ? __ldg(eij + (size_t)h * X.nfp + x0 + x) : 0.0;
+        }
+        __syncthreads();
+        if (act) {
+            for (int k = 0; k < nhx; ++k) {
+                const double2 a01 = *reinterpret_cast<const double2 *>(b.Ei + k * kGT + 4 * bi);
+                const double2 a23 = *reinterpret_cast<const double2 *>(b.Ei + k * kGT + 4 * bi + 2);
+                const double2 t01 = *reinterpret_cast<const double2 *>(b.T + k * kGT + 4 * bj);
+                const double2 t23 = *reinterpret_cast<const double2 *>(b.T + k * kGT + 4 * bj + 2);
+                const double a[4] = {a01.x, a01.y, a23.x, a23.y}, tv[4] = {t01.x, t01.y, t23.x, t23.y};
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) g[r][c] = fma(a[r], tv[c], g[r][c]);
+            }
+        }
+        __syncthreads();
     }
 }
 
 template <bool GAUGE>
-__global__ void __launch_bounds__(128) eri_rows_dmma_kernel(EriParams prm, const EriTask *tasks, int LtC, int LtR,
-                                                            int wdoubles, int nwarps) {
+__global__ void __launch_bounds__(128) eri_rows_gemm_kernel(EriParams prm, const EriTask *tasks, int Lt) {
     extern __shared__ double sm[];
     const EriTask tk = tasks[blockIdx.x];
     const PairDev AB = prm.pairs[tk.bra_sp];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
-    DSmem b = dcarve(sm + (size_t)warp * wdoubles, LtC, LtR);
+    const int tid = threadIdx.x, bi = tid / 9, bj = tid - 9 * bi;
+    GSmem b = gcarve(sm, Lt);
     const int IJ[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-    for (int kp = tk.k0 + warp; kp < tk.k1; kp += nwarps) {
+    for (int kp = tk.k0; kp < tk.k1; ++kp) {
         const int cd_id = prm.ket_sp[kp];
         const PairDev CD = prm.pairs[cd_id];
         const long long col = prm.ket_col[kp];
@@ -618,61 +598,59 @@ __global__ void __launch_bounds__(128) eri_rows_dmma_kernel(EriParams prm, const
         const long long col_rev = rev ? prm.ket_col[prm.ket_pos[tk.bra_sp]] : 0;
         const bool swap = orient_cost(CD, AB) < orient_cost(AB, CD);
         const PairDev &X = swap ? CD : AB, &Y = swap ? AB : CD;
-        for (int x0 = 0; x0 < X.nfp; x0 += kDTile) {
-            const int x1 = min(X.nfp, x0 + kDTile);
-            for (int y0 = 0; y0 < Y.nfp; y0 += kDTile) {
-                const int y1 = min(Y.nfp, y0 + kDTile);
+        for (int x0 = 0; x0 < X.nfp; x0 += kGT) {
+            const int x1 = min(X.nfp, x0 + kGT);
+            for (int y0 = 0; y0 < Y.nfp; y0 += kGT) {
+                const int y1 = min(Y.nfp, y0 + kGT);
                 const int ncomp = GAUGE ? 7 : 1;
                 for (int comp = 0; comp < ncomp; ++comp) {
-                    DAcc acc;
-                    dmma_chunk<GAUGE>(prm.pp, prm.E, prm.boys, X, Y, x0, x1, y0, y1, LtC, LtR, comp, b, acc);
+                    double g[4][4];
+                    gemm_chunk<GAUGE>(prm.pp, prm.E, prm.boys, X, Y, x0, x1, y0, y1, Lt, comp, b, g);
+                    if (tid >= 81) continue;
 #pragma unroll
-                    for (int mt = 0; mt < 4; ++mt)
+                    for (int r = 0; r < 4; ++r)
 #pragma unroll
-                        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                const int xx = mt * 8 + gq, yy = nt * 8 + 2 * tq + q;
-                                if (x0 + xx >= x1 || y0 + yy >= y1) continue;
-                                const int a = swap ? y0 + yy : x0 + xx;
-                                const int c = swap ? x0 + xx : y0 + yy;
-                                const long long row = AB.rowoff + a - prm.row0, cc = col + c;
-                                const long long row2 = rev ? CD.rowoff + c - prm.row0 : 0, cc2 = col_rev + a;
-                                const double v = acc.g[mt][nt][q];
-                                if (!GAUGE) {
-                                    prm.W[row * prm.ldw + cc] = v;
-                                    if (rev) prm.W[row2 * prm.ldw + cc2] = v;
-                                } else if (comp == 0) {
-                                    // Coulomb part: Gaunt block and the delta_IJ term of the gauge kernel
-                                    for (int I = 0; I < 3; ++I)
-                                        for (int J = 0; J < 3; ++J) {
-                                            const double w = I == J ? v : 0.0;
-                                            prm.W[(row * 3 + I) * prm.ldw + cc * 3 + J] = w;
-                                            if (rev) prm.W[(row2 * 3 + I) * prm.ldw + cc2 * 3 + J] = w;
-                                        }
-                                    if (prm.with_coulomb) {
-                                        prm.Wc[row * prm.ldwc + cc] = v;
-                                        if (rev) prm.Wc[row2 * prm.ldwc + cc2] = v;
+                        for (int c = 0; c < 4; ++c) {
+                            const int xx = 4 * bi + r, yy = 4 * bj + c;
+                            if (x0 + xx >= x1 || y0 + yy >= y1) continue;
+                            const int a = swap ? y0 + yy : x0 + xx;
+                            const int cq = swap ? x0 + xx : y0 + yy;
+                            const long long row = AB.rowoff + a - prm.row0, cc = col + cq;
+                            const long long row2 = rev ? CD.rowoff + cq - prm.row0 : 0, cc2 = col_rev + a;
+                            const double v = g[r][c];
+                            if (!GAUGE) {
+                                prm.W[row * prm.ldw + cc] = v;
+                                if (rev) prm.W[row2 * prm.ldw + cc2] = v;
+                            } else if (comp == 0) {
+                                // Coulomb part: Gaunt block and the delta_IJ term of the gauge kernel
+                                for (int I = 0; I < 3; ++I)
+                                    for (int J = 0; J < 3; ++J) {
+                                        const double w = I == J ? v : 0.0;
+                                        prm.W[(row * 3 + I) * prm.ldw + cc * 3 + J] = w;
+                                        if (rev) prm.W[(row2 * 3 + I) * prm.ldw + cc2 * 3 + J] = w;
                                     }
-                                } else {
-                                    // - (xy|d_I d_J r|zw), symmetric in I, J and in the electrons
-                                    const int I = IJ[comp - 1][0], J = IJ[comp - 1][1];
-                                    prm.W[(row * 3 + I) * prm.ldw + cc * 3 + J] -= v;
-                                    if (I != J) prm.W[(row * 3 + J) * prm.ldw + cc * 3 + I] -= v;
-                                    if (rev) {
-                                        prm.W[(row2 * 3 + I) * prm.ldw + cc2 * 3 + J] -= v;
-                                        if (I != J) prm.W[(row2 * 3 + J) * prm.ldw + cc2 * 3 + I] -= v;
-                                    }
+                                if (prm.with_coulomb) {
+                                    prm.Wc[row * prm.ldwc + cc] = v;
+                                    if (rev) prm.Wc[row2 * prm.ldwc + cc2] = v;
+                                }
+                            } else {
+                                // - (xy|d_I d_J r|zw), symmetric in I, J and in the electrons
+                                const int I = IJ[comp - 1][0], J = IJ[comp - 1][1];
+                                prm.W[(row * 3 + I) * prm.ldw + cc * 3 + J] -= v;
+                                if (I != J) prm.W[(row * 3 + J) * prm.ldw + cc * 3 + I] -= v;
+                                if (rev) {
+                                    prm.W[(row2 * 3 + I) * prm.ldw + cc2 * 3 + J] -= v;
+                                    if (I != J) prm.W[(row2 * 3 + J) * prm.ldw + cc2 * 3 + I] -= v;
                                 }
                             }
-                    __syncwarp();
+                        }
                 }
             }
         }
     }
 }
 
-bool eri_dmma_fits(int maxLab) { return maxLab <= kDM; }
+bool eri_gemm_fits(int maxLab) { return maxLab <= kDM; }
 
 // Screened rows: one CTA per task (bra shell pair x range of sorted ket
 // positions); the CTA's warps take the ket positions round robin.
@@ -757,17 +735,15 @@ void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxn
                 cudaStream_t s) {
     (void)maxnpp;
     if (ntasks <= 0) return;
-    if (eri_dmma_fits(maxLab) && !getenv("QDT_ERI_DFMA")) {
-        const int LtC = 2 * maxLab, LtR = prm.gauge ? 2 * maxLab + 2 : -1;
-        const int wd = (dsmem_doubles(LtC, LtR) + 31) & ~31;
-        const int nwarps = 4;
-        const size_t smem = (size_t)nwarps * wd * 8;
+    if (eri_gemm_fits(maxLab)) {
+        const int Lt = 2 * maxLab + (prm.gauge ? 2 : 0);
+        const size_t smem = (size_t)gsmem_doubles(Lt) * 8;
         if (prm.gauge) {
-            QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_dmma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            eri_rows_dmma_kernel<true><<<ntasks, 32 * nwarps, smem, s>>>(prm, tasks, LtC, LtR, wd, nwarps);
+            QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            eri_rows_gemm_kernel<true><<<ntasks, 128, smem, s>>>(prm, tasks, Lt);
         } else {
-            QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_dmma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            eri_rows_dmma_kernel<false><<<ntasks, 32 * nwarps, smem, s>>>(prm, tasks, LtC, LtR, wd, nwarps);
+            QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            eri_rows_gemm_kernel<false><<<ntasks, 128, smem, s>>>(prm, tasks, Lt);
         }
         QDT_CHECK_LAUNCH();
         return;
