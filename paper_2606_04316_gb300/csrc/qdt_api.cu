@@ -349,7 +349,7 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
         if (Wc) launch_zero(Wc, rows * ldwc, s);
         // tasks: bra pair x chunks of its ket prefix
         std::vector<EriTask> tk;
-        const int CH = 16;                 // ket positions per task (4 warps x 4)
+        const int CH = 8;                  // ket positions per task
         for (int k = b0; k < b1; ++k) {
             int sp = pc.bra_order[k];
             for (int q = 0; q < h_prefix[sp]; q += CH) tk.push_back({sp, q, std::min(h_prefix[sp], q + CH)});
