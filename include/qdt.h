@@ -158,6 +158,54 @@ int qdt_transform(qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end, double 
  */
 int qdt_unpack(qdt_ctx *ctx, const double *packed, int n_kramers, unsigned block, double *full);
 
+/* ------------------------------------------------------------------ batches
+ * Several transformations as one batch: after each request's screening (run
+ * on its own context's stream), the kept shell-quartet tiles of all requests
+ * are fused into one persistent launch of the integral kernel per kernel kind
+ * (Coulomb kernel; gauge kernel) over a shared tile queue, most expensive
+ * tiles first, and every request's first half, second half and packing then
+ * run concurrently on its own stream.  The result of each item equals that of
+ * qdt_transform with the same arguments to rounding (the fused launch sizes
+ * its shared-memory plan for the largest request, which can regroup the
+ * primitive sums).  A request whose integral rows do not fit in one row batch
+ * runs alone after the fused ones.  The paper computes one system at a time;
+ * batching is this library's addition.
+ *
+ * flags: 0, or QDT_BATCH_GRAPH: the launch sequence after screening is
+ * captured into a CUDA graph the second time the same batch is seen (same
+ * contexts, arguments, device buffers and screening outcome) and the graph is
+ * replayed from the third time on; the first sighting runs the sequence
+ * directly so that every buffer reaches its size before capture.  The graph
+ * belongs to the first item's context (its stream carries the fused launches)
+ * and is replaced when a different batch is seen.
+ *
+ * items: n >= 1 entries; every ctx distinct, non-NULL, on the same device, with
+ * basis and coefficients set.  Each item's fields mean what qdt_transform's
+ * arguments mean; `status` receives that item's own result and `stats`
+ * (nullable) its statistics, whose ms_total is the whole batch's time and
+ * whose per-phase times are 0 for fused items.  Returns QDT_OK when every
+ * item succeeded, else the first failing item's code; qdt_last_error(item
+ * ctx) describes that item's failure.  Synchronises every item's stream.
+ */
+#define QDT_BATCH_GRAPH 1u
+
+typedef struct {
+    qdt_ctx *ctx;
+    unsigned blocks;
+    int k_begin, k_end;
+    double schwarz_tau;
+    int precision;
+    double *out;                    /* host or device, qdt_packed_size bytes */
+    size_t out_bytes;
+    qdt_stats *stats;               /* nullable                              */
+    int status;                     /* written by the call                   */
+} qdt_batch_item;
+
+int qdt_transform_batch(qdt_batch_item *items, int n, unsigned flags);
+
+/* Graphs captured and replayed by batches this context owned (diagnostics). */
+int qdt_graph_counts(const qdt_ctx *ctx, long long *captures, long long *replays);
+
 /* ------------------------------------------------------------------ serving
  * A server runs transformation requests of different basis and active-space
  * sizes on one GPU with continuous batching: `n_slots` contexts, each with its

@@ -379,69 +379,85 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
     }
 }
 
-// Screened rows: one CTA per task (bra shell pair x range of sorted ket positions).
+// Screened rows as a persistent kernel: every CTA builds its tables once, then
+// takes tiles (bra shell pair x range of sorted ket positions) from the shared
+// counter until none are left.  A tile's parameter set comes from prms[req],
+// so one launch can mix the tiles of several transformations.
 template <bool GAUGE>
-__global__ void __launch_bounds__(256, 2) eri_rows_kernel(EriParams prm, const EriTask *tasks, Plan pl) {
+__global__ void __launch_bounds__(256, 2) eri_rows_kernel(const EriParams *prms, const EriTask *tasks, int ntasks,
+                                                          int *next, Plan pl) {
     extern __shared__ double sm[];
-    const EriTask tk = tasks[blockIdx.x];
-    const PairDev AB = prm.pairs[tk.bra_sp];
     BlockSmem b = carve(sm, pl);
+    int *slot = b.src + pl.nTab;                     // in the plan's 16 spare bytes
     build_tables(pl, b);
     const int ij_of[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-    for (int kp = tk.k0; kp < tk.k1; ++kp) {
-        const int cd_id = prm.ket_sp[kp];
-        const PairDev CD = prm.pairs[cd_id];
-        const long long col = prm.ket_col[kp];
-        // (CD|AB) also kept?  Then the lower pair id computes both blocks.
-        const bool rev = prm.sym && cd_id != tk.bra_sp && prm.ket_pos[tk.bra_sp] < prm.prefix[cd_id];
-        if (rev && cd_id < tk.bra_sp) continue;
-        const long long col_rev = rev ? prm.ket_col[prm.ket_pos[tk.bra_sp]] : 0;
-        // contract the orientation with the smaller cost; swapped -> G is (CD|AB)
-        const bool swap = orient_cost(CD, AB) < orient_cost(AB, CD);
-        const PairDev &X = swap ? CD : AB, &Y = swap ? AB : CD;
-        for (int x0 = 0; x0 < X.nfp; x0 += pl.ach) {
-            const int x1 = min(X.nfp, x0 + pl.ach);
-            for (int y0 = 0; y0 < Y.nfp; y0 += pl.cch) {
-                const int y1 = min(Y.nfp, y0 + pl.cch);
-                block_chunk<GAUGE>(prm.pp, prm.E, prm.boys, X, Y, x0, x1, y0, y1, pl, b);
-                const int xch = x1 - x0, ych = y1 - y0;
-                for (int idx = threadIdx.x; idx < xch * ych; idx += blockDim.x) {
-                    const int xx = idx / ych, yy = idx - xx * ych;
-                    const int a = swap ? y0 + yy : x0 + xx;      // bra function pair
-                    const int c = swap ? x0 + xx : y0 + yy;      // ket function pair
-                    const long long row = AB.rowoff + a - prm.row0;
-                    const long long cc = col + c;
-                    if (!GAUGE) {
-                        prm.W[row * prm.ldw + cc] = b.G[idx];
-                    } else {
-                        const double C = b.G[idx];
-                        const double *Hh = b.G + (size_t)xch * ych;
-                        for (int I = 0; I < 3; ++I)
-                            for (int J = 0; J < 3; ++J) {
-                                // K_IJ is symmetric, so the swapped block needs no index change
-                                const double h = Hh[(size_t)ij_of[I][J] * xch * ych + idx];
-                                prm.W[(row * 3 + I) * prm.ldw + cc * 3 + J] = (I == J ? C : 0.0) - h;
-                            }
-                        if (prm.with_coulomb) prm.Wc[row * prm.ldwc + cc] = C;
-                    }
-                    if (rev) {    // the same integrals at (cd, ab): rows of CD, columns of AB
-                        const long long row2 = CD.rowoff + c - prm.row0;
-                        const long long cc2 = col_rev + a;
+    for (;;) {
+        if (threadIdx.x == 0) *slot = atomicAdd(next, 1);
+        __syncthreads();
+        const int t = *slot;
+        __syncthreads();
+        if (t >= ntasks) break;
+        const EriTask tk = tasks[t];
+        const EriParams &prm = prms[tk.req];
+        const PairDev AB = prm.pairs[tk.bra_sp];
+        for (int kp = tk.k0; kp < tk.k1; ++kp) {
+            const int cd_id = prm.ket_sp[kp];
+            const PairDev CD = prm.pairs[cd_id];
+            const long long col = prm.ket_col[kp];
+            // (CD|AB) also kept?  Then the lower pair id computes both blocks.
+            const bool rev = prm.sym && cd_id != tk.bra_sp && prm.ket_pos[tk.bra_sp] < prm.prefix[cd_id];
+            if (rev && cd_id < tk.bra_sp) continue;
+            const long long col_rev = rev ? prm.ket_col[prm.ket_pos[tk.bra_sp]] : 0;
+            // contract the orientation with the smaller cost; swapped -> G is (CD|AB)
+            const bool swap = orient_cost(CD, AB) < orient_cost(AB, CD);
+            const PairDev &X = swap ? CD : AB, &Y = swap ? AB : CD;
+            double *W = prm.W, *Wc = prm.Wc;
+            const long long ldw = prm.ldw, ldwc = prm.ldwc, row0 = prm.row0;
+            const bool wc = prm.with_coulomb != 0;
+            for (int x0 = 0; x0 < X.nfp; x0 += pl.ach) {
+                const int x1 = min(X.nfp, x0 + pl.ach);
+                for (int y0 = 0; y0 < Y.nfp; y0 += pl.cch) {
+                    const int y1 = min(Y.nfp, y0 + pl.cch);
+                    block_chunk<GAUGE>(prm.pp, prm.E, prm.boys, X, Y, x0, x1, y0, y1, pl, b);
+                    const int xch = x1 - x0, ych = y1 - y0;
+                    for (int idx = threadIdx.x; idx < xch * ych; idx += blockDim.x) {
+                        const int xx = idx / ych, yy = idx - xx * ych;
+                        const int a = swap ? y0 + yy : x0 + xx;      // bra function pair
+                        const int c = swap ? x0 + xx : y0 + yy;      // ket function pair
+                        const long long row = AB.rowoff + a - row0;
+                        const long long cc = col + c;
                         if (!GAUGE) {
-                            prm.W[row2 * prm.ldw + cc2] = b.G[idx];
+                            W[row * ldw + cc] = b.G[idx];
                         } else {
                             const double C = b.G[idx];
                             const double *Hh = b.G + (size_t)xch * ych;
                             for (int I = 0; I < 3; ++I)
                                 for (int J = 0; J < 3; ++J) {
+                                    // K_IJ is symmetric, so the swapped block needs no index change
                                     const double h = Hh[(size_t)ij_of[I][J] * xch * ych + idx];
-                                    prm.W[(row2 * 3 + I) * prm.ldw + cc2 * 3 + J] = (I == J ? C : 0.0) - h;
+                                    W[(row * 3 + I) * ldw + cc * 3 + J] = (I == J ? C : 0.0) - h;
                                 }
-                            if (prm.with_coulomb) prm.Wc[row2 * prm.ldwc + cc2] = C;
+                            if (wc) Wc[row * ldwc + cc] = C;
+                        }
+                        if (rev) {    // the same integrals at (cd, ab): rows of CD, columns of AB
+                            const long long row2 = CD.rowoff + c - row0;
+                            const long long cc2 = col_rev + a;
+                            if (!GAUGE) {
+                                W[row2 * ldw + cc2] = b.G[idx];
+                            } else {
+                                const double C = b.G[idx];
+                                const double *Hh = b.G + (size_t)xch * ych;
+                                for (int I = 0; I < 3; ++I)
+                                    for (int J = 0; J < 3; ++J) {
+                                        const double h = Hh[(size_t)ij_of[I][J] * xch * ych + idx];
+                                        W[(row2 * 3 + I) * ldw + cc2 * 3 + J] = (I == J ? C : 0.0) - h;
+                                    }
+                                if (wc) Wc[row2 * ldwc + cc2] = C;
+                            }
                         }
                     }
+                    __syncthreads();
                 }
-                __syncthreads();
             }
         }
     }
@@ -485,19 +501,40 @@ Plan eri_plan(int maxnfp, int maxLab, int maxnpp, bool gauge) {
     return p;
 }
 
-void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxnfp, int maxLab, int maxnpp,
-                cudaStream_t s) {
+int eri_default_threads(const EriShape &shape, bool gauge) {
+    return eri_plan(shape.maxnfp, shape.maxLab, shape.maxnpp, gauge).threads;
+}
+
+namespace {
+template <bool GAUGE>
+int resident_ctas(int threads, size_t smem) {
+    int nb = 0, dev = 0, nsm = 0;
+    QDT_CUDA_TRY(cudaGetDevice(&dev));
+    QDT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    QDT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eri_rows_kernel<GAUGE>, threads, smem));
+    return (nb > 0 ? nb : 1) * nsm;
+}
+
+template <bool GAUGE>
+void launch_rows(const EriParams *prms, const EriTask *tasks, int ntasks, int *next, const Plan &pl, int threads,
+                 size_t smem, cudaStream_t s) {
+    QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_kernel<GAUGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = min(ntasks, resident_ctas<GAUGE>(threads, smem));
+    QDT_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(int), s));
+    eri_rows_kernel<GAUGE><<<grid, threads, smem, s>>>(prms, tasks, ntasks, next, pl);
+}
+}  // namespace
+
+void launch_eri(const EriParams *prms, const EriTask *tasks, int ntasks, int *next, const EriShape &shape,
+                bool gauge, const EriLaunch &how, cudaStream_t s) {
     if (ntasks <= 0) return;
-    const Plan pl = eri_plan(maxnfp, maxLab, maxnpp, prm.gauge != 0);
+    const Plan pl = eri_plan(shape.maxnfp, shape.maxLab, shape.maxnpp, gauge);
     const size_t smem = plan_smem(pl);
-    if (prm.gauge) {
-        QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        eri_rows_kernel<true><<<ntasks, pl.threads, smem, s>>>(prm, tasks, pl);
-    } else {
-        QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        eri_rows_kernel<false><<<ntasks, pl.threads, smem, s>>>(prm, tasks, pl);
-    }
-    QDT_CHECK_LAUNCH();
+    const int threads = how.threads > 0 ? how.threads : pl.threads;
+    if (threads % 32 || threads > 256) throw Error{QDT_ERR_ARG, "integral kernel: threads must be 32..256, a multiple of 32"};
+    if (gauge) launch_rows<true>(prms, tasks, ntasks, next, pl, threads, smem, s);
+    else launch_rows<false>(prms, tasks, ntasks, next, pl, threads, smem, s);
+    QDT_CHECK_KERNEL("eri_rows_kernel");
 }
 
 // Schwarz diagonals: Q[AB] = max over ab of sqrt(|(ab|ab)|), Coulomb kernel.

@@ -42,7 +42,7 @@ constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
 constexpr long long kWaitNs = 2000000000LL;   // 2 s bound on every wait
 
 // ------------------------------------------------------------ workspace
-enum { WS_A = 0, WS_B0 = 1, WS_B1 = 2, WS_EXP = 3, WS_KT = 4, WS_ERR = 5, WS_A2 = 6, WS_B2 = 7 };
+enum { WS_A = 0, WS_B0 = 1, WS_B1 = 2, WS_EXP = 3, WS_KT = 4, WS_ERR = 5, WS_A2 = 6, WS_B2 = 7, WS_STAT = 8 };
 
 static void *ws_get(SplitWorkspace &w, int slot, size_t bytes) {
     if (w.bytes[slot] >= bytes && w.buf[slot]) return w.buf[slot];
@@ -59,7 +59,7 @@ static void *ws_get(SplitWorkspace &w, int slot, size_t bytes) {
 }
 
 void split_release(SplitWorkspace &w) {
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < SplitWorkspace::kSlots; ++i) {
         if (w.buf[i]) cudaFree(w.buf[i]);
         w.buf[i] = nullptr;
         w.bytes[i] = 0;
@@ -72,11 +72,31 @@ int split_slices(const SplitWorkspace &w) { return w.slices; }
 
 size_t split_held_bytes(const SplitWorkspace &w) {
     size_t b = 0;
-    for (int i = 0; i < 8; ++i) b += w.bytes[i];
+    for (int i = 0; i < SplitWorkspace::kSlots; ++i) b += w.bytes[i];
     return b;
 }
 
-void split_invalidate(SplitWorkspace &w) { w.bkey[0] = w.bkey[1] = SplitKey(); }
+void split_clear_status(SplitWorkspace &w, cudaStream_t s) {
+    QDT_CUDA_TRY(cudaMemsetAsync(ws_get(w, WS_STAT, 256), 0, 256, s));
+}
+
+void split_begin_deferred(SplitWorkspace &w, cudaStream_t s) {
+    split_clear_status(w, s);
+    w.deferred = true;
+}
+
+void split_end_deferred(SplitWorkspace &w, cudaStream_t s) {
+    w.deferred = false;
+    int h = 0;
+    QDT_CUDA_TRY(cudaMemcpyAsync(&h, ws_get(w, WS_STAT, 256), sizeof(int), cudaMemcpyDeviceToHost, s));
+    QDT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) throw Error{QDT_ERR_TIMEOUT, "split contraction: a bounded tensor-core wait gave up"};
+}
+
+void split_invalidate(SplitWorkspace &w) {
+    w.bkey[0] = w.bkey[1] = SplitKey();
+    w.bnext = 0;      // every class fills the slots in the same order, call after call
+}
 
 static inline long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
 
@@ -456,7 +476,8 @@ static void run_umma(SplitWorkspace &w, void *Asl, long long Mpad, long long Kpa
                      long long ldc, long long M, long long N, int upper, cudaStream_t s) {
     CUtensorMap ta = make_map(Asl, kSlices * Mpad, KpadA, SBM);
     CUtensorMap tb = make_map(Bsl, kSlices * Npad, KpadB, SBN);
-    int *status = (int *)((char *)ws_get(w, WS_KT, 0) + 0);  // status lives in front of the tile extents
+    int *status = (int *)ws_get(w, WS_STAT, 256);
+    if (!w.deferred) QDT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
     QDT_CUDA_TRY(cudaFuncSetAttribute(ozaki_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     dim3 grid((unsigned)(Npad / SBN), (unsigned)(Mpad / SBM));
     ozaki_umma_kernel<<<grid, 128, kSmemBytes, s>>>(ta, tb, Mpad, Npad, d_kt128, rowexp, colexp, C, ldc, M, N,
@@ -478,10 +499,30 @@ static void run_umma(SplitWorkspace &w, void *Asl, long long Mpad, long long Kpa
                  fa.numRegs, fa.maxThreadsPerBlock, optin, perblock, sizeof(CUtensorMap));
         throw Error{QDT_ERR_CUDA, msg};
     }
+    if (w.deferred) return;
     int h = 0;
     QDT_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     QDT_CUDA_TRY(cudaStreamSynchronize(s));
     if (h) throw Error{QDT_ERR_TIMEOUT, "split contraction: a bounded tensor-core wait gave up"};
+}
+
+// Extents of the 128-row tensor-core tiles: the maximum over the 64-row tiles
+// they cover, or one constant extent when kt64 is null.  Kept on the device so
+// that the contraction needs no host-to-device copy.
+__global__ void tile_extent_kernel(const long long *kt64, long long n64, int ratio, long long *kt, long long n,
+                                   long long constant) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    if (!kt64) {
+        kt[t] = constant;
+        return;
+    }
+    long long m = 0;
+    for (int r = 0; r < ratio; ++r) {
+        const long long i = t * ratio + r;
+        if (i < n64) m = max(m, kt64[i]);
+    }
+    kt[t] = m;
 }
 
 void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B, long long ldb,
@@ -502,11 +543,12 @@ void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda
         kmax = std::max(kmax, h_ktile[t]);
     }
     const long long KpadA = std::max<long long>(SBK, rup(std::min(kmax, lda), SBK));
-    // tile extents + status word
-    char *ktb = (char *)ws_get(w, WS_KT, 256 + kt.size() * sizeof(long long));
-    QDT_CUDA_TRY(cudaMemsetAsync(ktb, 0, 256, s));
-    long long *d_kt = (long long *)(ktb + 256);
-    QDT_CUDA_TRY(cudaMemcpyAsync(d_kt, kt.data(), kt.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+    // tile extents of the 128-row tiles, from the 64-row ones on the device
+    static_assert(SBM % 64 == 0, "tensor-core row tile must cover whole 64-row tiles");
+    long long *d_kt = (long long *)ws_get(w, WS_KT, std::max<size_t>(256, kt.size() * sizeof(long long)));
+    tile_extent_kernel<<<(unsigned)((kt.size() + 127) / 128), 128, 0, s>>>(d_ktile, (long long)h_ktile.size(),
+                                                                          SBM / TMr, d_kt, (long long)kt.size(), 0);
+    QDT_CHECK_KERNEL("tile_extent_kernel");
     // A slices (row scaled)
     int *rowexp = (int *)ws_get(w, WS_EXP, (size_t)(Mpad + Npad + 64) * sizeof(int) * 2);
     __nv_bfloat16 *Asl = (__nv_bfloat16 *)ws_get(w, WS_A, (size_t)kSlices * Mpad * KpadA * 2);
@@ -548,11 +590,10 @@ void gemm_half2(SplitWorkspace &w, int precision, const double *A, long long lda
     int *aexp = exps, *bexp = exps + Mpad + 32;
     slice_cols(w, WS_A2, A, lda, K, N, Kpad, Mpad, aexp, s);
     slice_cols(w, WS_B2, B, ldb, K, N, Kpad, Npad, bexp, s);
-    std::vector<long long> kt((size_t)(Mpad / SBM), K);
-    char *ktb = (char *)ws_get(w, WS_KT, 256 + kt.size() * sizeof(long long));
-    QDT_CUDA_TRY(cudaMemsetAsync(ktb, 0, 256, s));
-    long long *d_kt = (long long *)(ktb + 256);
-    QDT_CUDA_TRY(cudaMemcpyAsync(d_kt, kt.data(), kt.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+    const long long nkt = Mpad / SBM;
+    long long *d_kt = (long long *)ws_get(w, WS_KT, std::max<size_t>(256, (size_t)nkt * sizeof(long long)));
+    tile_extent_kernel<<<(unsigned)((nkt + 127) / 128), 128, 0, s>>>(nullptr, 0, 1, d_kt, nkt, K);
+    QDT_CHECK_KERNEL("tile_extent_kernel");
     // the split kernel overwrites C; C = A^T B is the whole second half here
     run_umma(w, w.buf[WS_A2], Mpad, Kpad, w.buf[WS_B2], Npad, Kpad, d_kt, aexp, bexp, C, N, N, N, 1, s);
 }

@@ -12,10 +12,13 @@
 //   5. pack the canonical Kramers quadruples.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "qdt_internal.cuh"
@@ -71,6 +74,13 @@ struct ClassBufs {
     DBuf pairs, pp, E, Q, bra, pp_pair;
 };
 
+// Instantiated graph of a batch round and the signature it was captured for.
+struct GraphEntry {
+    uint64_t sig = 0;
+    int seen = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
 }  // namespace
 
 struct qdt_ctx {
@@ -93,10 +103,15 @@ struct qdt_ctx {
     std::vector<int> smap0, smap1;
     // per-transform workspace
     DBuf Dbra, Dket, V, Vg, W, Wc, Dmax, wsort, ketsp, ketcol, prefix, ktile, tasks, O, partial,
-        stage, rsR, rsS, kpos;
+        stage, rsR, rsS, kpos, prms, next, ktile2;
     SplitWorkspace split;
     cudaEvent_t ev[16];
     int launches = 0;
+    // batches owned by this context (its stream carries the fused launches)
+    DBuf bprms[2], btasks[2], bnext[2];
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    GraphEntry graph[2];
+    long long graph_captures = 0, graph_replays = 0;
 };
 
 namespace {
@@ -122,6 +137,120 @@ int lcart(int l) { return (l + 1) * (l + 2) / 2; }
 double orient_cost_h(const PairDev &X, const PairDev &Y) {
     double nhx = nherm(X.Lab), nhy = nherm(Y.Lab);
     return (double)X.npp * Y.npp * nhx * Y.nfp * nhy + (double)X.npp * X.nfp * Y.nfp * nhx;
+}
+
+// Cost proxy of the tiles of a bra pair: primitive pairs x Hermite terms x
+// function pairs.
+double bra_cost(const PairDev &p) { return (double)p.npp * nherm(p.Lab) * p.nfp; }
+
+// Bra pairs of a list in tile order: as given (the bra order, Schwarz Q
+// descending) or most expensive first, so that the tile queue ends on cheap
+// tiles.
+std::vector<int> tile_order(const PairClass &pc, std::vector<int> v, int order) {
+    if (order == 1)
+        std::stable_sort(v.begin(), v.end(),
+                         [&](int a, int b) { return bra_cost(pc.h_pairs[a]) > bra_cost(pc.h_pairs[b]); });
+    return v;
+}
+
+// Tiles: each bra pair's kept ket prefix cut into runs of `kets` positions.
+void build_tiles(const std::vector<int> &bras, const std::vector<int> &prefix, int kets, int req,
+                 std::vector<EriTask> &out) {
+    for (int sp : bras)
+        for (int q = 0; q < prefix[sp]; q += kets) out.push_back({sp, q, std::min(prefix[sp], q + kets), req});
+}
+
+// ---------------------------------------------------------------- autotuner
+// Launch shape of the integral kernel per class signature (kernel kind and
+// class maxima), chosen by timing on a sample of the class: every 8th bra
+// pair of the bra order (an eighth of the work, so that every candidate runs
+// many tiles per CTA slot).  The search is coordinate-wise from (plan threads,
+// 8 kets, bra order), the start point timed twice (warm): ket
+// positions per tile {4, 8, 16}, then CTA threads {128, 256}, then the tile
+// order.  The candidates differ only in how the work is cut and scheduled,
+// never in the arithmetic of an integral, so the choice changes no result bit.
+// Process-wide cache; QDT_AUTOTUNE=0 keeps the start point, QDT_AUTOTUNE_VERBOSE=1
+// prints every timing to stderr, QDT_ERI_LAUNCH="threads,kets,order" pins the
+// shape for every class.
+struct TuneKey {
+    int dev, gauge, maxnfp, maxLab, maxnpp;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(dev, gauge, maxnfp, maxLab, maxnpp) < std::tie(o.dev, o.gauge, o.maxnfp, o.maxLab, o.maxnpp);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, EriLaunch> g_tune;
+
+bool env_flag(const char *name, bool dflt) {
+    const char *e = std::getenv(name);
+    if (!e || !e[0]) return dflt;
+    return e[0] != '0';
+}
+
+EriLaunch eri_launch_for(qdt_ctx *ctx, const PairClass &pc, const EriShape &shape, bool gauge,
+                         const EriParams *d_prm, const std::vector<int> &bras, const std::vector<int> &prefix,
+                         cudaStream_t s) {
+    EriLaunch def;
+    def.threads = eri_default_threads(shape, gauge);
+    def.kets = 8;
+    def.order = 0;
+    if (const char *pin = std::getenv("QDT_ERI_LAUNCH")) {
+        EriLaunch p = def;
+        if (std::sscanf(pin, "%d,%d,%d", &p.threads, &p.kets, &p.order) == 3 && p.threads > 0 && p.kets > 0)
+            return p;
+        throw Error{QDT_ERR_ARG, "QDT_ERI_LAUNCH must read threads,kets,order"};
+    }
+    if (!env_flag("QDT_AUTOTUNE", true)) return def;
+    const bool verbose = env_flag("QDT_AUTOTUNE_VERBOSE", false);
+    const TuneKey key{ctx->device, gauge ? 1 : 0, shape.maxnfp, shape.maxLab, shape.maxnpp};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    int nsm = 0;
+    QDT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    long long total = 0;
+    for (int sp : bras) total += prefix[sp];
+    // too little work to tell the candidates apart: fewer than ~64 tiles per CTA slot in the sample
+    if (total / 8 < 64LL * 8 * 4 * nsm) return def;
+    std::vector<int> sample;
+    for (size_t i = 0; i < bras.size(); i += 8) sample.push_back(bras[i]);
+    cudaEvent_t e0, e1;
+    QDT_CUDA_TRY(cudaEventCreate(&e0));
+    QDT_CUDA_TRY(cudaEventCreate(&e1));
+    int *next = (int *)ctx->next.get(sizeof(int));
+    auto time_of = [&](const EriLaunch &how) {
+        std::vector<EriTask> tk;
+        build_tiles(tile_order(pc, sample, how.order), prefix, how.kets, 0, tk);
+        EriTask *d_tk = dcopy(ctx->tasks, tk, s);
+        QDT_CUDA_TRY(cudaEventRecord(e0, s));
+        launch_eri(d_prm, d_tk, (int)tk.size(), next, shape, gauge, how, s);
+        QDT_CUDA_TRY(cudaEventRecord(e1, s));
+        QDT_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        QDT_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (verbose)
+            std::fprintf(stderr, "qdt autotune %s nfp %d L %d npp %d: threads %d kets %d order %d -> %.3f ms\n",
+                         gauge ? "gauge" : "coulomb", shape.maxnfp, shape.maxLab, shape.maxnpp, how.threads,
+                         how.kets, how.order, ms);
+        return ms;
+    };
+    EriLaunch best = def;
+    time_of(best);                        // warm-up (module load, first-touch of the tables)
+    float best_ms = time_of(best);
+    auto consider = [&](EriLaunch c) {
+        const float ms = time_of(c);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    };
+    for (int k : {4, 16}) { EriLaunch c = best; c.kets = k; consider(c); }
+    { EriLaunch c = best; c.threads = best.threads == 128 ? 256 : 128; consider(c); }
+    { EriLaunch c = best; c.order = 1; consider(c); }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+    return best;
 }
 
 // Build the shell-pair tables of class `c` (0: LL+SS, 1: LS); pairs in natural
@@ -213,13 +342,14 @@ void build_class(qdt_ctx *ctx, int c) {
 struct Timer {
     qdt_ctx *c;
     int n = 0;
-    explicit Timer(qdt_ctx *cc) : c(cc) {}
+    bool on = true;
+    explicit Timer(qdt_ctx *cc, bool enabled = true) : c(cc), on(enabled) {}
     void mark() {
-        if (n < 16) QDT_CUDA_TRY(cudaEventRecord(c->ev[n++], c->stream));
+        if (on && n < 16) QDT_CUDA_TRY(cudaEventRecord(c->ev[n++], c->stream));
     }
     double ms(int a, int b) {
         float t = 0.f;
-        if (a < n && b < n && cudaEventElapsedTime(&t, c->ev[a], c->ev[b]) != cudaSuccess) {
+        if (on && a < n && b < n && cudaEventElapsedTime(&t, c->ev[a], c->ev[b]) != cudaSuccess) {
             cudaGetLastError();   // a timing failure must not surface as a later launch error
             t = 0.f;
         }
@@ -227,24 +357,46 @@ struct Timer {
     }
 };
 
-// One block class of a transformation.  Returns the device pointer of the
-// packed block written into `outp`.
+// One block class of a transformation.
 struct ClassRun {
     int c;                  // pair class
     bool coulomb = false, gaunt = false, gauge = false;
 };
 
-void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, int precision,
-               double *out_coul, double *out_gaunt, double *out_gauge, qdt_stats *st, Timer &tm,
-               double acc_ms[6]) {
+// Screening outcome and device operands of one class of a transformation.
+struct ClassPlan {
+    ClassRun cr{};
+    int k0 = 0, nKa = 0, precision = 0, nRS = 0, mult = 1;
+    double tau = 0;
+    bool ls = false, one_batch = true;
+    long long N4 = 0, ncolD = 0, M = 0, NV = 0;
+    double *Dbra = nullptr, *Dmax = nullptr, *Dket = nullptr, *Vc = nullptr, *Vg = nullptr;
+    int *prefix = nullptr, *ketsp = nullptr, *d_kpos = nullptr;
+    long long *ketcol = nullptr;
+    std::vector<int> h_prefix, h_ketsp, h_kpos;
+    std::vector<long long> h_col, Krow;
+    size_t wbudget = 0;
+};
+
+// Steps 1-3 on the context's stream: density in bra order and Dmax, ket order
+// and kept prefixes (copied to the host), ket-ordered density copy.
+void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, int precision, ClassPlan &P,
+                 Timer &tm) {
     PairClass &pc = ctx->cls[cr.c];
     cudaStream_t s = ctx->stream;
-    const int nRS = nKa * (nKa + 1) / 2;
-    const bool ls = cr.c == 1;
-    const long long N4 = 4LL * nRS;              // columns per J component
-    const long long ncolD = ls ? 3 * N4 : N4;     // density row length
-    const long long M = pc.M;
-    // Kramers pair list
+    P = ClassPlan();
+    P.cr = cr;
+    P.k0 = k0;
+    P.nKa = nKa;
+    P.tau = tau;
+    P.precision = precision;
+    P.nRS = nKa * (nKa + 1) / 2;
+    P.ls = cr.c == 1;
+    P.N4 = 4LL * P.nRS;                          // columns per J component
+    P.ncolD = P.ls ? 3 * P.N4 : P.N4;            // density row length
+    P.NV = P.ls ? 3 * P.N4 : P.N4;               // V row length (Coulomb / Gaunt)
+    P.M = pc.M;
+    P.mult = (P.ls && cr.gauge) ? 3 : 1;         // gauge rows/cols are (pair, I)
     std::vector<int> hR, hS;
     for (int r = 0; r < nKa; ++r)
         for (int q = r; q < nKa; ++q) { hR.push_back(r); hS.push_back(q); }
@@ -252,231 +404,301 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
     split_invalidate(ctx->split);
 
     // 1. density in bra order + Dmax
-    int t0 = tm.n; tm.mark();
-    double *Dbra = (double *)ctx->Dbra.get(std::max<long long>(1, M * ncolD) * sizeof(double));
-    double *Dmax = (double *)ctx->Dmax.get(std::max(1, pc.nsp) * sizeof(double));
-    QDT_CUDA_TRY(cudaMemsetAsync(Dmax, 0, pc.nsp * sizeof(double), s));
-    launch_density(ls, pc.d_pairs, pc.d_bra_order, pc.nsp, (const ShellDev *)ctx->shells.p,
-                   (const double *)ctx->Cq.p, ctx->nK, k0, d_rsR, d_rsS, nRS, Dbra, Dmax, s);
+    tm.mark();
+    P.Dbra = (double *)ctx->Dbra.get(std::max<long long>(1, P.M * P.ncolD) * sizeof(double));
+    P.Dmax = (double *)ctx->Dmax.get(std::max(1, pc.nsp) * sizeof(double));
+    QDT_CUDA_TRY(cudaMemsetAsync(P.Dmax, 0, pc.nsp * sizeof(double), s));
+    launch_density(P.ls, pc.d_pairs, pc.d_bra_order, pc.nsp, (const ShellDev *)ctx->shells.p,
+                   (const double *)ctx->Cq.p, ctx->nK, k0, d_rsR, d_rsS, P.nRS, P.Dbra, P.Dmax, s);
     ctx->launches++;
     tm.mark();
     // 2. ket order and prefixes
     double *wsort = (double *)ctx->wsort.get(std::max(1, pc.nsp) * sizeof(double));
-    int *ketsp = (int *)ctx->ketsp.get(std::max(1, pc.nsp) * sizeof(int));
-    long long *ketcol = (long long *)ctx->ketcol.get((pc.nsp + 1) * sizeof(long long));
-    int *prefix = (int *)ctx->prefix.get(std::max(1, pc.nsp) * sizeof(int));
-    launch_ket_order(pc.d_Q, Dmax, pc.nsp, wsort, ketsp, s);
-    launch_ket_columns(pc.d_pairs, ketsp, pc.nsp, ketcol, s);
-    launch_prefix_lengths(pc.d_Q, wsort, pc.nsp, tau, prefix, s);
+    P.ketsp = (int *)ctx->ketsp.get(std::max(1, pc.nsp) * sizeof(int));
+    P.ketcol = (long long *)ctx->ketcol.get((pc.nsp + 1) * sizeof(long long));
+    P.prefix = (int *)ctx->prefix.get(std::max(1, pc.nsp) * sizeof(int));
+    launch_ket_order(pc.d_Q, P.Dmax, pc.nsp, wsort, P.ketsp, s);
+    launch_ket_columns(pc.d_pairs, P.ketsp, pc.nsp, P.ketcol, s);
+    launch_prefix_lengths(pc.d_Q, wsort, pc.nsp, tau, P.prefix, s);
     ctx->launches += 3;
-    std::vector<int> h_prefix(pc.nsp);
-    std::vector<long long> h_col(pc.nsp + 1);
-    QDT_CUDA_TRY(cudaMemcpyAsync(h_prefix.data(), prefix, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
-    QDT_CUDA_TRY(cudaMemcpyAsync(h_col.data(), ketcol, (pc.nsp + 1) * sizeof(long long), cudaMemcpyDeviceToHost, s));
-    std::vector<int> h_ketsp(pc.nsp);
-    QDT_CUDA_TRY(cudaMemcpyAsync(h_ketsp.data(), ketsp, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
+    P.h_prefix.resize(pc.nsp);
+    P.h_col.resize(pc.nsp + 1);
+    P.h_ketsp.resize(pc.nsp);
+    QDT_CUDA_TRY(cudaMemcpyAsync(P.h_prefix.data(), P.prefix, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
+    QDT_CUDA_TRY(cudaMemcpyAsync(P.h_col.data(), P.ketcol, (pc.nsp + 1) * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    QDT_CUDA_TRY(cudaMemcpyAsync(P.h_ketsp.data(), P.ketsp, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
     // 3. ket-ordered density copy
-    double *Dket = (double *)ctx->Dket.get(std::max<long long>(1, M * ncolD) * sizeof(double));
-    launch_gather_rows(Dbra, pc.d_pairs, ketsp, ketcol, pc.nsp, ncolD, Dket, s);
+    P.Dket = (double *)ctx->Dket.get(std::max<long long>(1, P.M * P.ncolD) * sizeof(double));
+    launch_gather_rows(P.Dbra, pc.d_pairs, P.ketsp, P.ketcol, pc.nsp, P.ncolD, P.Dket, s);
     ctx->launches++;
-    QDT_CUDA_TRY(cudaStreamSynchronize(s));
     tm.mark();
+}
+
+// Waits for class_issue; kept-quartet statistics, V buffers and the row-batch
+// decision: one batch (and bra-ket symmetry) when the integral block and its
+// digit planes fit in 70 % of the device memory this context can use, else
+// batches of at most 6 GB.
+void class_finish(qdt_ctx *ctx, ClassPlan &P, qdt_stats *st) {
+    PairClass &pc = ctx->cls[P.cr.c];
+    cudaStream_t s = ctx->stream;
+    QDT_CUDA_TRY(cudaStreamSynchronize(s));
     long long kept = 0;
-    for (int i = 0; i < pc.nsp; ++i) kept += h_prefix[i];
+    for (int i = 0; i < pc.nsp; ++i) kept += P.h_prefix[i];
     if (st) {
-        int slot = ls ? 1 : 0;
+        int slot = P.ls ? 1 : 0;
         st->quartets_total[slot] += (long long)pc.nsp * pc.nsp;
         st->quartets_kept[slot] += kept;
-        if (ls && cr.gauge) {
+        if (P.ls && P.cr.gauge) {
             st->quartets_total[2] += (long long)pc.nsp * pc.nsp;
             st->quartets_kept[2] += kept;
         }
     }
-
-    // 4. batches of bra rows
-    const int TMr = gemm_fp64_tile_m();
-    // per-row K: K of its shell pair
-    std::vector<long long> Krow_pair(pc.nsp);
-    for (int i = 0; i < pc.nsp; ++i) Krow_pair[i] = h_col[h_prefix[i]];
-    const long long NV = ls ? 3 * N4 : N4;              // V row length (Coulomb / Gaunt)
-    double *Vc = nullptr, *Vg = nullptr;
-    if (!ls || cr.gaunt) Vc = (double *)ctx->V.get(std::max<long long>(1, M * NV) * sizeof(double));
-    if (ls && cr.gauge) Vg = (double *)ctx->Vg.get(std::max<long long>(1, 3 * M * N4) * sizeof(double));
-    const long long Kfull = h_col[pc.nsp];
-    const int mult = (ls && cr.gauge) ? 3 : 1;          // gauge rows/cols are (pair, I)
-    // one batch (and bra-ket symmetry) when all integral rows fit comfortably,
-    // else batches of at most 6 GB
-    size_t wall = 0;
-    {
-        long long kmax_all = 0;
-        for (int i = 0; i < pc.nsp; ++i) kmax_all = std::max(kmax_all, Krow_pair[i]);
-        wall = (size_t)M * mult * (size_t)std::max<long long>(kmax_all, 1) * mult * sizeof(double);
-    }
-    // all rows at once (bra-ket symmetry) when the integral block and its digit
-    // planes fit in 70 % of the device memory this context can use
+    P.Krow.assign(pc.nsp, 0);
+    for (int i = 0; i < pc.nsp; ++i) P.Krow[i] = P.h_col[P.h_prefix[i]];
+    if (!P.ls || P.cr.gaunt) P.Vc = (double *)ctx->V.get(std::max<long long>(1, P.M * P.NV) * sizeof(double));
+    if (P.ls && P.cr.gauge) P.Vg = (double *)ctx->Vg.get(std::max<long long>(1, 3 * P.M * P.N4) * sizeof(double));
+    long long kmax_all = 0;
+    for (int i = 0; i < pc.nsp; ++i) kmax_all = std::max(kmax_all, P.Krow[i]);
+    const size_t wall = (size_t)P.M * P.mult * (size_t)std::max<long long>(kmax_all, 1) * P.mult * sizeof(double);
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
     const size_t usable = (size_t)(0.7 * (double)(fr + ctx->W.n + ctx->Wc.n + split_held_bytes(ctx->split)));
-    const double wfac = (precision == QDT_SPLIT ? 2.5 : 1.0) * ((ls && cr.gauge && cr.gaunt) ? 1.12 : 1.0);
-    const bool one_batch = (double)wall * wfac <= (double)usable;
-    const size_t wbudget = one_batch ? wall : ((size_t)6 << 30);
-    std::vector<int> h_kpos(pc.nsp);
-    for (int q = 0; q < pc.nsp; ++q) h_kpos[h_ketsp[q]] = q;
-    int *d_kpos = one_batch ? dcopy(ctx->kpos, h_kpos, s) : nullptr;
+    const double wfac = (P.precision == QDT_SPLIT ? 2.5 : 1.0) * ((P.ls && P.cr.gauge && P.cr.gaunt) ? 1.12 : 1.0);
+    P.one_batch = (double)wall * wfac <= (double)usable;
+    P.wbudget = P.one_batch ? wall : ((size_t)6 << 30);
+    P.h_kpos.assign(pc.nsp, 0);
+    for (int q = 0; q < pc.nsp; ++q) P.h_kpos[P.h_ketsp[q]] = q;
+    P.d_kpos = P.one_batch ? dcopy(ctx->kpos, P.h_kpos, s) : nullptr;
+}
+
+// One batch of bra rows of a class.
+struct RowBatch {
+    int b0 = 0, b1 = 0;
+    long long rows = 0, kmax = 0, row0 = 0, ldw = 1, ldwc = 1;
+    double *W = nullptr, *Wc = nullptr;
+    EriParams prm{};
+    std::vector<int> bras;                  // the batch's bra pairs, in bra order
+    std::vector<long long> kt, kg;          // K extents of the 64-row tiles (gauge/Coulomb rows, Gaunt rows)
+    long long *d_kt = nullptr, *d_kg = nullptr;
+};
+
+// Next batch from bra position b0: sizes, integral-row buffers, the integral
+// kernel's parameters and the tile extents (uploaded to the context).
+void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
+    PairClass &pc = ctx->cls[P.cr.c];
+    cudaStream_t s = ctx->stream;
+    const int TMr = gemm_fp64_tile_m();
+    const int mult = P.mult;
+    B = RowBatch();
+    B.b0 = b0;
+    long long rows = 0, kmax = 0;
+    int b1 = b0;
+    while (b1 < pc.nsp) {      // grow the batch while the W block fits the budget
+        const PairDev &pr = pc.h_pairs[pc.bra_order[b1]];
+        long long k = std::max(kmax, P.Krow[pc.bra_order[b1]]);
+        size_t need = (size_t)(rows + pr.nfp) * mult * (size_t)std::max<long long>(k, 1) * mult * sizeof(double);
+        if (b1 > b0 && need > P.wbudget) break;
+        rows += pr.nfp;
+        kmax = k;
+        ++b1;
+    }
+    B.b1 = b1;
+    B.rows = rows;
+    B.kmax = kmax;
+    B.row0 = pc.h_pairs[pc.bra_order[b0]].rowoff;
+    B.ldw = std::max<long long>(kmax, 1) * mult;
+    B.W = (double *)ctx->W.get((size_t)std::max<long long>(rows, 1) * mult * B.ldw * sizeof(double));
+    B.ldwc = std::max<long long>(kmax, 1);
+    if (P.ls && P.cr.gauge && P.cr.gaunt) B.Wc = (double *)ctx->Wc.get((size_t)std::max<long long>(rows, 1) * B.ldwc * sizeof(double));
+    EriParams &prm = B.prm;
+    prm.shells = (const ShellDev *)ctx->shells.p;
+    prm.pairs = pc.d_pairs;
+    prm.pp = pc.d_pp;
+    prm.E = pc.d_E;
+    prm.boys = (const double *)ctx->boys.p;
+    prm.ket_sp = P.ketsp;
+    prm.ket_col = P.ketcol;
+    prm.W = B.W;
+    prm.ldw = B.ldw;
+    prm.row0 = B.row0;
+    prm.gauge = (P.ls && P.cr.gauge) ? 1 : 0;
+    prm.with_coulomb = B.Wc ? 1 : 0;
+    prm.Wc = B.Wc;
+    prm.ldwc = B.ldwc;
+    prm.sym = P.one_batch ? 1 : 0;
+    prm.ket_pos = P.d_kpos;
+    prm.prefix = P.prefix;
+    B.bras.assign(pc.bra_order.begin() + b0, pc.bra_order.begin() + b1);
+    // per-tile K extents (rows in units of W rows)
+    const long long Wrows = rows * mult;
+    B.kt.assign((Wrows + TMr - 1) / TMr, 0);
+    for (int k = b0; k < b1; ++k) {
+        const PairDev &pr = pc.h_pairs[pc.bra_order[k]];
+        long long r0 = (pr.rowoff - B.row0) * mult, r1 = (pr.rowoff - B.row0 + pr.nfp) * mult;
+        long long kk = P.Krow[pc.bra_order[k]] * mult;
+        for (long long t = r0 / TMr; t <= (r1 - 1) / TMr; ++t) B.kt[t] = std::max(B.kt[t], kk);
+    }
+    B.d_kt = dcopy(ctx->ktile, B.kt, s);
+    if (P.ls && P.cr.gaunt && P.cr.gauge) {
+        B.kg.assign((rows + TMr - 1) / TMr, 0);
+        for (int k = b0; k < b1; ++k) {
+            const PairDev &pr = pc.h_pairs[pc.bra_order[k]];
+            long long r0 = pr.rowoff - B.row0, r1 = r0 + pr.nfp;
+            for (long long t = r0 / TMr; t <= (r1 - 1) / TMr; ++t) B.kg[t] = std::max(B.kg[t], P.Krow[pc.bra_order[k]]);
+        }
+        B.d_kg = dcopy(ctx->ktile2, B.kg, s);
+    } else {
+        B.kg = B.kt;
+        B.d_kg = B.d_kt;
+    }
+}
+
+// Integral values, E R E flops and first-half flops of a batch.
+void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, qdt_stats *st) {
+    if (!st) return;
+    PairClass &pc = ctx->cls[P.cr.c];
+    const int TMr = gemm_fp64_tile_m();
+    long long v = 0;
+    double fl = 0.0;
+    const int NC = B.prm.gauge ? 7 : 1;
+    for (int k = B.b0; k < B.b1; ++k) {
+        int sp = pc.bra_order[k];
+        const PairDev &ab = pc.h_pairs[sp];
+        v += (long long)ab.nfp * P.Krow[sp];
+        // E R E contraction of every kept quartet: per primitive quartet
+        // 2 nha ncd nhc NC, per bra primitive pair 2 nab ncd nha NC.
+        for (int q = 0; q < P.h_prefix[sp]; ++q) {
+            const int cid = P.h_ketsp[q];
+            const PairDev &cd = pc.h_pairs[cid];
+            if (P.one_batch && cid < sp && P.h_kpos[sp] < P.h_prefix[cid]) continue;
+            fl += 2.0 * NC * std::min(orient_cost_h(ab, cd), orient_cost_h(cd, ab));
+        }
+    }
+    st->eri_values += v * (B.prm.gauge ? 6 : 1);
+    st->flops_eri += fl;
+    const long long Wrows = B.rows * P.mult;
+    double f = 0;
+    for (long long t = 0; t < (long long)B.kt.size(); ++t) f += (double)std::min<long long>(TMr, Wrows - t * TMr) * B.kt[t];
+    const double ncols = (double)(P.ls ? (P.cr.gauge ? P.N4 : 0) : P.N4);
+    st->flops_half1 += 2.0 * f * ncols;
+    if (P.ls && P.cr.gaunt) {
+        double fg = 0;
+        for (int k = B.b0; k < B.b1; ++k) fg += (double)pc.h_pairs[pc.bra_order[k]].nfp * P.Krow[pc.bra_order[k]];
+        st->flops_half1 += 2.0 * fg * 3 * P.N4;
+    }
+}
+
+// First half of a batch: V rows = W D_ket (launches only).
+void batch_half1(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, cudaStream_t s) {
+    const long long N4 = P.N4;
+    if (!P.ls) {
+        gemm_half1(ctx->split, P.precision, B.W, B.ldw, P.Dket, N4, P.Vc + B.row0 * N4, N4, B.rows, N4, B.d_kt, B.kt, s);
+        ctx->launches++;
+        return;
+    }
+    if (P.cr.gauge) {
+        // gauge: rows (ab, I), K (cd, J): D_ket viewed as [(cd, J)][4 nRS]
+        gemm_half1(ctx->split, P.precision, B.W, B.ldw, P.Dket, N4, P.Vg + B.row0 * 3 * N4, N4, B.rows * 3, N4,
+                   B.d_kt, B.kt, s);
+        ctx->launches++;
+    }
+    if (P.cr.gaunt) {
+        // Gaunt: Coulomb integrals over L-S pairs, N = 12 nRS
+        const double *Wg = P.cr.gauge ? B.Wc : B.W;
+        const long long ldg = P.cr.gauge ? B.ldwc : B.ldw;
+        gemm_half1(ctx->split, P.precision, Wg, ldg, P.Dket, 3 * N4, P.Vc + B.row0 * 3 * N4, 3 * N4, B.rows, 3 * N4,
+                   B.d_kg, B.kg, s);
+        ctx->launches++;
+    }
+}
+
+// Second-half operands of a class: the jobs (V, K, packed output) and buffers.
+struct Half2 {
+    struct Job { const double *V; long long K; double *out; };
+    std::vector<Job> jobs;
+    double *O = nullptr, *partial = nullptr;
+    size_t pe = 0;
+    long long NO = 0;
+};
+
+void half2_prepare(qdt_ctx *ctx, const ClassPlan &P, double *out_coul, double *out_gaunt, double *out_gauge,
+                   Half2 &H) {
+    H = Half2();
+    H.NO = 4LL * P.nRS;
+    H.O = (double *)ctx->O.get(std::max<long long>(1, H.NO * H.NO) * sizeof(double));
+    H.pe = (size_t)std::max<long long>(1, H.NO * H.NO) * 8;
+    if (H.pe * sizeof(double) > ((size_t)4 << 30))
+        H.pe = std::max<size_t>((size_t)H.NO * H.NO, ((size_t)4 << 30) / sizeof(double));
+    H.partial = (double *)ctx->partial.get(H.pe * sizeof(double));
+    if (!P.ls) H.jobs.push_back({P.Vc, P.M, out_coul});
+    if (P.ls && P.cr.gaunt) H.jobs.push_back({P.Vc, 3 * P.M, out_gaunt});
+    if (P.ls && P.cr.gauge) H.jobs.push_back({P.Vg, 3 * P.M, out_gauge});
+}
+
+// O = Dq^T V and packing of one job (launches only).
+void half2_job(qdt_ctx *ctx, const ClassPlan &P, const Half2 &H, const Half2::Job &j, cudaStream_t s) {
+    launch_zero(H.O, H.NO * H.NO, s);
+    gemm_half2(ctx->split, P.precision, P.Dbra, P.N4, j.V, P.N4, H.O, H.NO, j.K, H.partial, H.pe, s);
+    ctx->launches += 3;
+}
+
+void half2_pack(qdt_ctx *ctx, const ClassPlan &P, const Half2 &H, const Half2::Job &j, cudaStream_t s) {
+    launch_pack(H.O, H.NO, P.nKa, j.out, s);
+    ctx->launches++;
+}
+
+void half2_stats(const Half2 &H, qdt_stats *st) {
+    if (!st) return;
+    for (const Half2::Job &j : H.jobs) st->flops_half2 += 2.0 * (double)j.K * (H.NO * (H.NO + 1) / 2.0);
+}
+
+void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, int precision,
+               double *out_coul, double *out_gaunt, double *out_gauge, qdt_stats *st, Timer &tm,
+               double acc_ms[6]) {
+    PairClass &pc = ctx->cls[cr.c];
+    cudaStream_t s = ctx->stream;
+    ClassPlan P;
+    const int t0 = tm.n;
+    class_issue(ctx, cr, k0, nKa, tau, precision, P, tm);
+    class_finish(ctx, P, st);
+    // 4. batches of bra rows: integral rows, then the first half
     int b0 = 0;
     double ms_eri = 0, ms_h1 = 0;
     while (b0 < pc.nsp) {
-        // grow the batch while the W block fits the budget
-        long long rows = 0, kmax = 0;
-        int b1 = b0;
-        while (b1 < pc.nsp) {
-            const PairDev &pr = pc.h_pairs[pc.bra_order[b1]];
-            long long k = std::max(kmax, Krow_pair[pc.bra_order[b1]]);
-            size_t need = (size_t)(rows + pr.nfp) * mult * (size_t)std::max<long long>(k, 1) * mult * sizeof(double);
-            if (b1 > b0 && need > wbudget) break;
-            rows += pr.nfp;
-            kmax = k;
-            ++b1;
-        }
-        const long long row0 = pc.h_pairs[pc.bra_order[b0]].rowoff;
-        const long long ldw = std::max<long long>(kmax, 1) * mult;
-        double *W = (double *)ctx->W.get((size_t)rows * mult * ldw * sizeof(double));
-        double *Wc = nullptr;
-        long long ldwc = std::max<long long>(kmax, 1);
-        if (ls && cr.gauge && cr.gaunt) Wc = (double *)ctx->Wc.get((size_t)rows * ldwc * sizeof(double));
-        int te = tm.n; tm.mark();
-        launch_zero(W, rows * mult * ldw, s);
-        if (Wc) launch_zero(Wc, rows * ldwc, s);
-        // tasks: bra pair x chunks of its ket prefix
+        RowBatch B;
+        batch_prepare(ctx, P, b0, B);
+        const EriParams *d_prm = dcopy(ctx->prms, std::vector<EriParams>{B.prm}, s);
+        const EriShape shape{pc.maxnfp, pc.maxLab, pc.maxnpp};
+        const EriLaunch how = eri_launch_for(ctx, pc, shape, B.prm.gauge != 0, d_prm, B.bras, P.h_prefix, s);
         std::vector<EriTask> tk;
-        const int CH = 8;                  // ket positions per task
-        for (int k = b0; k < b1; ++k) {
-            int sp = pc.bra_order[k];
-            for (int q = 0; q < h_prefix[sp]; q += CH) tk.push_back({sp, q, std::min(h_prefix[sp], q + CH)});
-        }
+        build_tiles(tile_order(pc, B.bras, how.order), P.h_prefix, how.kets, 0, tk);
         EriTask *d_tk = dcopy(ctx->tasks, tk, s);
-        EriParams prm;
-        prm.shells = (const ShellDev *)ctx->shells.p;
-        prm.pairs = pc.d_pairs;
-        prm.pp = pc.d_pp;
-        prm.E = pc.d_E;
-        prm.boys = (const double *)ctx->boys.p;
-        prm.ket_sp = ketsp;
-        prm.ket_col = ketcol;
-        prm.W = W;
-        prm.ldw = ldw;
-        prm.row0 = row0;
-        prm.gauge = (ls && cr.gauge) ? 1 : 0;
-        prm.with_coulomb = Wc ? 1 : 0;
-        prm.Wc = Wc;
-        prm.ldwc = ldwc;
-        prm.sym = one_batch ? 1 : 0;
-        prm.ket_pos = d_kpos;
-        prm.prefix = prefix;
-        launch_eri(prm, d_tk, (int)tk.size(), pc.maxnfp, pc.maxLab, pc.maxnpp, s);
-        ctx->launches += 2 + (Wc ? 1 : 0);
-        if (st) {
-            long long v = 0;
-            double fl = 0.0;
-            const int NC = prm.gauge ? 7 : 1;
-            for (int k = b0; k < b1; ++k) {
-                int sp = pc.bra_order[k];
-                const PairDev &ab = pc.h_pairs[sp];
-                v += (long long)ab.nfp * Krow_pair[sp];
-                // E R E contraction of every kept quartet: per primitive quartet
-                // 2 nha ncd nhc NC, per bra primitive pair 2 nab ncd nha NC.
-                for (int q = 0; q < h_prefix[sp]; ++q) {
-                    const int cid = h_ketsp[q];
-                    const PairDev &cd = pc.h_pairs[cid];
-                    if (one_batch && cid < sp && h_kpos[sp] < h_prefix[cid]) continue;
-                    fl += 2.0 * NC * std::min(orient_cost_h(ab, cd), orient_cost_h(cd, ab));
-                }
-            }
-            st->eri_values += v * (prm.gauge ? 6 : 1);
-            st->flops_eri += fl;
-        }
+        int te = tm.n; tm.mark();
+        launch_zero(B.W, B.rows * P.mult * B.ldw, s);
+        if (B.Wc) launch_zero(B.Wc, B.rows * B.ldwc, s);
+        launch_eri(d_prm, d_tk, (int)tk.size(), (int *)ctx->next.get(sizeof(int)), shape, B.prm.gauge != 0, how, s);
+        ctx->launches += 2 + (B.Wc ? 1 : 0);
+        batch_stats(ctx, P, B, st);
         int th = tm.n; tm.mark();
-        // per-tile K extents (rows in units of W rows)
-        long long Wrows = rows * mult;
-        std::vector<long long> kt((Wrows + TMr - 1) / TMr, 0);
-        for (int k = b0; k < b1; ++k) {
-            const PairDev &pr = pc.h_pairs[pc.bra_order[k]];
-            long long r0 = (pr.rowoff - row0) * mult, r1 = (pr.rowoff - row0 + pr.nfp) * mult;
-            long long kk = Krow_pair[pc.bra_order[k]] * mult;
-            for (long long t = r0 / TMr; t <= (r1 - 1) / TMr; ++t) kt[t] = std::max(kt[t], kk);
-        }
-        long long *d_kt = dcopy(ctx->ktile, kt, s);
-        if (st) {
-            double f = 0;
-            for (long long t = 0; t < (long long)kt.size(); ++t) f += (double)std::min<long long>(TMr, Wrows - t * TMr) * kt[t];
-            double ncols = (double)(ls ? (cr.gauge ? N4 : 0) : N4);
-            st->flops_half1 += 2.0 * f * ncols;
-            if (ls && cr.gaunt) {
-                double fg = 0;
-                for (int k = b0; k < b1; ++k) {
-                    const PairDev &pr = pc.h_pairs[pc.bra_order[k]];
-                    fg += (double)pr.nfp * Krow_pair[pc.bra_order[k]];
-                }
-                st->flops_half1 += 2.0 * fg * 3 * N4;
-            }
-        }
-        if (!ls) {
-            gemm_half1(ctx->split, precision, W, ldw, Dket, N4, Vc + row0 * N4, N4, rows, N4, d_kt, kt, s);
-            ctx->launches++;
-        } else {
-            if (cr.gauge) {
-                // gauge: rows (ab, I), K (cd, J): D_ket viewed as [(cd, J)][4 nRS]
-                gemm_half1(ctx->split, precision, W, ldw, Dket, N4, Vg + row0 * 3 * N4, N4, rows * 3, N4, d_kt, kt, s);
-                ctx->launches++;
-            }
-            if (cr.gaunt) {
-                // Gaunt: Coulomb integrals over L-S pairs, N = 12 nRS
-                const double *Wg = cr.gauge ? Wc : W;
-                long long ldg = cr.gauge ? ldwc : ldw;
-                std::vector<long long> kg((rows + TMr - 1) / TMr, 0);
-                for (int k = b0; k < b1; ++k) {
-                    const PairDev &pr = pc.h_pairs[pc.bra_order[k]];
-                    long long r0 = pr.rowoff - row0, r1 = r0 + pr.nfp;
-                    for (long long t = r0 / TMr; t <= (r1 - 1) / TMr; ++t)
-                        kg[t] = std::max(kg[t], Krow_pair[pc.bra_order[k]]);
-                }
-                long long *d_kg = dcopy(ctx->ktile, kg, s);
-                gemm_half1(ctx->split, precision, Wg, ldg, Dket, 3 * N4, Vc + row0 * 3 * N4, 3 * N4, rows, 3 * N4, d_kg, kg, s);
-                ctx->launches++;
-            }
-        }
+        batch_half1(ctx, P, B, s);
         int tend = tm.n; tm.mark();
         QDT_CUDA_TRY(cudaStreamSynchronize(s));
         ms_eri += tm.ms(te, th);
         ms_h1 += tm.ms(th, tend);
         tm.n = te;   // reuse the batch's events
-        b0 = b1;
+        b0 = B.b1;
     }
     acc_ms[2] += ms_eri;
     acc_ms[3] += ms_h1;
-    (void)Kfull;
-
     // 5. second half + packing, one block at a time
-    const int nP = nRS;
-    const long long NO = 4LL * nP;
-    double *O = (double *)ctx->O.get(std::max<long long>(1, NO * NO) * sizeof(double));
-    size_t pe = (size_t)std::max<long long>(1, NO * NO) * 8;
-    if (pe * sizeof(double) > ((size_t)4 << 30)) pe = std::max<size_t>((size_t)NO * NO, ((size_t)4 << 30) / sizeof(double));
-    double *partial = (double *)ctx->partial.get(pe * sizeof(double));
-    struct Job { const double *V; long long K; double *out; };
-    std::vector<Job> jobs;
-    if (!ls) jobs.push_back({Vc, M, out_coul});
-    if (ls && cr.gaunt) jobs.push_back({Vc, 3 * M, out_gaunt});
-    if (ls && cr.gauge) jobs.push_back({Vg, 3 * M, out_gauge});
-    for (const Job &j : jobs) {
+    Half2 H;
+    half2_prepare(ctx, P, out_coul, out_gaunt, out_gauge, H);
+    half2_stats(H, st);
+    for (const Half2::Job &j : H.jobs) {
         int t2 = tm.n; tm.mark();
-        launch_zero(O, NO * NO, s);
-        gemm_half2(ctx->split, precision, Dbra, N4, j.V, N4, O, NO, j.K, partial, pe, s);
-        ctx->launches += 3;
-        if (st) st->flops_half2 += 2.0 * (double)j.K * (NO * (NO + 1) / 2.0);
+        half2_job(ctx, P, H, j, s);
         int t3 = tm.n; tm.mark();
-        launch_pack(O, NO, nKa, j.out, s);
-        ctx->launches++;
+        half2_pack(ctx, P, H, j, s);
         int t4 = tm.n; tm.mark();
         QDT_CUDA_TRY(cudaStreamSynchronize(s));
         acc_ms[4] += tm.ms(t2, t3);
@@ -486,6 +708,272 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
     acc_ms[0] += tm.ms(t0, t0 + 1);
     acc_ms[1] += tm.ms(t0 + 1, t0 + 2);
     tm.n = t0;
+}
+
+// ------------------------------------------------------------------ batches
+// Validated request of a batch: outputs split per block, host staging.
+struct BatchReq {
+    qdt_batch_item *it = nullptr;
+    qdt_ctx *c = nullptr;
+    int nKa = 0;
+    bool dev_out = true;
+    double *dst = nullptr, *o[3] = {nullptr, nullptr, nullptr};
+    size_t need = 0;
+    qdt_stats st{};
+    int status = QDT_OK;
+    std::string err;
+    ClassPlan P;
+    RowBatch B;
+    Half2 H;
+    bool active = false;       // has this round's class
+    bool fused = false;        // this round runs in the fused sequence
+};
+
+// Everything the captured sequence of a round reads or writes, plus the
+// screening outcome; equal signatures give the same launch sequence.
+uint64_t fnv(uint64_t h, const void *p, size_t n) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ULL; }
+    return h;
+}
+template <class T> uint64_t fnv_v(uint64_t h, const std::vector<T> &v) {
+    const size_t n = v.size();
+    h = fnv(h, &n, sizeof n);
+    return v.empty() ? h : fnv(h, v.data(), v.size() * sizeof(T));
+}
+
+uint64_t round_signature(const std::vector<BatchReq *> &fz, const std::vector<EriTask> tiles[2],
+                         const EriLaunch how[2], const EriShape shape[2]) {
+    uint64_t h = 1469598103934665603ULL;
+    for (int k = 0; k < 2; ++k) {
+        h = fnv_v(h, tiles[k]);
+        h = fnv(h, &how[k], sizeof(EriLaunch));
+        h = fnv(h, &shape[k], sizeof(EriShape));
+    }
+    for (BatchReq *r : fz) {
+        const ClassPlan &P = r->P;
+        const RowBatch &B = r->B;
+        h = fnv(h, &r->c, sizeof r->c);
+        h = fnv(h, &P.precision, sizeof P.precision);
+        h = fnv(h, &P.nKa, sizeof P.nKa);
+        const void *ptrs[] = {P.Dbra, P.Dket, P.Vc, P.Vg, P.ketsp, P.ketcol, P.prefix, P.d_kpos, B.W, B.Wc,
+                              B.d_kt, B.d_kg, r->H.O, r->H.partial, r->o[0], r->o[1], r->o[2]};
+        h = fnv(h, ptrs, sizeof ptrs);
+        h = fnv(h, &B.prm, sizeof B.prm);
+        h = fnv_v(h, B.kt);
+        h = fnv_v(h, B.kg);
+        const long long sz[] = {B.rows, B.ldw, B.ldwc, B.row0, r->H.NO};
+        h = fnv(h, sz, sizeof sz);
+        for (int i = 0; i < SplitWorkspace::kSlots; ++i) {
+            h = fnv(h, &r->c->split.buf[i], sizeof(void *));
+            h = fnv(h, &r->c->split.bytes[i], sizeof(size_t));
+        }
+    }
+    return h;
+}
+
+// The launch sequence of one batch round after screening: integral rows of all
+// fused requests (one persistent launch per kernel kind over the shared tile
+// queue), then every request's first half, second half and packing on its own
+// stream.  Allocates nothing, copies nothing from the host and never waits, so
+// it can be captured into a CUDA graph.
+void issue_round(qdt_ctx *owner, const std::vector<BatchReq *> &fz, const EriParams *const d_prms[2],
+                 const EriTask *const d_tiles[2], const int ntiles[2], const EriShape shape[2],
+                 const EriLaunch how[2]) {
+    cudaStream_t s0 = owner->stream;
+    for (BatchReq *r : fz) {
+        split_clear_status(r->c->split, s0);
+        launch_zero(r->B.W, r->B.rows * r->P.mult * r->B.ldw, s0);
+        if (r->B.Wc) launch_zero(r->B.Wc, r->B.rows * r->B.ldwc, s0);
+        r->c->launches += 1 + (r->B.Wc ? 1 : 0);
+    }
+    for (int k = 0; k < 2; ++k)
+        if (ntiles[k] > 0) {
+            launch_eri(d_prms[k], d_tiles[k], ntiles[k], (int *)owner->bnext[k].p, shape[k], k == 1, how[k], s0);
+            owner->launches++;
+        }
+    QDT_CUDA_TRY(cudaEventRecord(owner->fork_ev, s0));
+    for (BatchReq *r : fz) {
+        cudaStream_t cs = r->c->stream;
+        if (cs != s0) QDT_CUDA_TRY(cudaStreamWaitEvent(cs, owner->fork_ev, 0));
+        batch_half1(r->c, r->P, r->B, cs);
+        for (const Half2::Job &j : r->H.jobs) {
+            half2_job(r->c, r->P, r->H, j, cs);
+            half2_pack(r->c, r->P, r->H, j, cs);
+        }
+        if (cs != s0) {
+            QDT_CUDA_TRY(cudaEventRecord(r->c->join_ev, cs));
+            QDT_CUDA_TRY(cudaStreamWaitEvent(s0, r->c->join_ev, 0));
+        }
+    }
+}
+
+ClassRun round_class(int round, unsigned blocks) {
+    if (round == 0) return ClassRun{0, true, false, false};
+    return ClassRun{1, false, (blocks & QDT_GAUNT) != 0, (blocks & QDT_GAUGE) != 0};
+}
+
+bool round_wanted(int round, unsigned blocks) {
+    return round == 0 ? (blocks & QDT_COULOMB) != 0 : (blocks & (QDT_GAUNT | QDT_GAUGE)) != 0;
+}
+
+void item_fail(BatchReq &r, const Error &e) {
+    if (r.status == QDT_OK) {
+        r.status = e.code;
+        r.err = e.msg;
+    }
+    r.active = false;
+    r.fused = false;
+}
+
+// One round (0: Coulomb class, 1: Gaunt/gauge class) of a batch.
+void batch_round(qdt_ctx *owner, std::vector<BatchReq> &R, int round, unsigned flags) {
+    cudaStream_t s0 = owner->stream;
+    // screening of every request, issued on all streams before the first wait
+    for (BatchReq &r : R) {
+        r.active = r.status == QDT_OK && round_wanted(round, r.it->blocks);
+        r.fused = false;
+        if (!r.active) continue;
+        try {
+            Timer off(r.c, false);
+            class_issue(r.c, round_class(round, r.it->blocks), r.it->k_begin, r.nKa, r.it->schwarz_tau,
+                        r.it->precision, r.P, off);
+        } catch (const Error &e) { item_fail(r, e); }
+    }
+    std::vector<BatchReq *> fz;
+    for (BatchReq &r : R) {
+        if (!r.active) continue;
+        try {
+            const qdt_stats before = r.st;
+            class_finish(r.c, r.P, &r.st);
+            batch_prepare(r.c, r.P, 0, r.B);
+            r.fused = r.B.b1 == r.c->cls[r.P.cr.c].nsp;     // the whole class in one row batch
+            if (r.fused) {
+                half2_prepare(r.c, r.P, r.o[0], r.o[1], r.o[2], r.H);
+                batch_stats(r.c, r.P, r.B, &r.st);
+                half2_stats(r.H, &r.st);
+                fz.push_back(&r);
+            } else {
+                r.st = before;       // run_class below screens again and counts
+            }
+        } catch (const Error &e) { item_fail(r, e); }
+    }
+    if (!fz.empty()) {
+        // shared tile queues: kernel kind 0 (Coulomb kernel) and 1 (gauge kernel);
+        // tiles of all requests, most expensive bra pairs first
+        std::vector<EriParams> prms[2];
+        std::vector<int> req_of(fz.size());
+        EriShape shape[2];
+        for (size_t i = 0; i < fz.size(); ++i) {
+            BatchReq *r = fz[i];
+            const int k = r->B.prm.gauge ? 1 : 0;
+            req_of[i] = (int)prms[k].size();
+            prms[k].push_back(r->B.prm);
+            const PairClass &pc = r->c->cls[r->P.cr.c];
+            shape[k].merge(EriShape{pc.maxnfp, pc.maxLab, pc.maxnpp});
+        }
+        const EriParams *d_prms[2] = {nullptr, nullptr};
+        const EriTask *d_tiles[2] = {nullptr, nullptr};
+        int ntiles[2] = {0, 0};
+        EriLaunch how[2];
+        std::vector<EriTask> tiles[2];
+        for (int k = 0; k < 2; ++k) {
+            if (prms[k].empty()) continue;
+            d_prms[k] = dcopy(owner->bprms[k], prms[k], s0);
+            owner->bnext[k].get(sizeof(int));
+            // the tuner samples the first request of this kind
+            size_t first = 0;
+            while ((fz[first]->B.prm.gauge ? 1 : 0) != k) ++first;
+            how[k] = eri_launch_for(owner, fz[first]->c->cls[fz[first]->P.cr.c], shape[k], k == 1, d_prms[k],
+                                    fz[first]->B.bras, fz[first]->P.h_prefix, s0);
+            // tile order across requests: request by request in bra order, or
+            // all bra pairs most expensive first
+            struct Key { double cost; int i; int sp; };
+            std::vector<Key> order;
+            for (size_t i = 0; i < fz.size(); ++i) {
+                BatchReq *r = fz[i];
+                if ((r->B.prm.gauge ? 1 : 0) != k) continue;
+                const PairClass &pc = r->c->cls[r->P.cr.c];
+                for (int sp : r->B.bras) order.push_back({bra_cost(pc.h_pairs[sp]), (int)i, sp});
+            }
+            if (how[k].order == 1)
+                std::stable_sort(order.begin(), order.end(), [](const Key &a, const Key &b) { return a.cost > b.cost; });
+            for (const Key &o : order) {
+                const std::vector<int> &pre = fz[o.i]->P.h_prefix;
+                for (int q = 0; q < pre[o.sp]; q += how[k].kets)
+                    tiles[k].push_back({o.sp, q, std::min(pre[o.sp], q + how[k].kets), req_of[o.i]});
+            }
+            d_tiles[k] = dcopy(owner->btasks[k], tiles[k], s0);
+            ntiles[k] = (int)tiles[k].size();
+        }
+        for (BatchReq *r : fz) r->c->split.deferred = true;
+        QDT_CUDA_TRY(cudaStreamSynchronize(s0));          // uploads done before any capture
+        GraphEntry &g = owner->graph[round];
+        const bool graph = (flags & QDT_BATCH_GRAPH) != 0;
+        uint64_t sig = graph ? round_signature(fz, tiles, how, shape) : 0;
+        const void *own[] = {owner->bprms[0].p, owner->bprms[1].p, owner->btasks[0].p, owner->btasks[1].p,
+                             owner->bnext[0].p, owner->bnext[1].p};
+        sig = fnv(sig, own, sizeof own);
+        try {
+            if (!graph) {
+                issue_round(owner, fz, d_prms, d_tiles, ntiles, shape, how);
+            } else if (g.exec && g.sig == sig) {
+                QDT_CUDA_TRY(cudaGraphLaunch(g.exec, s0));
+                owner->graph_replays++;
+            } else if (g.seen && g.sig == sig) {
+                // second sighting: every buffer already has its size, so the
+                // sequence can be captured and replayed from now on
+                QDT_CUDA_TRY(cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed));
+                try {
+                    issue_round(owner, fz, d_prms, d_tiles, ntiles, shape, how);
+                } catch (...) {
+                    cudaGraph_t dead = nullptr;
+                    cudaStreamEndCapture(s0, &dead);
+                    if (dead) cudaGraphDestroy(dead);
+                    cudaGetLastError();
+                    throw;
+                }
+                cudaGraph_t cg = nullptr;
+                QDT_CUDA_TRY(cudaStreamEndCapture(s0, &cg));
+                cudaGraphExec_t ex = nullptr;
+                const cudaError_t ie = cudaGraphInstantiate(&ex, cg, 0);
+                cudaGraphDestroy(cg);
+                QDT_CUDA_TRY(ie);
+                if (g.exec) cudaGraphExecDestroy(g.exec);
+                g.exec = ex;
+                QDT_CUDA_TRY(cudaGraphLaunch(g.exec, s0));
+                owner->graph_captures++;
+            } else {
+                if (g.exec) cudaGraphExecDestroy(g.exec);
+                g.exec = nullptr;
+                g.sig = sig;
+                g.seen = 1;
+                issue_round(owner, fz, d_prms, d_tiles, ntiles, shape, how);
+            }
+            QDT_CUDA_TRY(cudaStreamSynchronize(s0));
+        } catch (const Error &e) {
+            for (BatchReq *r : fz) {
+                r->c->split.deferred = false;
+                item_fail(*r, e);
+            }
+            fz.clear();
+        }
+        for (BatchReq *r : fz) {
+            try {
+                split_end_deferred(r->c->split, r->c->stream);
+            } catch (const Error &e) { item_fail(*r, e); }
+        }
+    }
+    // requests too large for one row batch run alone
+    for (BatchReq &r : R) {
+        if (!r.active || r.fused) continue;
+        try {
+            Timer off(r.c, false);
+            double acc[6] = {0, 0, 0, 0, 0, 0};
+            run_class(r.c, round_class(round, r.it->blocks), r.it->k_begin, r.nKa, r.it->schwarz_tau,
+                      r.it->precision, r.o[0], r.o[1], r.o[2], &r.st, off, acc);
+        } catch (const Error &e) { item_fail(r, e); }
+    }
 }
 
 }  // namespace
@@ -509,6 +997,8 @@ int qdt_create(qdt_ctx **out, int device, void *cuda_stream) {
             c->own_stream = true;
         }
         for (int i = 0; i < 16; ++i) QDT_CUDA_TRY(cudaEventCreate(&c->ev[i]));
+        QDT_CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+        QDT_CUDA_TRY(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
         double *tab = (double *)c->boys.get((size_t)kBoysGrid * kBoysCols * sizeof(double));
         launch_boys_table(tab, c->stream);
         QDT_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -527,14 +1017,20 @@ void qdt_destroy(qdt_ctx *c) {
     DBuf *bufs[] = {&c->shells, &c->exps, &c->coefs, &c->norms, &c->boys, &c->Cq, &c->Craw, &c->dsmap0,
                     &c->dsmap1, &c->Dbra, &c->Dket,
                     &c->V, &c->Vg, &c->W, &c->Wc, &c->Dmax, &c->wsort, &c->ketsp, &c->ketcol,
-                    &c->prefix, &c->ktile, &c->tasks, &c->O, &c->partial, &c->stage, &c->rsR, &c->rsS};
+                    &c->prefix, &c->ktile, &c->tasks, &c->O, &c->partial, &c->stage, &c->rsR, &c->rsS,
+                    &c->kpos, &c->prms, &c->next, &c->ktile2, &c->bprms[0], &c->bprms[1],
+                    &c->btasks[0], &c->btasks[1], &c->bnext[0], &c->bnext[1]};
     for (DBuf *b : bufs) b->release();
     for (int k = 0; k < 2; ++k) {
         c->cb[k].pairs.release(); c->cb[k].pp.release(); c->cb[k].E.release();
         c->cb[k].Q.release(); c->cb[k].bra.release(); c->cb[k].pp_pair.release();
     }
     split_release(c->split);
+    for (GraphEntry &g : c->graph)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (int i = 0; i < 16; ++i) cudaEventDestroy(c->ev[i]);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -710,6 +1206,92 @@ int qdt_transform(qdt_ctx *c, unsigned blocks, int k_begin, int k_end, double ta
         return fail(c, e);
     }
     c->err.clear();
+    return QDT_OK;
+}
+
+int qdt_transform_batch(qdt_batch_item *items, int n, unsigned flags) {
+    if (!items || n <= 0 || (flags & ~QDT_BATCH_GRAPH)) return QDT_ERR_ARG;
+    std::vector<BatchReq> R(n);
+    qdt_ctx *owner = nullptr;
+    for (int i = 0; i < n; ++i) {
+        BatchReq &r = R[i];
+        r.it = &items[i];
+        r.c = items[i].ctx;
+        try {
+            arg_check(r.c != nullptr, "qdt_transform_batch: null context");
+            for (int j = 0; j < i; ++j) arg_check(items[j].ctx != r.c, "qdt_transform_batch: a context appears twice");
+            if (!owner) owner = r.c;
+            arg_check(r.c->device == owner->device, "qdt_transform_batch: contexts on different devices");
+            QDT_CUDA_TRY(cudaSetDevice(r.c->device));
+            cudaGetLastError();
+            if (!r.c->has_basis || !r.c->has_coef) throw Error{QDT_ERR_STATE, "qdt_transform_batch: basis or coefficients not set"};
+            const qdt_batch_item &it = items[i];
+            arg_check(it.blocks != 0 && (it.blocks & ~7u) == 0, "qdt_transform_batch: blocks must be a non-empty subset of COULOMB|GAUNT|GAUGE");
+            arg_check(it.k_begin >= 0 && it.k_end > it.k_begin && it.k_end <= r.c->nK, "qdt_transform_batch: bad Kramers range");
+            arg_check(it.schwarz_tau >= 0.0, "qdt_transform_batch: negative Schwarz threshold");
+            arg_check(it.precision == QDT_FP64 || it.precision == QDT_SPLIT, "qdt_transform_batch: bad precision");
+            r.need = qdt_packed_size(r.c, it.blocks, it.k_begin, it.k_end);
+            arg_check(it.out != nullptr && it.out_bytes >= r.need, "qdt_transform_batch: output buffer too small");
+            r.nKa = it.k_end - it.k_begin;
+            const long long nP = (long long)r.nKa * (r.nKa + 1) / 2, per = nP * (nP + 1) / 2 * 16;
+            r.dev_out = is_device_ptr(it.out);
+            r.dst = r.dev_out ? it.out : (double *)r.c->stage.get(r.need);
+            double *cur = r.dst;
+            if (it.blocks & QDT_COULOMB) { r.o[0] = cur; cur += per; }
+            if (it.blocks & QDT_GAUNT) { r.o[1] = cur; cur += per; }
+            if (it.blocks & QDT_GAUGE) { r.o[2] = cur; cur += per; }
+            r.st.precision = it.precision;
+            r.st.slices = split_slices(r.c->split);
+            r.c->launches = 0;
+        } catch (const Error &e) {
+            r.status = e.code;
+            r.err = e.msg;
+        }
+    }
+    if (owner) {
+        try {
+            QDT_CUDA_TRY(cudaSetDevice(owner->device));
+            QDT_CUDA_TRY(cudaEventRecord(owner->ev[14], owner->stream));
+            for (int round = 0; round < 2; ++round) batch_round(owner, R, round, flags);
+            for (BatchReq &r : R)
+                if (r.status == QDT_OK && !r.dev_out)
+                    QDT_CUDA_TRY(cudaMemcpyAsync(r.it->out, r.dst, r.need, cudaMemcpyDeviceToHost, r.c->stream));
+            for (BatchReq &r : R)
+                if (r.status == QDT_OK) {
+                    QDT_CUDA_TRY(cudaEventRecord(r.c->join_ev, r.c->stream));
+                    QDT_CUDA_TRY(cudaStreamWaitEvent(owner->stream, r.c->join_ev, 0));
+                }
+            QDT_CUDA_TRY(cudaEventRecord(owner->ev[15], owner->stream));
+            QDT_CUDA_TRY(cudaStreamSynchronize(owner->stream));
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, owner->ev[14], owner->ev[15]) != cudaSuccess) { cudaGetLastError(); ms = 0.f; }
+            for (BatchReq &r : R) r.st.ms_total = ms;
+        } catch (const Error &e) {
+            for (BatchReq &r : R)
+                if (r.status == QDT_OK) { r.status = e.code; r.err = e.msg; }
+        }
+    }
+    int first = QDT_OK;
+    for (int i = 0; i < n; ++i) {
+        BatchReq &r = R[i];
+        items[i].status = r.status;
+        if (r.c) {
+            if (r.status == QDT_OK) r.c->err.clear();
+            else r.c->err = r.err;
+        }
+        if (items[i].stats && r.status == QDT_OK) {
+            r.st.kernel_launches = r.c->launches;
+            *items[i].stats = r.st;
+        }
+        if (first == QDT_OK && r.status != QDT_OK) first = r.status;
+    }
+    return first;
+}
+
+int qdt_graph_counts(const qdt_ctx *c, long long *captures, long long *replays) {
+    if (!c) return QDT_ERR_ARG;
+    if (captures) *captures = c->graph_captures;
+    if (replays) *replays = c->graph_replays;
     return QDT_OK;
 }
 

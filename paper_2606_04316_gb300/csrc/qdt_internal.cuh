@@ -135,16 +135,39 @@ struct EriParams {
     const int *prefix;          // kept ket prefix length of every pair id
 };
 
-struct EriTask {                // one CTA: bra shell pair x range of ket positions
+struct EriTask {                // one tile: bra shell pair x range of sorted ket positions
     int bra_sp;
     int k0, k1;
+    int req;                    // index into the EriParams array of the launch
+};
+
+// Class maxima that fix the integral kernel's shared-memory plan.
+struct EriShape {
+    int maxnfp = 0, maxLab = 0, maxnpp = 0;
+    void merge(const EriShape &o) {
+        maxnfp = maxnfp > o.maxnfp ? maxnfp : o.maxnfp;
+        maxLab = maxLab > o.maxLab ? maxLab : o.maxLab;
+        maxnpp = maxnpp > o.maxnpp ? maxnpp : o.maxnpp;
+    }
+};
+
+// Launch shape of the integral kernel (the autotuned part): CTA threads and
+// ket positions per tile.  Neither changes the arithmetic of an integral.
+struct EriLaunch {
+    int threads = 0;            // 0: the plan's default
+    int kets = 8;
+    int order = 0;              // tile order: 0 bra pairs by Schwarz Q (bra order), 1 most expensive first
 };
 
 void launch_boys_table(double *d_tab, cudaStream_t s);
 void launch_shell_norms(const ShellDev *shells, int nL_shells, const double *exps,
                         const double *coefs, double *norms, cudaStream_t s);
-void launch_eri(const EriParams &prm, const EriTask *tasks, int ntasks, int maxnfp, int maxLab,
-                int maxnpp, cudaStream_t s);
+// Persistent integral kernel over a shared tile queue: `next` (device int,
+// zeroed by this call) hands out the tiles in array order.  prms: device array
+// of the parameter sets the tiles' `req` index.
+void launch_eri(const EriParams *prms, const EriTask *tasks, int ntasks, int *next, const EriShape &shape,
+                bool gauge, const EriLaunch &how, cudaStream_t s);
+int eri_default_threads(const EriShape &shape, bool gauge);
 void launch_schwarz(const ShellDev *shells, const PairDev *pairs, const PrimPairDev *pp,
                     const double *E, const double *boys, int npairs, int maxnfp, int maxLab,
                     int maxnpp, double *Q, cudaStream_t s);

@@ -15,11 +15,13 @@ struct SplitKey {
 };
 
 struct SplitWorkspace {
-    void *buf[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    size_t bytes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    static constexpr int kSlots = 9;
+    void *buf[kSlots] = {};
+    size_t bytes[kSlots] = {};
     int slices = 6;            // 7-bit digits per operand
     SplitKey bkey[2];          // cached first-half B operands (density slices)
     int bnext = 0;
+    bool deferred = false;     // status of the tensor-core waits read once at the end
 };
 
 void split_release(SplitWorkspace &w);
@@ -28,6 +30,14 @@ int split_slices(const SplitWorkspace &w);
 size_t split_held_bytes(const SplitWorkspace &w);
 // Drop cached operand slices (call whenever the densities change).
 void split_invalidate(SplitWorkspace &w);
+// Deferred status: begin clears the status word (a stream operation, so it
+// can be part of a captured graph) and stops the per-launch status reads;
+// end reads the word once (synchronising `s`) and throws QDT_ERR_TIMEOUT if a
+// bounded wait gave up in any contraction since begin.
+// split_clear_status alone clears the word without changing the mode.
+void split_begin_deferred(SplitWorkspace &w, cudaStream_t s);
+void split_clear_status(SplitWorkspace &w, cudaStream_t s);
+void split_end_deferred(SplitWorkspace &w, cudaStream_t s);
 
 // C[M x N] = A[M x K_t] B[K_t x N], K_t from the per-64-row-tile extents.
 void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B,

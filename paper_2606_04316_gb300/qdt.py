@@ -22,7 +22,8 @@ ERRORS = {-1: "QDT_ERR_ARG", -2: "QDT_ERR_OOM", -3: "QDT_ERR_CUDA", -4: "QDT_ERR
 EXPORTS = ["qdt_create", "qdt_destroy", "qdt_set_basis", "qdt_num_functions", "qdt_set_coefficients",
            "qdt_packed_size", "qdt_transform", "qdt_unpack", "qdt_last_error", "qdt_version",
            "qdt_footprint", "qdt_server_create", "qdt_server_destroy", "qdt_submit", "qdt_poll", "qdt_wait",
-           "qdt_second_half_noalloc"]
+           "qdt_second_half_noalloc", "qdt_transform_batch", "qdt_graph_counts"]
+BATCH_GRAPH = 1
 
 
 class QdtError(RuntimeError):
@@ -56,6 +57,13 @@ class Request(ctypes.Structure):
                 ("CL", ctypes.c_void_p), ("CS", ctypes.c_void_p), ("blocks", ctypes.c_uint),
                 ("k_begin", ctypes.c_int), ("k_end", ctypes.c_int), ("schwarz_tau", ctypes.c_double),
                 ("precision", ctypes.c_int), ("out", ctypes.c_void_p), ("out_bytes", ctypes.c_size_t)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("blocks", ctypes.c_uint), ("k_begin", ctypes.c_int),
+                ("k_end", ctypes.c_int), ("schwarz_tau", ctypes.c_double), ("precision", ctypes.c_int),
+                ("out", ctypes.c_void_p), ("out_bytes", ctypes.c_size_t), ("stats", ctypes.c_void_p),
+                ("status", ctypes.c_int)]
 
 
 _LIB = None
@@ -102,6 +110,8 @@ def load(build_if_missing=True):
                            ctypes.POINTER(Stats)]
     L.qdt_second_half_noalloc.argtypes = [vp, vp, ctypes.c_longlong, ctypes.c_longlong, vp, vp,
                                           ctypes.c_char_p, ctypes.c_size_t]
+    L.qdt_transform_batch.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_int, ctypes.c_uint]
+    L.qdt_graph_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     _LIB = L
     return L
 
@@ -186,6 +196,41 @@ class Context:
     def unpack(self, packed, n_kramers, block, full):
         """packed/full: torch cuda float64 tensors; full holds (2n)^4 complex values."""
         self._check(self.L.qdt_unpack(self.h, _ptr(packed), int(n_kramers), blocks_mask([block]), _ptr(full)))
+
+
+    def graph_counts(self):
+        """(graphs captured, graph replays) of the batches this context owned."""
+        c, r = ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(self.L.qdt_graph_counts(self.h, ctypes.byref(c), ctypes.byref(r)))
+        return c.value, r.value
+
+
+def transform_batch(jobs, graph=False, raise_on_error=True):
+    """Several transformations as one batch (qdt_transform_batch).
+
+    jobs: list of (Context, blocks, k_begin, k_end, tau, precision, out), every
+    Context distinct.  Returns (status list, stats dicts); with raise_on_error
+    a failing item raises QdtError with its message instead."""
+    L = load()
+    n = len(jobs)
+    items = (BatchItem * n)()
+    stats = [Stats() for _ in range(n)]
+    for i, (ctx, blocks, k0, k1, tau, prec, out) in enumerate(jobs):
+        nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+        items[i].ctx = ctx.h
+        items[i].blocks = blocks_mask(blocks)
+        items[i].k_begin, items[i].k_end = int(k0), int(k1)
+        items[i].schwarz_tau = float(tau)
+        items[i].precision = int(prec)
+        items[i].out = _ptr(out)
+        items[i].out_bytes = nbytes
+        items[i].stats = ctypes.addressof(stats[i])
+    rc = L.qdt_transform_batch(items, n, BATCH_GRAPH if graph else 0)
+    status = [items[i].status for i in range(n)]
+    if rc != 0 and raise_on_error:
+        bad = next(i for i in range(n) if status[i] != 0)
+        raise QdtError(rc, "item %d: %s" % (bad, L.qdt_last_error(jobs[bad][0].h).decode()))
+    return status, [s.as_dict() for s in stats]
 
 
 def version():
