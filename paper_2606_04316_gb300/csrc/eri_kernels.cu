@@ -195,18 +195,27 @@ __device__ void build_tables(const Plan &p, BlockSmem &b) {
     __syncthreads();
 }
 
-__host__ __device__ inline double orient_cost(const PairDev &X, const PairDev &Y) {
-    double nhx = nherm(X.Lab), nhy = nherm(Y.Lab);
-    return (double)X.npp * Y.npp * nhx * Y.nfp * nhy + (double)X.npp * X.nfp * Y.nfp * nhx;
+// Rows of T per outer primitive pair: the Hermite triples h of X for the
+// Coulomb tensor and, for the gauge kernel, the triples g with 2 <= |g| <= Lx+2
+// of the r12 tensor (g = h + e_I + e_J covers all six second derivatives).
+__host__ __device__ inline int t_rows(int Lx, bool gauge) { return nherm(Lx) + (gauge ? nherm(Lx + 2) - 4 : 0); }
+
+// FP64 multiply-adds of the contraction of a shell quartet with X outer: the
+// ket pass (T rows x inner function pairs x inner Hermite terms per primitive
+// quartet) plus the bra pass (components x function pairs x outer Hermite
+// terms per outer primitive pair).
+__host__ __device__ inline double orient_cost(const PairDev &X, const PairDev &Y, bool gauge) {
+    const double nhx = nherm(X.Lab), nhy = nherm(Y.Lab);
+    return (double)X.npp * Y.npp * t_rows(X.Lab, gauge) * Y.nfp * nhy +
+           (double)X.npp * X.nfp * Y.nfp * nhx * (gauge ? 7 : 1);
 }
 
-// acc[c] += sign * sum_{h' of orders n0, n0+2, ...} sum_kl R_{kl}[h + h' (+ e_IJ)] E^{kl}[h'][y],
+// acc += sign * sum_{h' of orders n0, n0+2, ...} sum_kl R_{kl}[h + h'] E^{kl}[h'][y],
 // sign = -1 (NEG) for the odd orders.
-template <bool GAUGE, bool NEG>
+template <bool NEG>
 __device__ __forceinline__ void ket_orders(int n0, int Ly, int tx, int ux, int vx, const int *trip,
-                                           const double *RCq, int nrC, const double *RRq, int nrR,
-                                           const double *ey, int nfpY, const long long *eoff, int nk,
-                                           double (&acc)[GAUGE ? 7 : 1]) {
+                                           const double *Rq, int nr, const double *ey, int nfpY,
+                                           const long long *eoff, int nk, double &acc) {
     for (int n = n0; n <= Ly; n += 2) {
         const int hb = n ? nherm(n - 1) : 0, he = nherm(n);
         for (int hp = hb; hp < he; ++hp) {
@@ -215,39 +224,13 @@ __device__ __forceinline__ void ket_orders(int n0, int Ly, int tx, int ux, int v
             const int s = T0 + U0 + V0, w = U0 + V0;
             const int i0 = s * (s + 1) * (s + 2) / 6 + w * (w + 1) / 2 + V0;
             const double *e = ey + (size_t)hp * nfpY;
-            if (!GAUGE) {
-                double a = acc[0];
-                for (int kl = 0; kl < nk; ++kl) {
-                    const double r = RCq[kl * nrC + i0];
-                    const double ev = __ldg(e + eoff[kl]);
-                    a = NEG ? fma(-r, ev, a) : fma(r, ev, a);
-                }
-                acc[0] = a;
-            } else {
-                // shifted triples, all of order s + 2: xx, xy, xz, yy, yz, zz
-                const int b2 = (s + 2) * (s + 3) * (s + 4) / 6;
-                const int o0 = b2 + w * (w + 1) / 2 + V0;
-                const int o1 = b2 + (w + 1) * (w + 2) / 2 + V0;
-                const int o3 = b2 + (w + 2) * (w + 3) / 2 + V0;
-                for (int kl = 0; kl < nk; ++kl) {
-                    const double ev = __ldg(e + eoff[kl]);
-                    const double *rr = RRq + (size_t)kl * nrR;
-                    const double r0 = RCq[kl * nrC + i0];
-                    const double r1 = rr[o0], r2 = rr[o1], r3 = rr[o1 + 1];
-                    const double r4 = rr[o3], r5 = rr[o3 + 1], r6 = rr[o3 + 2];
-                    if (NEG) {
-                        acc[0] = fma(-r0, ev, acc[0]); acc[1] = fma(-r1, ev, acc[1]);
-                        acc[2] = fma(-r2, ev, acc[2]); acc[3] = fma(-r3, ev, acc[3]);
-                        acc[4] = fma(-r4, ev, acc[4]); acc[5] = fma(-r5, ev, acc[5]);
-                        acc[6] = fma(-r6, ev, acc[6]);
-                    } else {
-                        acc[0] = fma(r0, ev, acc[0]); acc[1] = fma(r1, ev, acc[1]);
-                        acc[2] = fma(r2, ev, acc[2]); acc[3] = fma(r3, ev, acc[3]);
-                        acc[4] = fma(r4, ev, acc[4]); acc[5] = fma(r5, ev, acc[5]);
-                        acc[6] = fma(r6, ev, acc[6]);
-                    }
-                }
+            double a = acc;
+            for (int kl = 0; kl < nk; ++kl) {
+                const double r = Rq[kl * nr + i0];
+                const double ev = __ldg(e + eoff[kl]);
+                a = NEG ? fma(-r, ev, a) : fma(r, ev, a);
             }
+            acc = a;
         }
     }
 }
@@ -266,7 +249,8 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
     const int nrC = nherm(L), nrR = GAUGE ? nherm(Lr) : 0;
     const int hs = header_len(L, GAUGE), perq = quartet_len(L, GAUGE);
     const int xch = x1 - x0, ych = y1 - y0;
-    const int tsz = NC * nhx * ych;                    // T doubles per outer primitive pair
+    const int nT = t_rows(Lx, GAUGE);                   // T rows per outer primitive pair
+    const int tsz = nT * ych;                           // T doubles per outer primitive pair
 
     // primitive grouping: nij outer pairs x nkl inner pairs at a time
     int nijMax, nkl;
@@ -334,30 +318,31 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
                 }
                 __syncthreads();
             }
-            // T[ij][c][h][y] += sum_kl sum_h' (-1)^{|h'|} R[h+h'] E^{kl}[h'][y]
-            for (int it = tid; it < nij * nhx * ych; it += nt) {
-                const int ijl = it / (nhx * ych);
-                const int rem = it - ijl * nhx * ych;
-                const int h = rem / ych, yy = rem - h * ych;
+            // T[ij][h][y] += sum_kl sum_h' (-1)^{|h'|} R[h+h'] E^{kl}[h'][y]: rows h < nhx
+            // with the Coulomb tensor, then (gauge) rows g = 4.. with the r12 tensor
+            for (int it = tid; it < nij * nT * ych; it += nt) {
+                const int ijl = it / (nT * ych);
+                const int rem = it - ijl * nT * ych;
+                const int hh = rem / ych, yy = rem - hh * ych;
+                const bool r12 = GAUGE && hh >= nhx;
+                const int h = r12 ? hh - nhx + 4 : hh;
                 const int tr = b.trip[h];
                 const int tx = tr & 255, ux = (tr >> 8) & 255, vx = tr >> 16;
-                double *Tq = T + (size_t)ijl * tsz + (size_t)h * ych + yy;
-                double acc[NC];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) acc[c] = Tq[(size_t)c * nhx * ych];
-                const double *RCq = RC + (size_t)ijl * nk * nrC;
-                const double *RRq = GAUGE ? RR + (size_t)ijl * nk * nrR : nullptr;
+                double *Tq = T + (size_t)ijl * tsz + (size_t)hh * ych + yy;
+                double acc = *Tq;
+                const double *Rq = r12 ? RR + (size_t)ijl * nk * nrR : RC + (size_t)ijl * nk * nrC;
+                const int nr = r12 ? nrR : nrC;
                 const double *ey = E + (y0 + yy);
-                ket_orders<GAUGE, false>(0, Ly, tx, ux, vx, b.trip, RCq, nrC, RRq, nrR, ey, Y.nfp, b.eY + k0, nk, acc);
-                ket_orders<GAUGE, true>(1, Ly, tx, ux, vx, b.trip, RCq, nrC, RRq, nrR, ey, Y.nfp, b.eY + k0, nk, acc);
-#pragma unroll
-                for (int c = 0; c < NC; ++c) Tq[(size_t)c * nhx * ych] = acc[c];
+                ket_orders<false>(0, Ly, tx, ux, vx, b.trip, Rq, nr, ey, Y.nfp, b.eY + k0, nk, acc);
+                ket_orders<true>(1, Ly, tx, ux, vx, b.trip, Rq, nr, ey, Y.nfp, b.eY + k0, nk, acc);
+                *Tq = acc;
             }
             // the next group's header pass touches neither T nor R, and its
             // barrier orders this pass before the recursion overwrites R
             if (k0 + nkl >= Y.npp) __syncthreads();
         }
-        // G[c][x][y] += sum_{ij} sum_h E^{ij}[h][x] T[ij][c][h][y]
+        // G[0][x][y] += sum_{ij} sum_h E^{ij}[h][x] T[ij][h][y]; gauge: G[1+IJ] from
+        // the r12 rows h + e_I + e_J (order |h| + 2) for IJ = xx, xy, xz, yy, yz, zz
         for (int it = tid; it < xch * ych; it += nt) {
             const int xx = it / ych, yy = it - xx * ych;
             double s[NC];
@@ -366,10 +351,25 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
             for (int ijl = 0; ijl < nij; ++ijl) {
                 const double *e = E + b.eX[i0 + ijl] + (x0 + xx);
                 const double *Tq = T + (size_t)ijl * tsz + yy;
+                const double *Tr = Tq + (size_t)(nhx - 4) * ych;     // row of triple g: nhx + g - 4
                 for (int h = 0; h < nhx; ++h) {
                     const double ev = __ldg(e + (size_t)h * X.nfp);
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) s[c] = fma(ev, Tq[((size_t)c * nhx + h) * ych], s[c]);
+                    s[0] = fma(ev, Tq[(size_t)h * ych], s[0]);
+                    if (GAUGE) {
+                        const int tr = b.trip[h];
+                        const int u = (tr >> 8) & 255, v = tr >> 16;
+                        const int o = (tr & 255) + u + v, w = u + v;
+                        const int b2 = (o + 2) * (o + 3) * (o + 4) / 6;
+                        const int g0 = b2 + w * (w + 1) / 2 + v;
+                        const int g1 = b2 + (w + 1) * (w + 2) / 2 + v;
+                        const int g3 = b2 + (w + 2) * (w + 3) / 2 + v;
+                        s[1] = fma(ev, Tr[(size_t)g0 * ych], s[1]);
+                        s[2] = fma(ev, Tr[(size_t)g1 * ych], s[2]);
+                        s[3] = fma(ev, Tr[(size_t)(g1 + 1) * ych], s[3]);
+                        s[4] = fma(ev, Tr[(size_t)g3 * ych], s[4]);
+                        s[5] = fma(ev, Tr[(size_t)(g3 + 1) * ych], s[5]);
+                        s[6] = fma(ev, Tr[(size_t)(g3 + 2) * ych], s[6]);
+                    }
                 }
             }
 #pragma unroll
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(256, 2) eri_rows_kernel(const EriParams *prms,
             if (rev && cd_id < tk.bra_sp) continue;
             const long long col_rev = rev ? prm.ket_col[prm.ket_pos[tk.bra_sp]] : 0;
             // contract the orientation with the smaller cost; swapped -> G is (CD|AB)
-            const bool swap = orient_cost(CD, AB) < orient_cost(AB, CD);
+            const bool swap = orient_cost(CD, AB, GAUGE) < orient_cost(AB, CD, GAUGE);
             const PairDev &X = swap ? CD : AB, &Y = swap ? AB : CD;
             double *W = prm.W, *Wc = prm.Wc;
             const long long ldw = prm.ldw, ldwc = prm.ldwc, row0 = prm.row0;
@@ -487,7 +487,7 @@ Plan eri_plan(int maxnfp, int maxLab, int maxnpp, bool gauge) {
         for (;;) {
             p.pool = 0;
             const long long fixed = (long long)plan_smem(p);
-            tsz = (long long)p.NC * p.nhMax * p.cch;
+            tsz = (long long)t_rows(maxLab, gauge) * p.cch;
             const long long pool = (budget - fixed) / (long long)sizeof(double);
             if (pool >= tsz + 8 * perq || p.ach <= 8) {
                 p.pool = pool > tsz + perq ? pool : tsz + perq;

@@ -132,11 +132,19 @@ bool is_device_ptr(const void *p) {
 
 int lcart(int l) { return (l + 1) * (l + 2) / 2; }
 
+// Rows of W per split-form first-half call: the digit planes of one call
+// (6 BF16 digits per element, 12 bytes) stay within kSliceBudget, so the
+// integral rows themselves decide whether a class fits one row batch.
+constexpr size_t kSliceBudget = (size_t)8 << 30;
+
 // FP64 multiply-adds of the E R E contraction of one shell quartet with X as
-// the outer (per primitive pair) side.
-double orient_cost_h(const PairDev &X, const PairDev &Y) {
-    double nhx = nherm(X.Lab), nhy = nherm(Y.Lab);
-    return (double)X.npp * Y.npp * nhx * Y.nfp * nhy + (double)X.npp * X.nfp * Y.nfp * nhx;
+// the outer (per primitive pair) side: the ket pass over T rows (X's Hermite
+// triples; gauge: also the r12 rows 2 <= |g| <= Lx + 2) and the bra pass per
+// component (1 Coulomb, 7 gauge).
+double orient_cost_h(const PairDev &X, const PairDev &Y, bool gauge) {
+    const double nhx = nherm(X.Lab), nhy = nherm(Y.Lab);
+    const double trows = nherm(X.Lab) + (gauge ? nherm(X.Lab + 2) - 4 : 0);
+    return (double)X.npp * Y.npp * trows * Y.nfp * nhy + (double)X.npp * X.nfp * Y.nfp * nhx * (gauge ? 7 : 1);
 }
 
 // Cost proxy of the tiles of a bra pair: primitive pairs x Hermite terms x
@@ -435,9 +443,9 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
 }
 
 // Waits for class_issue; kept-quartet statistics, V buffers and the row-batch
-// decision: one batch (and bra-ket symmetry) when the integral block and its
-// digit planes fit in 70 % of the device memory this context can use, else
-// batches of at most 6 GB.
+// decision: one batch (and bra-ket symmetry) when the integral block (plus the
+// split form's digit planes of one row chunk) fits in 70 % of the device
+// memory this context can use, else batches of at most 6 GB.
 void class_finish(qdt_ctx *ctx, ClassPlan &P, qdt_stats *st) {
     PairClass &pc = ctx->cls[P.cr.c];
     cudaStream_t s = ctx->stream;
@@ -463,8 +471,11 @@ void class_finish(qdt_ctx *ctx, ClassPlan &P, qdt_stats *st) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
     const size_t usable = (size_t)(0.7 * (double)(fr + ctx->W.n + ctx->Wc.n + split_held_bytes(ctx->split)));
-    const double wfac = (P.precision == QDT_SPLIT ? 2.5 : 1.0) * ((P.ls && P.cr.gauge && P.cr.gaunt) ? 1.12 : 1.0);
-    P.one_batch = (double)wall * wfac <= (double)usable;
+    const double wfac = (P.ls && P.cr.gauge && P.cr.gaunt) ? 1.12 : 1.0;
+    const double slices = P.precision == QDT_SPLIT ? 1.1 * (double)kSliceBudget : 0.0;
+    P.one_batch = (double)wall * wfac + slices <= (double)usable;
+    // what the decision counted as reusable is handed back first
+    if (P.one_batch && (double)wall * wfac + slices > 0.7 * (double)(fr + ctx->W.n + ctx->Wc.n)) split_release(ctx->split);
     P.wbudget = P.one_batch ? wall : ((size_t)6 << 30);
     P.h_kpos.assign(pc.nsp, 0);
     for (int q = 0; q < pc.nsp; ++q) P.h_kpos[P.h_ketsp[q]] = q;
@@ -560,18 +571,17 @@ void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, qdt_stats 
     const int TMr = gemm_fp64_tile_m();
     long long v = 0;
     double fl = 0.0;
-    const int NC = B.prm.gauge ? 7 : 1;
+    const bool gauge = B.prm.gauge != 0;
     for (int k = B.b0; k < B.b1; ++k) {
         int sp = pc.bra_order[k];
         const PairDev &ab = pc.h_pairs[sp];
         v += (long long)ab.nfp * P.Krow[sp];
-        // E R E contraction of every kept quartet: per primitive quartet
-        // 2 nha ncd nhc NC, per bra primitive pair 2 nab ncd nha NC.
+        // E R E contraction of every kept quartet, cheaper orientation
         for (int q = 0; q < P.h_prefix[sp]; ++q) {
             const int cid = P.h_ketsp[q];
             const PairDev &cd = pc.h_pairs[cid];
             if (P.one_batch && cid < sp && P.h_kpos[sp] < P.h_prefix[cid]) continue;
-            fl += 2.0 * NC * std::min(orient_cost_h(ab, cd), orient_cost_h(cd, ab));
+            fl += 2.0 * std::min(orient_cost_h(ab, cd, gauge), orient_cost_h(cd, ab, gauge));
         }
     }
     st->eri_values += v * (B.prm.gauge ? 6 : 1);
@@ -588,27 +598,53 @@ void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, qdt_stats 
     }
 }
 
+// QDT_SPLIT_CHUNK_ROWS (a positive multiple of 128) caps the rows per call.
+long long split_chunk_rows(long long ldw) {
+    if (const char *e = std::getenv("QDT_SPLIT_CHUNK_ROWS")) {
+        const long long r = std::atoll(e);
+        if (r > 0 && r % 128 == 0) return r;
+        throw Error{QDT_ERR_ARG, "QDT_SPLIT_CHUNK_ROWS must be a positive multiple of 128"};
+    }
+    const long long per_row = 12 * std::max<long long>(ldw, 1) + 64;
+    long long r = (long long)(kSliceBudget / (size_t)per_row);
+    r = std::max<long long>(128, r / 128 * 128);
+    return r;
+}
+
+// V rows = W D_ket over `rows` W rows from row 0, in row chunks for the split
+// form (launches only).
+void half1_rows(qdt_ctx *ctx, int precision, const double *W, long long ldw, const double *B, long long ldb,
+                double *C, long long ldc, long long rows, long long N, const long long *d_kt,
+                const std::vector<long long> &kt, cudaStream_t s) {
+    const int TMr = gemm_fp64_tile_m();
+    const long long chunk = precision == QDT_SPLIT ? split_chunk_rows(ldw) : std::max<long long>(rows, 1);
+    for (long long r0 = 0; r0 < rows; r0 += chunk) {
+        const long long m = std::min(chunk, rows - r0);
+        const size_t t0 = (size_t)(r0 / TMr), t1 = std::min(kt.size(), (size_t)((r0 + m + TMr - 1) / TMr));
+        const std::vector<long long> sub(kt.begin() + t0, kt.begin() + t1);
+        gemm_half1(ctx->split, precision, W + r0 * ldw, ldw, B, ldb, C + r0 * ldc, ldc, m, N, d_kt + t0, sub, s);
+        ctx->launches++;
+    }
+}
+
 // First half of a batch: V rows = W D_ket (launches only).
 void batch_half1(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, cudaStream_t s) {
     const long long N4 = P.N4;
     if (!P.ls) {
-        gemm_half1(ctx->split, P.precision, B.W, B.ldw, P.Dket, N4, P.Vc + B.row0 * N4, N4, B.rows, N4, B.d_kt, B.kt, s);
-        ctx->launches++;
+        half1_rows(ctx, P.precision, B.W, B.ldw, P.Dket, N4, P.Vc + B.row0 * N4, N4, B.rows, N4, B.d_kt, B.kt, s);
         return;
     }
     if (P.cr.gauge) {
         // gauge: rows (ab, I), K (cd, J): D_ket viewed as [(cd, J)][4 nRS]
-        gemm_half1(ctx->split, P.precision, B.W, B.ldw, P.Dket, N4, P.Vg + B.row0 * 3 * N4, N4, B.rows * 3, N4,
-                   B.d_kt, B.kt, s);
-        ctx->launches++;
+        half1_rows(ctx, P.precision, B.W, B.ldw, P.Dket, N4, P.Vg + B.row0 * 3 * N4, N4, B.rows * 3, N4, B.d_kt,
+                   B.kt, s);
     }
     if (P.cr.gaunt) {
         // Gaunt: Coulomb integrals over L-S pairs, N = 12 nRS
         const double *Wg = P.cr.gauge ? B.Wc : B.W;
         const long long ldg = P.cr.gauge ? B.ldwc : B.ldw;
-        gemm_half1(ctx->split, P.precision, Wg, ldg, P.Dket, 3 * N4, P.Vc + B.row0 * 3 * N4, 3 * N4, B.rows, 3 * N4,
+        half1_rows(ctx, P.precision, Wg, ldg, P.Dket, 3 * N4, P.Vc + B.row0 * 3 * N4, 3 * N4, B.rows, 3 * N4,
                    B.d_kg, B.kg, s);
-        ctx->launches++;
     }
 }
 

@@ -192,3 +192,20 @@ def test_argument_errors(torch_cuda):
     with pytest.raises(qdt.QdtError) as e:
         ctx.set_basis(bad.basis)                        # f shells are not accepted
     assert e.value.code == -1
+
+
+def test_split_first_half_in_row_chunks(oracle, torch_cuda, monkeypatch):
+    """The split form's first half runs in row chunks when the digit planes of
+    all integral rows would exceed their budget; chunks of 128 rows must give
+    the same result as one call (same digits, same products)."""
+    torch = torch_cuda
+    p = synth.chain_problem(6, 4, seed=311, shells=(0, 1), nprim=2, blocks=("coulomb", "gaunt", "gauge"),
+                            tau=1e-12)
+    _, whole, _ = run_gpu(torch, p, list(p.blocks), 0, p.nK, p.tau, precision=1)
+    monkeypatch.setenv("QDT_SPLIT_CHUNK_ROWS", "128")
+    _, chunked, st = run_gpu(torch, p, list(p.blocks), 0, p.nK, p.tau, precision=1)
+    monkeypatch.delenv("QDT_SPLIT_CHUNK_ROWS")
+    assert np.array_equal(chunked, whole)
+    tr = oracle.Transform(p)
+    for i, b in enumerate(p.blocks):
+        assert np.abs(chunked[i] - tr.packed(b).reshape(-1)).max() <= 1e-10
