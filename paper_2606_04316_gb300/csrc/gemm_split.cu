@@ -373,10 +373,12 @@ __global__ void __launch_bounds__(128, 1)
             tmem_ld16(trow + 0 * SBN + q * 16, v0);
             tmem_ld16(trow + 1 * SBN + q * 16, v1);
             tmem_ld16(trow + 2 * SBN + q * 16, v2);
+            // |sums| < 3 * 127^2 * 256 < 2^24: integers exact in FP32 and in 32-bit ints;
+            // 32-bit conversions and 64-bit integer adds keep the FP64 pipe free
 #pragma unroll
             for (int t = 0; t < 16; ++t)
-                acc[q * 16 + t] += ((long long)__float2ll_rn(v0[t]) << 14) + ((long long)__float2ll_rn(v1[t]) << 7) +
-                                   (long long)__float2ll_rn(v2[t]);
+                acc[q * 16 + t] += ((long long)__float2int_rn(v0[t]) << 14) + ((long long)__float2int_rn(v1[t]) << 7) +
+                                   (long long)__float2int_rn(v2[t]);
         }
         tc_fence_before();
         __syncthreads();
@@ -397,9 +399,14 @@ __global__ void __launch_bounds__(128, 1)
                 for (int t = 0; t < 16; ++t) {
                     long long n = n0 + q * 16 + t;
                     if (n < Nvalid) {
-                        double v = ldexp((double)acc[q * 16 + t], -28) + ldexp((double)v3[t], -35) +
-                                   ldexp((double)v4[t], -42) + ldexp((double)v5[t], -49);
-                        C[m * ldc + n] = ldexp(v, er + colexp[n]);
+                        // diagonals 5, 6, 7 (weights 2^-35, -42, -49) folded in FP32, whose
+                        // rounding is ~2^-59 of the result; then acc (weight 2^-28) in FP64
+                        const float w = fmaf(v5[t], 0x1p-14f, fmaf(v4[t], 0x1p-7f, v3[t]));
+                        const double v = fma((double)w, 0x1p-7, (double)acc[q * 16 + t]);
+                        const int k = er + colexp[n] - 28;
+                        C[m * ldc + n] = (k > -1022 && k < 1023)
+                                             ? v * __longlong_as_double((long long)(k + 1023) << 52)
+                                             : ldexp(v, k);
                     }
                 }
             }
