@@ -16,8 +16,11 @@
 //  Tensor-core kernel: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), M = 128,
 //  N = 64, operands K-major in shared memory with the 128-byte swizzle, staged
 //  by TMA (cp.async.bulk.tensor) through a 3-deep mbarrier pipeline; six FP32
-//  accumulators (384 TMEM columns) per CTA; every wait is bounded and reports
-//  a timeout through a device status word instead of hanging.
+//  accumulators (384 TMEM columns) per CTA.  Roles: one thread issues the TMA
+//  loads, one the MMAs (its loops unrolled over the digit pairs, so stage,
+//  barrier phase, accumulator and descriptors are compile-time constants), four
+//  warps fold the exact diagonals and write the result.  Every wait is bounded
+//  and reports a timeout through a device status word instead of hanging.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -275,9 +278,16 @@ __device__ inline void tmem_ld16(uint32_t taddr, float *v) {
 }
 
 // ------------------------------------------------------------ GEMM kernel
+__device__ inline void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+constexpr int kThreads = 192;       // warps 0-3 fold and write, warp 4 loads, warp 5 issues MMAs
+static_assert(kSlices % kStages == 0, "a K subtile's steps must map onto the stages in a fixed pattern");
+
 // C[M x N] (FP64, ld ldc) = sum of digit products of A slices (tmA rows
 // i*Mpad + m) and B slices (tmB rows j*Npad + n), K extent per 128-row tile.
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     ozaki_umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       long long Mpad, long long Npad, const long long *__restrict__ ktile,
                       const int *__restrict__ rowexp, const int *__restrict__ colexp, double *C, long long ldc,
@@ -286,18 +296,20 @@ __global__ void __launch_bounds__(128, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long m0 = (long long)blockIdx.y * SBM, n0 = (long long)blockIdx.x * SBN;
     if (upper_only && (m0 / 4) > (n0 + SBN - 1) / 4) return;   // below the block diagonal: unused
+    if (*(volatile int *)status) return;                       // an earlier CTA gave up: skip the work
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(base + kStages * kStageBytes);
     uint64_t *empty = full + kStages;
-    uint64_t *chunk_bar = empty + kStages;
-    uint32_t *tslot = (uint32_t *)(chunk_bar + 1);
+    uint64_t *chunk_bar = empty + kStages;     // a chunk's MMAs finished
+    uint64_t *folded = chunk_bar + 1;          // the exact accumulators were read (4 warps)
+    uint64_t *done = folded + 1;               // every MMA finished
+    uint32_t *tslot = (uint32_t *)(done + 1);
     __shared__ int abort_flag;
 
     const long long K = ktile[blockIdx.y];
     const int nk = (int)((K + SBK - 1) / SBK);
-    long long acc[SBN];
-#pragma unroll
-    for (int j = 0; j < SBN; ++j) acc[j] = 0;
+    const int total = nk * kSlices;                    // pipeline steps: (k subtile, A slice)
+    const int nchunks = (nk + kChunkSub - 1) / kChunkSub;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(tslot)));
@@ -306,6 +318,8 @@ __global__ void __launch_bounds__(128, 1)
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
         mbar_init(chunk_bar, 1);
+        mbar_init(folded, 4);
+        mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
@@ -313,116 +327,135 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const int total = nk * kSlices;                    // pipeline steps: (k subtile, A slice)
-    const int nchunks = (nk + kChunkSub - 1) / kChunkSub;
 
-    auto load_step = [&](int s) {
-        int st = s % kStages, kt = s / kSlices, i = s % kSlices;
-        uint8_t *sa = base + st * kStageBytes, *sb = sa + kATile;
-        int nb = kSlices - i;                          // B slices j with i + j <= 5 (0-based)
-        mbar_expect_tx(full + st, kATile + nb * kBTile);
-        tma_load(sa, &tmA, kt * SBK, (int)(i * Mpad + m0), full + st);
-        for (int j = 0; j < nb; ++j)
-            tma_load(sb + j * kBTile, &tmB, kt * SBK, (int)(j * Npad + n0), full + st);
-    };
-
-    bool ok = true;
-    if (tid == 0)
-        for (int s = 0; s < min(kStages, total); ++s) load_step(s);
-    for (int c = 0; c < nchunks; ++c) {
-        if (tid == 0 && ok) {
-            bool fresh[kSlices];
-            for (int a = 0; a < kSlices; ++a) fresh[a] = (a < 3) || (c == 0);
-            int s_begin = c * kChunkSub * kSlices, s_end = min(total, (c + 1) * kChunkSub * kSlices);
-            for (int s = s_begin; s < s_end && ok; ++s) {
-                int st = s % kStages;
-                if (!mbar_wait(full + st, (uint32_t)((s / kStages) & 1))) { ok = false; break; }
-                tc_fence_after();
-                int i = s % kSlices;
-                uint32_t sa = su32(base + st * kStageBytes), sb = sa + kATile;
-                for (int j = 0; j < kSlices - i; ++j) {
-                    int a = i + j;
-                    for (int k16 = 0; k16 < SBK / 16; ++k16) {
-                        umma(tmem + (uint32_t)(a * SBN), sdesc(sa + k16 * 32), sdesc(sb + j * kBTile + k16 * 32),
-                             fresh[a] ? 0u : 1u);
-                        fresh[a] = false;
-                    }
+    if (warp == 4) {
+        if (lane == 0) {                               // TMA producer
+            for (int s = 0; s < total; ++s) {
+                const int st = s % kStages, kt = s / kSlices, i = s % kSlices;
+                if (s >= kStages && !mbar_wait(empty + st, (uint32_t)(((s / kStages) - 1) & 1))) {
+                    abort_flag = 1;
+                    break;
                 }
-                umma_commit(empty + st);
-                if (s >= 1) {
-                    int prev = s - 1;
-                    if (prev + kStages < total) {
-                        if (!mbar_wait(empty + prev % kStages, (uint32_t)((prev / kStages) & 1))) { ok = false; break; }
-                        load_step(prev + kStages);
-                    }
-                }
+                if (*(volatile int *)&abort_flag) break;
+                uint8_t *sa = base + st * kStageBytes, *sb = sa + kATile;
+                const int nb = kSlices - i;            // B slices j with i + j <= 5 (0-based)
+                mbar_expect_tx(full + st, kATile + nb * kBTile);
+                tma_load(sa, &tmA, kt * SBK, (int)(i * Mpad + m0), full + st);
+                for (int j = 0; j < nb; ++j) tma_load(sb + j * kBTile, &tmB, kt * SBK, (int)(j * Npad + n0), full + st);
             }
-            if (ok) umma_commit(chunk_bar);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {                               // MMA issuer
+            bool ok = true;
+            const uint64_t d0 = sdesc(su32(base));
+            for (int c = 0; c < nchunks && ok; ++c) {
+                // the exact accumulators of chunk c - 1 must be folded before they are overwritten
+                if (c > 0 && !mbar_wait(folded, (uint32_t)((c - 1) & 1))) { ok = false; break; }
+                tc_fence_after();
+                const int kt1 = min(nk, (c + 1) * kChunkSub);
+                for (int kt = c * kChunkSub; kt < kt1 && ok; ++kt) {
+                    const bool chunk_first = kt == c * kChunkSub, first_kt = kt == 0;
+#pragma unroll
+                    for (int i = 0; i < kSlices; ++i) {
+                        // step s = 6 kt + i uses stage i % 3, for the (2 kt + i / 3)-th time
+                        const int st = i % kStages;
+                        if (!mbar_wait(full + st, (uint32_t)((i / kStages) & 1)) || *(volatile int *)&abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t da = d0 + (uint64_t)((st * kStageBytes) >> 4);
+                        const uint64_t db = da + (uint64_t)(kATile >> 4);
+#pragma unroll
+                        for (int j = 0; j < kSlices - i; ++j) {
+                            const int a = i + j;
+                            const bool fresh_i = i == 0 && (a <= 2 ? chunk_first : first_kt);
+#pragma unroll
+                            for (int k16 = 0; k16 < SBK / 16; ++k16)
+                                umma(tmem + (uint32_t)(a * SBN), da + (uint64_t)(2 * k16),
+                                     db + (uint64_t)(j * (kBTile >> 4) + 2 * k16), (fresh_i && k16 == 0) ? 0u : 1u);
+                        }
+                        umma_commit(empty + st);
+                    }
+                }
+                if (ok) umma_commit(chunk_bar);
+            }
+            umma_commit(done);                         // also on abort: lets issued MMAs be awaited
             if (!ok) abort_flag = 1;
         }
-        __syncthreads();
-        if (abort_flag) break;
-        bool mine = mbar_wait(chunk_bar, (uint32_t)(c & 1));
-        if (__syncthreads_or(!mine)) { if (tid == 0) abort_flag = 1; break; }
-        tc_fence_after();
-        // fold the exact diagonals (accumulators 0, 1, 2) into the integer accumulator
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    } else {                                           // warps 0-3: rows 32 warp .. + 31
+        long long acc[SBN];
 #pragma unroll
-        for (int q = 0; q < SBN / 16; ++q) {
-            float v0[16], v1[16], v2[16];
-            tmem_ld16(trow + 0 * SBN + q * 16, v0);
-            tmem_ld16(trow + 1 * SBN + q * 16, v1);
-            tmem_ld16(trow + 2 * SBN + q * 16, v2);
-            // |sums| < 3 * 127^2 * 256 < 2^24: integers exact in FP32 and in 32-bit ints;
+        for (int j = 0; j < SBN; ++j) acc[j] = 0;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            if (!mbar_wait(chunk_bar, (uint32_t)(c & 1)) || *(volatile int *)&abort_flag) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            // fold the exact diagonals (accumulators 0, 1, 2) into the integer accumulator;
+            // |sums| < 3 * 127^2 * 256 < 2^24: integers exact in FP32 and in 32-bit ints,
             // 32-bit conversions and 64-bit integer adds keep the FP64 pipe free
 #pragma unroll
-            for (int t = 0; t < 16; ++t)
-                acc[q * 16 + t] += ((long long)__float2int_rn(v0[t]) << 14) + ((long long)__float2int_rn(v1[t]) << 7) +
-                                   (long long)__float2int_rn(v2[t]);
+            for (int q = 0; q < SBN / 16; ++q) {
+                float v0[16], v1[16], v2[16];
+                tmem_ld16(trow + 0 * SBN + q * 16, v0);
+                tmem_ld16(trow + 1 * SBN + q * 16, v1);
+                tmem_ld16(trow + 2 * SBN + q * 16, v2);
+#pragma unroll
+                for (int t = 0; t < 16; ++t)
+                    acc[q * 16 + t] += ((long long)__float2int_rn(v0[t]) << 14) +
+                                       ((long long)__float2int_rn(v1[t]) << 7) + (long long)__float2int_rn(v2[t]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(folded);
         }
-        tc_fence_before();
-        __syncthreads();
-    }
-    if (!abort_flag && nk > 0) {
-        tc_fence_after();
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         const long long m = m0 + warp * 32 + lane;
-        const int er = (m < Mpad) ? rowexp[m] : 0;
+        if (ok && nk > 0 && !mbar_wait(done, 0)) ok = false;
+        if (!ok) {
+            abort_flag = 1;
+        } else if (nk > 0) {
+            tc_fence_after();
+            const int er = (m < Mpad) ? rowexp[m] : 0;
 #pragma unroll
-        for (int q = 0; q < SBN / 16; ++q) {
-            float v3[16], v4[16], v5[16];
-            tmem_ld16(trow + 3 * SBN + q * 16, v3);
-            tmem_ld16(trow + 4 * SBN + q * 16, v4);
-            tmem_ld16(trow + 5 * SBN + q * 16, v5);
-            if (m < Mvalid) {
+            for (int q = 0; q < SBN / 16; ++q) {
+                float v3[16], v4[16], v5[16];
+                tmem_ld16(trow + 3 * SBN + q * 16, v3);
+                tmem_ld16(trow + 4 * SBN + q * 16, v4);
+                tmem_ld16(trow + 5 * SBN + q * 16, v5);
+                if (m < Mvalid) {
 #pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    long long n = n0 + q * 16 + t;
-                    if (n < Nvalid) {
-                        // diagonals 5, 6, 7 (weights 2^-35, -42, -49) folded in FP32, whose
-                        // rounding is ~2^-59 of the result; then acc (weight 2^-28) in FP64
-                        const float w = fmaf(v5[t], 0x1p-14f, fmaf(v4[t], 0x1p-7f, v3[t]));
-                        const double v = fma((double)w, 0x1p-7, (double)acc[q * 16 + t]);
-                        const int k = er + colexp[n] - 28;
-                        C[m * ldc + n] = (k > -1022 && k < 1023)
-                                             ? v * __longlong_as_double((long long)(k + 1023) << 52)
-                                             : ldexp(v, k);
+                    for (int t = 0; t < 16; ++t) {
+                        const long long n = n0 + q * 16 + t;
+                        if (n < Nvalid) {
+                            // diagonals 5, 6, 7 (weights 2^-35, -42, -49) folded in FP32, whose
+                            // rounding is ~2^-59 of the result; then acc (weight 2^-28) in FP64
+                            const float w = fmaf(v5[t], 0x1p-14f, fmaf(v4[t], 0x1p-7f, v3[t]));
+                            const double v = fma((double)w, 0x1p-7, (double)acc[q * 16 + t]);
+                            const int k = er + colexp[n] - 28;
+                            C[m * ldc + n] = (k > -1022 && k < 1023)
+                                                 ? v * __longlong_as_double((long long)(k + 1023) << 52)
+                                                 : ldexp(v, k);
+                        }
                     }
                 }
             }
-        }
-    } else if (!abort_flag && nk == 0) {
-        const long long m = m0 + warp * 32 + lane;
-        if (m < Mvalid)
+        } else if (m < Mvalid) {
             for (int t = 0; t < SBN; ++t)
                 if (n0 + t < Nvalid) C[m * ldc + n0 + t] = 0.0;
+        }
     }
+    tc_fence_before();
+    __syncthreads();
     if (abort_flag && tid == 0) {
         atomicExch(status, 1);
         // let copies and MMAs in flight land before the CTA exits (bounded)
+        mbar_wait(done, 0);
         for (int s = 0; s < kStages; ++s) { mbar_wait(full + s, 0); mbar_wait(full + s, 1); }
     }
-    tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
@@ -487,7 +520,7 @@ static void run_umma(SplitWorkspace &w, void *Asl, long long Mpad, long long Kpa
     if (!w.deferred) QDT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
     QDT_CUDA_TRY(cudaFuncSetAttribute(ozaki_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     dim3 grid((unsigned)(Npad / SBN), (unsigned)(Mpad / SBM));
-    ozaki_umma_kernel<<<grid, 128, kSmemBytes, s>>>(ta, tb, Mpad, Npad, d_kt128, rowexp, colexp, C, ldc, M, N,
+    ozaki_umma_kernel<<<grid, kThreads, kSmemBytes, s>>>(ta, tb, Mpad, Npad, d_kt128, rowexp, colexp, C, ldc, M, N,
                                                     upper, status);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) {
