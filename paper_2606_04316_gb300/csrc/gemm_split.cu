@@ -15,11 +15,13 @@
 //
 //  Tensor-core kernel: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), M = 128,
 //  N = 64, operands K-major in shared memory with the 128-byte swizzle, staged
-//  by TMA (cp.async.bulk.tensor) through a 3-deep mbarrier pipeline; six FP32
-//  accumulators (384 TMEM columns) per CTA.  Roles: one thread issues the TMA
-//  loads, one the MMAs (its loops unrolled over the digit pairs, so stage,
-//  barrier phase, accumulator and descriptors are compile-time constants), four
-//  warps fold the exact diagonals and write the result.  Every wait is bounded
+//  by TMA (cp.async.bulk.tensor): per K subtile of 64 the six B planes are
+//  loaded once into one of two panels and the six A planes into one stage
+//  each, all tracked by mbarriers; six FP32 accumulators (384 TMEM columns)
+//  per CTA.  Roles: one thread issues the TMA loads, one the MMAs (its loops
+//  unrolled over the digit pairs, so A stage, barrier phase, accumulator and
+//  descriptors are compile-time constants), four warps fold the exact
+//  diagonals and write the result.  Every wait is bounded
 //  and reports a timeout through a device status word instead of hanging.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -37,11 +39,11 @@ constexpr int kBits = 7;
 constexpr int kFrac = kSlices * kBits;       // 42 fractional bits
 constexpr int SBM = 128, SBN = 64, SBK = 64;
 constexpr int kChunkSub = 4;                  // 4 x 64 = 256 K per exact chunk
-constexpr int kStages = 3;
-constexpr int kATile = SBM * SBK * 2;         // 16 KB
-constexpr int kBTile = SBN * SBK * 2;         // 8 KB
-constexpr int kStageBytes = kATile + kSlices * kBTile;   // 64 KB
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr int kATile = SBM * SBK * 2;         // 16 KB: one A digit plane of a K subtile
+constexpr int kBTile = SBN * SBK * 2;         // 8 KB: one B digit plane
+constexpr int kBPanel = kSlices * kBTile;     // 48 KB: the six B planes of a K subtile
+// shared memory: one stage per A plane (6 x 16 KB) and two B panels (2 x 48 KB)
+constexpr int kSmemBytes = kSlices * kATile + 2 * kBPanel + 1024 + 256;
 constexpr long long kWaitNs = 2000000000LL;   // 2 s bound on every wait
 
 // ------------------------------------------------------------ workspace
@@ -283,7 +285,6 @@ __device__ inline void mbar_arrive(uint64_t *b) {
 }
 
 constexpr int kThreads = 192;       // warps 0-3 fold and write, warp 4 loads, warp 5 issues MMAs
-static_assert(kSlices % kStages == 0, "a K subtile's steps must map onto the stages in a fixed pattern");
 
 // C[M x N] (FP64, ld ldc) = sum of digit products of A slices (tmA rows
 // i*Mpad + m) and B slices (tmB rows j*Npad + n), K extent per 128-row tile.
@@ -298,9 +299,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (upper_only && (m0 / 4) > (n0 + SBN - 1) / 4) return;   // below the block diagonal: unused
     if (*(volatile int *)status) return;                       // an earlier CTA gave up: skip the work
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = (uint64_t *)(base + kStages * kStageBytes);
-    uint64_t *empty = full + kStages;
-    uint64_t *chunk_bar = empty + kStages;     // a chunk's MMAs finished
+    uint8_t *bpanel = base + kSlices * kATile;                  // two B panels after the six A stages
+    uint64_t *afull = (uint64_t *)(bpanel + 2 * kBPanel);
+    uint64_t *aempty = afull + kSlices;
+    uint64_t *bfull = aempty + kSlices;        // [2]
+    uint64_t *bempty = bfull + 2;              // [2]
+    uint64_t *chunk_bar = bempty + 2;          // a chunk's MMAs finished
     uint64_t *folded = chunk_bar + 1;          // the exact accumulators were read (4 warps)
     uint64_t *done = folded + 1;               // every MMA finished
     uint32_t *tslot = (uint32_t *)(done + 1);
@@ -308,7 +312,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const long long K = ktile[blockIdx.y];
     const int nk = (int)((K + SBK - 1) / SBK);
-    const int total = nk * kSlices;                    // pipeline steps: (k subtile, A slice)
     const int nchunks = (nk + kChunkSub - 1) / kChunkSub;
 
     if (warp == 0) {
@@ -316,7 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+        for (int i = 0; i < kSlices; ++i) { mbar_init(afull + i, 1); mbar_init(aempty + i, 1); }
+        for (int p = 0; p < 2; ++p) { mbar_init(bfull + p, 1); mbar_init(bempty + p, 1); }
         mbar_init(chunk_bar, 1);
         mbar_init(folded, 4);
         mbar_init(done, 1);
@@ -330,24 +334,28 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 4) {
         if (lane == 0) {                               // TMA producer
-            for (int s = 0; s < total; ++s) {
-                const int st = s % kStages, kt = s / kSlices, i = s % kSlices;
-                if (s >= kStages && !mbar_wait(empty + st, (uint32_t)(((s / kStages) - 1) & 1))) {
-                    abort_flag = 1;
-                    break;
+            bool ok = true;
+            for (int kt = 0; kt < nk && ok; ++kt) {
+                const int p = kt & 1;
+                // B panel of subtile kt: the panel's previous user is subtile kt - 2
+                if (kt >= 2 && !mbar_wait(bempty + p, (uint32_t)(((kt >> 1) - 1) & 1))) { ok = false; break; }
+                mbar_expect_tx(bfull + p, kBPanel);
+                for (int j = 0; j < kSlices; ++j)
+                    tma_load(bpanel + p * kBPanel + j * kBTile, &tmB, kt * SBK, (int)(j * Npad + n0), bfull + p);
+                // A planes: stage i's previous user is subtile kt - 1
+                for (int i = 0; i < kSlices; ++i) {
+                    if (kt >= 1 && !mbar_wait(aempty + i, (uint32_t)((kt - 1) & 1))) { ok = false; break; }
+                    if (*(volatile int *)&abort_flag) { ok = false; break; }
+                    mbar_expect_tx(afull + i, kATile);
+                    tma_load(base + i * kATile, &tmA, kt * SBK, (int)(i * Mpad + m0), afull + i);
                 }
-                if (*(volatile int *)&abort_flag) break;
-                uint8_t *sa = base + st * kStageBytes, *sb = sa + kATile;
-                const int nb = kSlices - i;            // B slices j with i + j <= 5 (0-based)
-                mbar_expect_tx(full + st, kATile + nb * kBTile);
-                tma_load(sa, &tmA, kt * SBK, (int)(i * Mpad + m0), full + st);
-                for (int j = 0; j < nb; ++j) tma_load(sb + j * kBTile, &tmB, kt * SBK, (int)(j * Npad + n0), full + st);
             }
+            if (!ok) abort_flag = 1;
         }
     } else if (warp == 5) {
         if (lane == 0) {                               // MMA issuer
             bool ok = true;
-            const uint64_t d0 = sdesc(su32(base));
+            const uint64_t da0 = sdesc(su32(base)), db0 = sdesc(su32(bpanel));
             for (int c = 0; c < nchunks && ok; ++c) {
                 // the exact accumulators of chunk c - 1 must be folded before they are overwritten
                 if (c > 0 && !mbar_wait(folded, (uint32_t)((c - 1) & 1))) { ok = false; break; }
@@ -355,17 +363,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int kt1 = min(nk, (c + 1) * kChunkSub);
                 for (int kt = c * kChunkSub; kt < kt1 && ok; ++kt) {
                     const bool chunk_first = kt == c * kChunkSub, first_kt = kt == 0;
+                    const int p = kt & 1;
+                    if (!mbar_wait(bfull + p, (uint32_t)((kt >> 1) & 1))) { ok = false; break; }
+                    const uint64_t db = db0 + (uint64_t)((p * kBPanel) >> 4);
 #pragma unroll
                     for (int i = 0; i < kSlices; ++i) {
-                        // step s = 6 kt + i uses stage i % 3, for the (2 kt + i / 3)-th time
-                        const int st = i % kStages;
-                        if (!mbar_wait(full + st, (uint32_t)((i / kStages) & 1)) || *(volatile int *)&abort_flag) {
+                        if (!mbar_wait(afull + i, (uint32_t)(kt & 1)) || *(volatile int *)&abort_flag) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint64_t da = d0 + (uint64_t)((st * kStageBytes) >> 4);
-                        const uint64_t db = da + (uint64_t)(kATile >> 4);
+                        const uint64_t da = da0 + (uint64_t)((i * kATile) >> 4);
 #pragma unroll
                         for (int j = 0; j < kSlices - i; ++j) {
                             const int a = i + j;
@@ -375,8 +383,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 umma(tmem + (uint32_t)(a * SBN), da + (uint64_t)(2 * k16),
                                      db + (uint64_t)(j * (kBTile >> 4) + 2 * k16), (fresh_i && k16 == 0) ? 0u : 1u);
                         }
-                        umma_commit(empty + st);
+                        umma_commit(aempty + i);
                     }
+                    if (ok) umma_commit(bempty + p);
                 }
                 if (ok) umma_commit(chunk_bar);
             }
@@ -454,7 +463,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         atomicExch(status, 1);
         // let copies and MMAs in flight land before the CTA exits (bounded)
         mbar_wait(done, 0);
-        for (int s = 0; s < kStages; ++s) { mbar_wait(full + s, 0); mbar_wait(full + s, 1); }
+        for (int i = 0; i < kSlices; ++i) { mbar_wait(afull + i, 0); mbar_wait(afull + i, 1); }
+        for (int q = 0; q < 2; ++q) { mbar_wait(bfull + q, 0); mbar_wait(bfull + q, 1); }
     }
     __syncthreads();
     if (warp == 0) {
