@@ -209,6 +209,7 @@ __global__ void prim_pair_kernel(const ShellDev *shells, const PairDev *pairs, c
         if (x == 0) {
             PrimPairDev o;
             o.p = p;
+            o.inv_p = 1.0 / p;
             for (int d = 0; d < 3; ++d) o.P[d] = (a * A.A[d] + b * B.A[d]) / p;
             o.eoff = pp[ipp].eoff;
             o.ia = ia;

@@ -24,6 +24,12 @@
 // primitive quartet; recursion sources and coefficients come from tables; the
 // sign (-1)^{|h'|} is a negated FMA operand (even and odd Hermite orders run in
 // separate loops) instead of a multiplication.
+//
+// Split form (DF): Boys values, prefactors and the Hermite recursion stay in
+// FP64; the two contraction passes run in compensated FP32 pairs (x = hi + lo,
+// ~48-bit significands): products by the exact-product FMA, sums by the
+// error-free two-sum, so each multiply-add costs about twelve FP32
+// operations, which issue 64 times faster than FP64 on this part.
 #include <math.h>
 
 #include "qdt_internal.cuh"
@@ -89,6 +95,67 @@ __device__ __forceinline__ double boys_eval(const double *tab, double T, int nma
     return e;
 }
 
+// Compensated FP32 pair arithmetic.  The intrinsics keep the compiler from
+// fusing the rounded product into the following sum.
+__device__ __forceinline__ float2 df_split(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// The same split by integer operations on the bits (no FP64 instruction):
+// hi = the top 24 significand bits of x, lo = the remaining 29 bits rounded to
+// FP32.  Magnitudes outside [2^-70, 2^120) take the FP64 route.
+__device__ __forceinline__ float2 df_split_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+    const int e = (int)((hi32 >> 20) & 0x7FF);
+    if (e < 1023 - 70 || e >= 1023 + 120) return df_split(x);
+    const unsigned sign = hi32 & 0x80000000u;
+    const float h = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | ((hi32 & 0xFFFFFu) << 3) |
+                                    (lo32 >> 29));
+    const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);   // 2^(e - 1075) >= 2^-122
+    const float l = __fmul_rn(__uint2float_rn(lo32 & 0x1FFFFFFFu), scale);
+    return make_float2(h, __uint_as_float(__float_as_uint(l) | sign));
+}
+
+// (ah, al) += sign * a * b: exact product error of the high parts plus the
+// cross terms, then the two-sum of the high parts.
+template <bool NEG>
+__device__ __forceinline__ void df_madd(float2 a, float2 b, float &ah, float &al) {
+    float p = __fmul_rn(a.x, b.x);
+    float pe = __fmaf_rn(a.x, b.x, -p);
+    pe = __fmaf_rn(a.x, b.y, pe);
+    pe = __fmaf_rn(a.y, b.x, pe);
+    if (NEG) { p = -p; pe = -pe; }
+    const float t = __fadd_rn(ah, p);
+    const float bv = __fsub_rn(t, ah);
+    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+    ah = t;
+    al = __fadd_rn(al, __fadd_rn(err, pe));
+}
+
+// x a + cf c in compensated FP32 pairs, renormalised (one Hermite recursion step).
+__device__ __forceinline__ float2 df_rec(float2 x, float2 a, float cf, float2 c) {
+    const float p1 = __fmul_rn(x.x, a.x);
+    float e1 = __fmaf_rn(x.x, a.x, -p1);
+    e1 = __fmaf_rn(x.x, a.y, e1);
+    e1 = __fmaf_rn(x.y, a.x, e1);
+    const float p2 = __fmul_rn(cf, c.x);
+    float e2 = __fmaf_rn(cf, c.x, -p2);
+    e2 = __fmaf_rn(cf, c.y, e2);
+    const float t = __fadd_rn(p1, p2);
+    const float bv = __fsub_rn(t, p1);
+    const float err = __fadd_rn(__fsub_rn(p1, __fsub_rn(t, bv)), __fsub_rn(p2, bv));
+    const float lo = __fadd_rn(err, __fadd_rn(e1, e2));
+    const float hi = __fadd_rn(t, lo);
+    return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, t)));
+}
+
+__global__ void split_pairs_kernel(const double *E, long long n, float2 *E2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) E2[i] = df_split(E[i]);
+}
+
 // Doubles of one primitive quartet's header: X_PQ (3), R^n_000 of the Coulomb
 // tensor (n = 0..L) and, for the gauge kernel, of the r12 tensor (n = 0..L+2).
 __host__ __device__ inline int header_len(int L, bool gauge) { return gauge ? 2 * L + 7 : L + 4; }
@@ -96,18 +163,19 @@ __host__ __device__ inline int quartet_len(int L, bool gauge) {
     return header_len(L, gauge) + 2 * (nherm(L) + (gauge ? nherm(L + 2) : 0));
 }
 
-template <bool GAUGE>
+template <bool GAUGE, bool DF>
 __device__ __forceinline__ void quartet_header(const double *boys, const PrimPairDev *pa, const PrimPairDev *pc,
                                                int L, double *hd) {
-    const double p = pa->p, q = pc->p, s = p + q, pq = p * q;
+    const double p = pa->p, q = pc->p, s = p + q;
     const double X = pa->P[0] - pc->P[0], Y = pa->P[1] - pc->P[1], Z = pa->P[2] - pc->P[2];
-    const double rho = pq / s;
+    const double inv_s = 1.0 / s;
+    const double rho = p * q * inv_s;
     const double T = rho * fma(X, X, fma(Y, Y, Z * Z));
     hd[0] = X;
     hd[1] = Y;
     hd[2] = Z;
     const double sq = sqrt(s);
-    const double d = 1.0 / (pq * sq);
+    const double d = pa->inv_p * pc->inv_p * inv_s * sq;      // 1 / (p q sqrt(p + q))
     const double m2r = -2.0 * rho;
     double fC = kTwoPi52 * d;
     if (!GAUGE) {
@@ -132,6 +200,11 @@ __device__ __forceinline__ void quartet_header(const double *boys, const PrimPai
             fR *= m2r;
             prev = cur;
         }
+    }
+    if (DF) {       // the recursion runs in compensated FP32 pairs: X_PQ and R^n_000 as (hi, lo)
+        float2 *h2 = reinterpret_cast<float2 *>(hd);
+        const int len = header_len(L, GAUGE);
+        for (int i = 0; i < len; ++i) h2[i] = df_split_bits(hd[i]);
     }
 }
 
@@ -173,7 +246,8 @@ __device__ inline BlockSmem carve(double *sm, const Plan &p) {
 }
 
 // Hermite triple h -> packed (t, u, v); recursion sources of R_h: direction,
-// h - e_dir, h - 2 e_dir and the coefficient (component - 1) of the latter.
+// h - e_dir, h - 2 e_dir and the coefficient (component - 1) of the latter
+// (also packed into bits 22..25 of the source word for the FP32-pair path).
 __device__ void build_tables(const Plan &p, BlockSmem &b) {
     for (int h = threadIdx.x; h < p.nTab; h += blockDim.x) {
         int t, u, v;
@@ -189,7 +263,7 @@ __device__ void build_tables(const Plan &p, BlockSmem &b) {
             i1 = hidx(t - dt, u - du, v - dv);
             if (c >= 2) i2 = hidx(t - 2 * dt, u - 2 * du, v - 2 * dv);
         }
-        b.src[h] = dir | (i1 << 2) | (i2 << 12);
+        b.src[h] = dir | (i1 << 2) | (i2 << 12) | ((c >= 2 ? c - 1 : 0) << 22);
         b.cf[h] = c >= 2 ? (double)(c - 1) : 0.0;
     }
     __syncthreads();
@@ -235,12 +309,31 @@ __device__ __forceinline__ void ket_orders(int n0, int Ly, int tx, int ux, int v
     }
 }
 
+// The same in compensated FP32 pairs (R, E and the accumulator as hi + lo).
+template <bool NEG>
+__device__ __forceinline__ void ket_orders_df(int n0, int Ly, int tx, int ux, int vx, const int *trip,
+                                              const float2 *Rq, int nr, const float2 *ey, int nfpY,
+                                              const long long *eoff, int nk, float &ah, float &al) {
+    for (int n = n0; n <= Ly; n += 2) {
+        const int hb = n ? nherm(n - 1) : 0, he = nherm(n);
+        for (int hp = hb; hp < he; ++hp) {
+            const int tq = trip[hp];
+            const int T0 = tx + (tq & 255), U0 = ux + ((tq >> 8) & 255), V0 = vx + (tq >> 16);
+            const int s = T0 + U0 + V0, w = U0 + V0;
+            const int i0 = s * (s + 1) * (s + 2) / 6 + w * (w + 1) / 2 + V0;
+            const float2 *e = ey + (size_t)hp * nfpY;
+            for (int kl = 0; kl < nk; ++kl) df_madd<NEG>(Rq[kl * nr + i0], __ldg(e + eoff[kl]), ah, al);
+        }
+    }
+}
+
 // One chunk (x in [x0,x1) of X, y in [y0,y1) of Y) of the block (X|Y);
 // results in b.G[comp][x][y].  NC = 1 (Coulomb) or 7 (gauge: [0] Coulomb,
 // [1..6] (xy|d_I d_J r|zw) for IJ = xx,xy,xz,yy,yz,zz).
-template <bool GAUGE>
-__device__ void block_chunk(const PrimPairDev *pp, const double *E, const double *boys, const PairDev &X,
-                            const PairDev &Y, int x0, int x1, int y0, int y1, const Plan &pl, BlockSmem &b) {
+template <bool GAUGE, bool DF>
+__device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2 *E2, const double *boys,
+                            const PairDev &X, const PairDev &Y, int x0, int x1, int y0, int y1, const Plan &pl,
+                            BlockSmem &b) {
     constexpr int NC = GAUGE ? 7 : 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int Lx = X.Lab, Ly = Y.Lab;
@@ -283,7 +376,7 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
             // Boys values, prefactors and X_PQ of every primitive quartet of the group
             for (int q = tid; q < nq; q += nt) {
                 const int ijl = q / nk, kl = q - ijl * nk;
-                quartet_header<GAUGE>(boys, pp + X.ppoff + i0 + ijl, pp + Y.ppoff + k0 + kl, L, H + (size_t)q * hs);
+                quartet_header<GAUGE, DF>(boys, pp + X.ppoff + i0 + ijl, pp + Y.ppoff + k0 + kl, L, H + (size_t)q * hs);
             }
             __syncthreads();
             // Hermite recursion, one auxiliary order per pass; order 0 ends in buffer 0
@@ -298,23 +391,35 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
                     const double *hd = H + (size_t)q * hs;
                     double *dst;
                     const double *src;
-                    double r0;
+                    int i0h;
                     if (!GAUGE || h < cC) {
                         dst = RC + ((size_t)cur * nq + q) * nrC;
                         src = RC + ((size_t)prv * nq + q) * nrC;
-                        r0 = hd[3 + m];
+                        i0h = 3 + m;
                     } else {
                         h -= cC;
                         dst = RR + ((size_t)cur * nq + q) * nrR;
                         src = RR + ((size_t)prv * nq + q) * nrR;
-                        r0 = hd[4 + L + m];
+                        i0h = 4 + L + m;
                     }
-                    double r = r0;
-                    if (h > 0) {
-                        const int sw = b.src[h];
-                        r = fma(b.cf[h], src[(sw >> 12) & 1023], hd[sw & 3] * src[(sw >> 2) & 1023]);
+                    if constexpr (DF) {
+                        const float2 *hd2 = reinterpret_cast<const float2 *>(hd);
+                        const float2 *src2 = reinterpret_cast<const float2 *>(src);
+                        float2 r = hd2[i0h];
+                        if (h > 0) {
+                            const int sw = b.src[h];
+                            r = df_rec(hd2[sw & 3], src2[(sw >> 2) & 1023], (float)((sw >> 22) & 15),
+                                       src2[(sw >> 12) & 1023]);
+                        }
+                        reinterpret_cast<float2 *>(dst)[h] = r;
+                    } else {
+                        double r = hd[i0h];
+                        if (h > 0) {
+                            const int sw = b.src[h];
+                            r = fma(b.cf[h], src[(sw >> 12) & 1023], hd[sw & 3] * src[(sw >> 2) & 1023]);
+                        }
+                        dst[h] = r;
                     }
-                    dst[h] = r;
                 }
                 __syncthreads();
             }
@@ -329,13 +434,23 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
                 const int tr = b.trip[h];
                 const int tx = tr & 255, ux = (tr >> 8) & 255, vx = tr >> 16;
                 double *Tq = T + (size_t)ijl * tsz + (size_t)hh * ych + yy;
-                double acc = *Tq;
                 const double *Rq = r12 ? RR + (size_t)ijl * nk * nrR : RC + (size_t)ijl * nk * nrC;
                 const int nr = r12 ? nrR : nrC;
-                const double *ey = E + (y0 + yy);
-                ket_orders<false>(0, Ly, tx, ux, vx, b.trip, Rq, nr, ey, Y.nfp, b.eY + k0, nk, acc);
-                ket_orders<true>(1, Ly, tx, ux, vx, b.trip, Rq, nr, ey, Y.nfp, b.eY + k0, nk, acc);
-                *Tq = acc;
+                if constexpr (DF) {
+                    float2 *T2 = reinterpret_cast<float2 *>(Tq);
+                    float ah = T2->x, al = T2->y;
+                    const float2 *R2 = reinterpret_cast<const float2 *>(Rq);
+                    const float2 *ey = E2 + (y0 + yy);
+                    ket_orders_df<false>(0, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, ah, al);
+                    ket_orders_df<true>(1, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, ah, al);
+                    *T2 = make_float2(ah, al);
+                } else {
+                    double acc = *Tq;
+                    const double *ey = E + (y0 + yy);
+                    ket_orders<false>(0, Ly, tx, ux, vx, b.trip, Rq, nr, ey, Y.nfp, b.eY + k0, nk, acc);
+                    ket_orders<true>(1, Ly, tx, ux, vx, b.trip, Rq, nr, ey, Y.nfp, b.eY + k0, nk, acc);
+                    *Tq = acc;
+                }
             }
             // the next group's header pass touches neither T nor R, and its
             // barrier orders this pass before the recursion overwrites R
@@ -346,34 +461,45 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
         for (int it = tid; it < xch * ych; it += nt) {
             const int xx = it / ych, yy = it - xx * ych;
             double s[NC];
+            float sh[NC], sl[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) s[c] = 0.0;
+            for (int c = 0; c < NC; ++c) { s[c] = 0.0; sh[c] = 0.f; sl[c] = 0.f; }
             for (int ijl = 0; ijl < nij; ++ijl) {
-                const double *e = E + b.eX[i0 + ijl] + (x0 + xx);
-                const double *Tq = T + (size_t)ijl * tsz + yy;
-                const double *Tr = Tq + (size_t)(nhx - 4) * ych;     // row of triple g: nhx + g - 4
+                const size_t off = (size_t)ijl * tsz + yy;
                 for (int h = 0; h < nhx; ++h) {
-                    const double ev = __ldg(e + (size_t)h * X.nfp);
-                    s[0] = fma(ev, Tq[(size_t)h * ych], s[0]);
+                    int g[6] = {0, 0, 0, 0, 0, 0};               // r12 rows, offset by nhx - 4
                     if (GAUGE) {
                         const int tr = b.trip[h];
                         const int u = (tr >> 8) & 255, v = tr >> 16;
                         const int o = (tr & 255) + u + v, w = u + v;
-                        const int b2 = (o + 2) * (o + 3) * (o + 4) / 6;
-                        const int g0 = b2 + w * (w + 1) / 2 + v;
-                        const int g1 = b2 + (w + 1) * (w + 2) / 2 + v;
-                        const int g3 = b2 + (w + 2) * (w + 3) / 2 + v;
-                        s[1] = fma(ev, Tr[(size_t)g0 * ych], s[1]);
-                        s[2] = fma(ev, Tr[(size_t)g1 * ych], s[2]);
-                        s[3] = fma(ev, Tr[(size_t)(g1 + 1) * ych], s[3]);
-                        s[4] = fma(ev, Tr[(size_t)g3 * ych], s[4]);
-                        s[5] = fma(ev, Tr[(size_t)(g3 + 1) * ych], s[5]);
-                        s[6] = fma(ev, Tr[(size_t)(g3 + 2) * ych], s[6]);
+                        const int b2 = (o + 2) * (o + 3) * (o + 4) / 6 + nhx - 4;
+                        g[0] = b2 + w * (w + 1) / 2 + v;
+                        g[1] = b2 + (w + 1) * (w + 2) / 2 + v;
+                        g[2] = g[1] + 1;
+                        g[3] = b2 + (w + 2) * (w + 3) / 2 + v;
+                        g[4] = g[3] + 1;
+                        g[5] = g[3] + 2;
+                    }
+                    if constexpr (DF) {
+                        const float2 *T2 = reinterpret_cast<const float2 *>(T) + off;
+                        const float2 ev = __ldg(E2 + b.eX[i0 + ijl] + (x0 + xx) + (size_t)h * X.nfp);
+                        df_madd<false>(ev, T2[(size_t)h * ych], sh[0], sl[0]);
+                        if (GAUGE)
+#pragma unroll
+                            for (int c = 1; c < NC; ++c) df_madd<false>(ev, T2[(size_t)g[c - 1] * ych], sh[c], sl[c]);
+                    } else {
+                        const double *Tq = T + off;
+                        const double ev = __ldg(E + b.eX[i0 + ijl] + (x0 + xx) + (size_t)h * X.nfp);
+                        s[0] = fma(ev, Tq[(size_t)h * ych], s[0]);
+                        if (GAUGE)
+#pragma unroll
+                            for (int c = 1; c < NC; ++c) s[c] = fma(ev, Tq[(size_t)g[c - 1] * ych], s[c]);
                     }
                 }
             }
 #pragma unroll
-            for (int c = 0; c < NC; ++c) b.G[((size_t)c * xch + xx) * ych + yy] += s[c];
+            for (int c = 0; c < NC; ++c)
+                b.G[((size_t)c * xch + xx) * ych + yy] += DF ? (double)sh[c] + (double)sl[c] : s[c];
         }
         __syncthreads();
     }
@@ -383,7 +509,7 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const double
 // takes tiles (bra shell pair x range of sorted ket positions) from the shared
 // counter until none are left.  A tile's parameter set comes from prms[req],
 // so one launch can mix the tiles of several transformations.
-template <bool GAUGE>
+template <bool GAUGE, bool DF>
 __global__ void __launch_bounds__(256, 2) eri_rows_kernel(const EriParams *prms, const EriTask *tasks, int ntasks,
                                                           int *next, Plan pl) {
     extern __shared__ double sm[];
@@ -418,7 +544,7 @@ __global__ void __launch_bounds__(256, 2) eri_rows_kernel(const EriParams *prms,
                 const int x1 = min(X.nfp, x0 + pl.ach);
                 for (int y0 = 0; y0 < Y.nfp; y0 += pl.cch) {
                     const int y1 = min(Y.nfp, y0 + pl.cch);
-                    block_chunk<GAUGE>(prm.pp, prm.E, prm.boys, X, Y, x0, x1, y0, y1, pl, b);
+                    block_chunk<GAUGE, DF>(prm.pp, prm.E, prm.E2, prm.boys, X, Y, x0, x1, y0, y1, pl, b);
                     const int xch = x1 - x0, ych = y1 - y0;
                     for (int idx = threadIdx.x; idx < xch * ych; idx += blockDim.x) {
                         const int xx = idx / ych, yy = idx - xx * ych;
@@ -506,35 +632,47 @@ int eri_default_threads(const EriShape &shape, bool gauge) {
 }
 
 namespace {
-template <bool GAUGE>
+template <bool GAUGE, bool DF>
 int resident_ctas(int threads, size_t smem) {
     int nb = 0, dev = 0, nsm = 0;
     QDT_CUDA_TRY(cudaGetDevice(&dev));
     QDT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    QDT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eri_rows_kernel<GAUGE>, threads, smem));
+    QDT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eri_rows_kernel<GAUGE, DF>, threads, smem));
     return (nb > 0 ? nb : 1) * nsm;
 }
 
-template <bool GAUGE>
+template <bool GAUGE, bool DF>
 void launch_rows(const EriParams *prms, const EriTask *tasks, int ntasks, int *next, const Plan &pl, int threads,
                  size_t smem, cudaStream_t s) {
-    QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_kernel<GAUGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = min(ntasks, resident_ctas<GAUGE>(threads, smem));
+    QDT_CUDA_TRY(cudaFuncSetAttribute(eri_rows_kernel<GAUGE, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    const int grid = min(ntasks, resident_ctas<GAUGE, DF>(threads, smem));
     QDT_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(int), s));
-    eri_rows_kernel<GAUGE><<<grid, threads, smem, s>>>(prms, tasks, ntasks, next, pl);
+    eri_rows_kernel<GAUGE, DF><<<grid, threads, smem, s>>>(prms, tasks, ntasks, next, pl);
 }
 }  // namespace
 
 void launch_eri(const EriParams *prms, const EriTask *tasks, int ntasks, int *next, const EriShape &shape,
-                bool gauge, const EriLaunch &how, cudaStream_t s) {
+                bool gauge, bool df, const EriLaunch &how, cudaStream_t s) {
     if (ntasks <= 0) return;
     const Plan pl = eri_plan(shape.maxnfp, shape.maxLab, shape.maxnpp, gauge);
     const size_t smem = plan_smem(pl);
     const int threads = how.threads > 0 ? how.threads : pl.threads;
     if (threads % 32 || threads > 256) throw Error{QDT_ERR_ARG, "integral kernel: threads must be 32..256, a multiple of 32"};
-    if (gauge) launch_rows<true>(prms, tasks, ntasks, next, pl, threads, smem, s);
-    else launch_rows<false>(prms, tasks, ntasks, next, pl, threads, smem, s);
+    if (gauge) {
+        if (df) launch_rows<true, true>(prms, tasks, ntasks, next, pl, threads, smem, s);
+        else launch_rows<true, false>(prms, tasks, ntasks, next, pl, threads, smem, s);
+    } else {
+        if (df) launch_rows<false, true>(prms, tasks, ntasks, next, pl, threads, smem, s);
+        else launch_rows<false, false>(prms, tasks, ntasks, next, pl, threads, smem, s);
+    }
     QDT_CHECK_KERNEL("eri_rows_kernel");
+}
+
+void launch_split_pairs(const double *E, long long n, float2 *E2, cudaStream_t s) {
+    if (n <= 0) return;
+    split_pairs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E, n, E2);
+    QDT_CHECK_KERNEL("split_pairs_kernel");
 }
 
 // Schwarz diagonals: Q[AB] = max over ab of sqrt(|(ab|ab)|), Coulomb kernel.
@@ -547,7 +685,7 @@ __global__ void __launch_bounds__(256, 2) schwarz_kernel(const PrimPairDev *pp, 
     double qmax = 0.0;
     for (int a0 = 0; a0 < AB.nfp; a0 += pl.ach) {
         const int a1 = min(AB.nfp, a0 + pl.ach);
-        block_chunk<false>(pp, E, boys, AB, AB, a0, a1, a0, a1, pl, b);
+        block_chunk<false, false>(pp, E, nullptr, boys, AB, AB, a0, a1, a0, a1, pl, b);
         const int ach = a1 - a0;
         if (threadIdx.x == 0)
             for (int a = 0; a < ach; ++a) qmax = fmax(qmax, sqrt(fabs(b.G[(size_t)a * ach + a])));

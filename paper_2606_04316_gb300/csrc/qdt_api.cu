@@ -71,7 +71,7 @@ T *dcopy(DBuf &b, const std::vector<T> &v, cudaStream_t s) {
 }
 
 struct ClassBufs {
-    DBuf pairs, pp, E, Q, bra, pp_pair;
+    DBuf pairs, pp, E, E2, Q, bra, pp_pair;
 };
 
 // Instantiated graph of a batch round and the signature it was captured for.
@@ -108,7 +108,7 @@ struct qdt_ctx {
     cudaEvent_t ev[16];
     int launches = 0;
     // batches owned by this context (its stream carries the fused launches)
-    DBuf bprms[2], btasks[2], bnext[2];
+    DBuf bprms[4], btasks[4], bnext[4];      // per kernel kind: gauge x compensated FP32
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     GraphEntry graph[2];
     long long graph_captures = 0, graph_replays = 0;
@@ -181,9 +181,10 @@ void build_tiles(const std::vector<int> &bras, const std::vector<int> &prefix, i
 // prints every timing to stderr, QDT_ERI_LAUNCH="threads,kets,order" pins the
 // shape for every class.
 struct TuneKey {
-    int dev, gauge, maxnfp, maxLab, maxnpp;
+    int dev, gauge, df, maxnfp, maxLab, maxnpp;
     bool operator<(const TuneKey &o) const {
-        return std::tie(dev, gauge, maxnfp, maxLab, maxnpp) < std::tie(o.dev, o.gauge, o.maxnfp, o.maxLab, o.maxnpp);
+        return std::tie(dev, gauge, df, maxnfp, maxLab, maxnpp) <
+               std::tie(o.dev, o.gauge, o.df, o.maxnfp, o.maxLab, o.maxnpp);
     }
 };
 std::mutex g_tune_mu;
@@ -195,7 +196,7 @@ bool env_flag(const char *name, bool dflt) {
     return e[0] != '0';
 }
 
-EriLaunch eri_launch_for(qdt_ctx *ctx, const PairClass &pc, const EriShape &shape, bool gauge,
+EriLaunch eri_launch_for(qdt_ctx *ctx, const PairClass &pc, const EriShape &shape, bool gauge, bool df,
                          const EriParams *d_prm, const std::vector<int> &bras, const std::vector<int> &prefix,
                          cudaStream_t s) {
     EriLaunch def;
@@ -210,7 +211,7 @@ EriLaunch eri_launch_for(qdt_ctx *ctx, const PairClass &pc, const EriShape &shap
     }
     if (!env_flag("QDT_AUTOTUNE", true)) return def;
     const bool verbose = env_flag("QDT_AUTOTUNE_VERBOSE", false);
-    const TuneKey key{ctx->device, gauge ? 1 : 0, shape.maxnfp, shape.maxLab, shape.maxnpp};
+    const TuneKey key{ctx->device, gauge ? 1 : 0, df ? 1 : 0, shape.maxnfp, shape.maxLab, shape.maxnpp};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -233,15 +234,15 @@ EriLaunch eri_launch_for(qdt_ctx *ctx, const PairClass &pc, const EriShape &shap
         build_tiles(tile_order(pc, sample, how.order), prefix, how.kets, 0, tk);
         EriTask *d_tk = dcopy(ctx->tasks, tk, s);
         QDT_CUDA_TRY(cudaEventRecord(e0, s));
-        launch_eri(d_prm, d_tk, (int)tk.size(), next, shape, gauge, how, s);
+        launch_eri(d_prm, d_tk, (int)tk.size(), next, shape, gauge, df, how, s);
         QDT_CUDA_TRY(cudaEventRecord(e1, s));
         QDT_CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.f;
         QDT_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
         if (verbose)
-            std::fprintf(stderr, "qdt autotune %s nfp %d L %d npp %d: threads %d kets %d order %d -> %.3f ms\n",
-                         gauge ? "gauge" : "coulomb", shape.maxnfp, shape.maxLab, shape.maxnpp, how.threads,
-                         how.kets, how.order, ms);
+            std::fprintf(stderr, "qdt autotune %s%s nfp %d L %d npp %d: threads %d kets %d order %d -> %.3f ms\n",
+                         gauge ? "gauge" : "coulomb", df ? " fp32-pairs" : "", shape.maxnfp, shape.maxLab,
+                         shape.maxnpp, how.threads, how.kets, how.order, ms);
         return ms;
     };
     EriLaunch best = def;
@@ -322,7 +323,9 @@ void build_class(qdt_ctx *ctx, int c) {
     launch_prim_pairs_map(ctx->shells.p ? (const ShellDev *)ctx->shells.p : nullptr, pc.d_pairs, d_ppp,
                           pc.npp_total, (const double *)ctx->exps.p, (const double *)ctx->coefs.p,
                           (const double *)ctx->norms.p, pc.d_pp, pc.d_E, s);
-    ctx->launches++;
+    pc.d_E2 = (float2 *)b.E2.get(std::max<long long>(1, eoff) * sizeof(float2));
+    launch_split_pairs(pc.d_E, eoff, pc.d_E2, s);
+    ctx->launches += 2;
     // Schwarz diagonals, then the bra order (Q descending, ties by id)
     pc.d_Q = (double *)b.Q.get(std::max(1, pc.nsp) * sizeof(double));
     launch_schwarz((const ShellDev *)ctx->shells.p, pc.d_pairs, pc.d_pp, pc.d_E,
@@ -526,6 +529,7 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
     prm.pairs = pc.d_pairs;
     prm.pp = pc.d_pp;
     prm.E = pc.d_E;
+    prm.E2 = P.precision == QDT_SPLIT ? pc.d_E2 : nullptr;
     prm.boys = (const double *)ctx->boys.p;
     prm.ket_sp = P.ketsp;
     prm.ket_col = P.ketcol;
@@ -705,14 +709,16 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
         batch_prepare(ctx, P, b0, B);
         const EriParams *d_prm = dcopy(ctx->prms, std::vector<EriParams>{B.prm}, s);
         const EriShape shape{pc.maxnfp, pc.maxLab, pc.maxnpp};
-        const EriLaunch how = eri_launch_for(ctx, pc, shape, B.prm.gauge != 0, d_prm, B.bras, P.h_prefix, s);
+        const bool df = B.prm.E2 != nullptr;
+        const EriLaunch how = eri_launch_for(ctx, pc, shape, B.prm.gauge != 0, df, d_prm, B.bras, P.h_prefix, s);
         std::vector<EriTask> tk;
         build_tiles(tile_order(pc, B.bras, how.order), P.h_prefix, how.kets, 0, tk);
         EriTask *d_tk = dcopy(ctx->tasks, tk, s);
         int te = tm.n; tm.mark();
         launch_zero(B.W, B.rows * P.mult * B.ldw, s);
         if (B.Wc) launch_zero(B.Wc, B.rows * B.ldwc, s);
-        launch_eri(d_prm, d_tk, (int)tk.size(), (int *)ctx->next.get(sizeof(int)), shape, B.prm.gauge != 0, how, s);
+        launch_eri(d_prm, d_tk, (int)tk.size(), (int *)ctx->next.get(sizeof(int)), shape, B.prm.gauge != 0, df, how,
+                   s);
         ctx->launches += 2 + (B.Wc ? 1 : 0);
         batch_stats(ctx, P, B, st);
         int th = tm.n; tm.mark();
@@ -778,10 +784,13 @@ template <class T> uint64_t fnv_v(uint64_t h, const std::vector<T> &v) {
     return v.empty() ? h : fnv(h, v.data(), v.size() * sizeof(T));
 }
 
-uint64_t round_signature(const std::vector<BatchReq *> &fz, const std::vector<EriTask> tiles[2],
-                         const EriLaunch how[2], const EriShape shape[2]) {
+constexpr int kKinds = 4;           // integral kernel kinds: (gauge kernel) x (compensated FP32)
+inline int kind_of(const EriParams &p) { return (p.gauge ? 2 : 0) + (p.E2 ? 1 : 0); }
+
+uint64_t round_signature(const std::vector<BatchReq *> &fz, const std::vector<EriTask> tiles[kKinds],
+                         const EriLaunch how[kKinds], const EriShape shape[kKinds]) {
     uint64_t h = 1469598103934665603ULL;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kKinds; ++k) {
         h = fnv_v(h, tiles[k]);
         h = fnv(h, &how[k], sizeof(EriLaunch));
         h = fnv(h, &shape[k], sizeof(EriShape));
@@ -813,9 +822,9 @@ uint64_t round_signature(const std::vector<BatchReq *> &fz, const std::vector<Er
 // queue), then every request's first half, second half and packing on its own
 // stream.  Allocates nothing, copies nothing from the host and never waits, so
 // it can be captured into a CUDA graph.
-void issue_round(qdt_ctx *owner, const std::vector<BatchReq *> &fz, const EriParams *const d_prms[2],
-                 const EriTask *const d_tiles[2], const int ntiles[2], const EriShape shape[2],
-                 const EriLaunch how[2]) {
+void issue_round(qdt_ctx *owner, const std::vector<BatchReq *> &fz, const EriParams *const d_prms[kKinds],
+                 const EriTask *const d_tiles[kKinds], const int ntiles[kKinds], const EriShape shape[kKinds],
+                 const EriLaunch how[kKinds]) {
     cudaStream_t s0 = owner->stream;
     for (BatchReq *r : fz) {
         split_clear_status(r->c->split, s0);
@@ -823,9 +832,10 @@ void issue_round(qdt_ctx *owner, const std::vector<BatchReq *> &fz, const EriPar
         if (r->B.Wc) launch_zero(r->B.Wc, r->B.rows * r->B.ldwc, s0);
         r->c->launches += 1 + (r->B.Wc ? 1 : 0);
     }
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < kKinds; ++k)
         if (ntiles[k] > 0) {
-            launch_eri(d_prms[k], d_tiles[k], ntiles[k], (int *)owner->bnext[k].p, shape[k], k == 1, how[k], s0);
+            launch_eri(d_prms[k], d_tiles[k], ntiles[k], (int *)owner->bnext[k].p, shape[k], (k & 2) != 0,
+                       (k & 1) != 0, how[k], s0);
             owner->launches++;
         }
     QDT_CUDA_TRY(cudaEventRecord(owner->fork_ev, s0));
@@ -895,40 +905,40 @@ void batch_round(qdt_ctx *owner, std::vector<BatchReq> &R, int round, unsigned f
         } catch (const Error &e) { item_fail(r, e); }
     }
     if (!fz.empty()) {
-        // shared tile queues: kernel kind 0 (Coulomb kernel) and 1 (gauge kernel);
-        // tiles of all requests, most expensive bra pairs first
-        std::vector<EriParams> prms[2];
+        // shared tile queues, one per kernel kind (Coulomb or gauge kernel, FP64 or
+        // compensated FP32 contraction); tiles of all requests of the kind
+        std::vector<EriParams> prms[kKinds];
         std::vector<int> req_of(fz.size());
-        EriShape shape[2];
+        EriShape shape[kKinds];
         for (size_t i = 0; i < fz.size(); ++i) {
             BatchReq *r = fz[i];
-            const int k = r->B.prm.gauge ? 1 : 0;
+            const int k = kind_of(r->B.prm);
             req_of[i] = (int)prms[k].size();
             prms[k].push_back(r->B.prm);
             const PairClass &pc = r->c->cls[r->P.cr.c];
             shape[k].merge(EriShape{pc.maxnfp, pc.maxLab, pc.maxnpp});
         }
-        const EriParams *d_prms[2] = {nullptr, nullptr};
-        const EriTask *d_tiles[2] = {nullptr, nullptr};
-        int ntiles[2] = {0, 0};
-        EriLaunch how[2];
-        std::vector<EriTask> tiles[2];
-        for (int k = 0; k < 2; ++k) {
+        const EriParams *d_prms[kKinds] = {};
+        const EriTask *d_tiles[kKinds] = {};
+        int ntiles[kKinds] = {};
+        EriLaunch how[kKinds];
+        std::vector<EriTask> tiles[kKinds];
+        for (int k = 0; k < kKinds; ++k) {
             if (prms[k].empty()) continue;
             d_prms[k] = dcopy(owner->bprms[k], prms[k], s0);
             owner->bnext[k].get(sizeof(int));
             // the tuner samples the first request of this kind
             size_t first = 0;
-            while ((fz[first]->B.prm.gauge ? 1 : 0) != k) ++first;
-            how[k] = eri_launch_for(owner, fz[first]->c->cls[fz[first]->P.cr.c], shape[k], k == 1, d_prms[k],
-                                    fz[first]->B.bras, fz[first]->P.h_prefix, s0);
+            while (kind_of(fz[first]->B.prm) != k) ++first;
+            how[k] = eri_launch_for(owner, fz[first]->c->cls[fz[first]->P.cr.c], shape[k], (k & 2) != 0,
+                                    (k & 1) != 0, d_prms[k], fz[first]->B.bras, fz[first]->P.h_prefix, s0);
             // tile order across requests: request by request in bra order, or
             // all bra pairs most expensive first
             struct Key { double cost; int i; int sp; };
             std::vector<Key> order;
             for (size_t i = 0; i < fz.size(); ++i) {
                 BatchReq *r = fz[i];
-                if ((r->B.prm.gauge ? 1 : 0) != k) continue;
+                if (kind_of(r->B.prm) != k) continue;
                 const PairClass &pc = r->c->cls[r->P.cr.c];
                 for (int sp : r->B.bras) order.push_back({bra_cost(pc.h_pairs[sp]), (int)i, sp});
             }
@@ -947,8 +957,12 @@ void batch_round(qdt_ctx *owner, std::vector<BatchReq> &R, int round, unsigned f
         GraphEntry &g = owner->graph[round];
         const bool graph = (flags & QDT_BATCH_GRAPH) != 0;
         uint64_t sig = graph ? round_signature(fz, tiles, how, shape) : 0;
-        const void *own[] = {owner->bprms[0].p, owner->bprms[1].p, owner->btasks[0].p, owner->btasks[1].p,
-                             owner->bnext[0].p, owner->bnext[1].p};
+        const void *own[3 * kKinds];
+        for (int k = 0; k < kKinds; ++k) {
+            own[3 * k] = owner->bprms[k].p;
+            own[3 * k + 1] = owner->btasks[k].p;
+            own[3 * k + 2] = owner->bnext[k].p;
+        }
         sig = fnv(sig, own, sizeof own);
         try {
             if (!graph) {
@@ -1055,10 +1069,11 @@ void qdt_destroy(qdt_ctx *c) {
                     &c->V, &c->Vg, &c->W, &c->Wc, &c->Dmax, &c->wsort, &c->ketsp, &c->ketcol,
                     &c->prefix, &c->ktile, &c->tasks, &c->O, &c->partial, &c->stage, &c->rsR, &c->rsS,
                     &c->kpos, &c->prms, &c->next, &c->ktile2, &c->bprms[0], &c->bprms[1],
-                    &c->btasks[0], &c->btasks[1], &c->bnext[0], &c->bnext[1]};
+                    &c->bprms[2], &c->bprms[3], &c->btasks[0], &c->btasks[1], &c->btasks[2],
+                    &c->btasks[3], &c->bnext[0], &c->bnext[1], &c->bnext[2], &c->bnext[3]};
     for (DBuf *b : bufs) b->release();
     for (int k = 0; k < 2; ++k) {
-        c->cb[k].pairs.release(); c->cb[k].pp.release(); c->cb[k].E.release();
+        c->cb[k].pairs.release(); c->cb[k].pp.release(); c->cb[k].E.release(); c->cb[k].E2.release();
         c->cb[k].Q.release(); c->cb[k].bra.release(); c->cb[k].pp_pair.release();
     }
     split_release(c->split);

@@ -87,6 +87,7 @@ struct PairDev {
 
 struct PrimPairDev {
     double p;
+    double inv_p;   // 1 / p
     double P[3];
     long long eoff; // offset of this primitive pair's E matrix [nherm(Lab)][nfp]
     int ia, ib;     // primitives of the two shells
@@ -106,6 +107,7 @@ struct PairClass {
     PairDev *d_pairs = nullptr;
     PrimPairDev *d_pp = nullptr;
     double *d_E = nullptr;
+    float2 *d_E2 = nullptr;     // E split into FP32 pairs (hi, lo) for the split form's integrals
     double *d_Q = nullptr;
     int *d_bra_order = nullptr;
     long long npp_total = 0, e_total = 0;
@@ -118,6 +120,7 @@ struct EriParams {
     const PairDev *pairs;
     const PrimPairDev *pp;
     const double *E;
+    const float2 *E2;           // E as FP32 pairs: non-null selects the compensated FP32 contraction
     const double *boys;         // [kBoysGrid][kBoysCols]
     const int *ket_sp;          // shell pair id at each sorted ket position
     const long long *ket_col;   // first column of each sorted ket position
@@ -165,8 +168,12 @@ void launch_shell_norms(const ShellDev *shells, int nL_shells, const double *exp
 // Persistent integral kernel over a shared tile queue: `next` (device int,
 // zeroed by this call) hands out the tiles in array order.  prms: device array
 // of the parameter sets the tiles' `req` index.
+// df: every parameter set carries E2 and the contractions run in compensated
+// FP32 pairs (the split form); otherwise in FP64.
 void launch_eri(const EriParams *prms, const EriTask *tasks, int ntasks, int *next, const EriShape &shape,
-                bool gauge, const EriLaunch &how, cudaStream_t s);
+                bool gauge, bool df, const EriLaunch &how, cudaStream_t s);
+// E2[i] = (hi, lo) with hi = fl32(E[i]), lo = fl32(E[i] - hi).
+void launch_split_pairs(const double *E, long long n, float2 *E2, cudaStream_t s);
 int eri_default_threads(const EriShape &shape, bool gauge);
 void launch_schwarz(const ShellDev *shells, const PairDev *pairs, const PrimPairDev *pp,
                     const double *E, const double *boys, int npairs, int maxnfp, int maxLab,

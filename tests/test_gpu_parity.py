@@ -209,3 +209,23 @@ def test_split_first_half_in_row_chunks(oracle, torch_cuda, monkeypatch):
     tr = oracle.Transform(p)
     for i, b in enumerate(p.blocks):
         assert np.abs(chunked[i] - tr.packed(b).reshape(-1)).max() <= 1e-10
+
+
+def test_integral_launch_shapes_change_no_bit(torch_cuda, monkeypatch):
+    """The autotuner's candidates (CTA threads, ket positions per tile, tile
+    order) change how the integral work is cut and scheduled, never the
+    arithmetic of an integral: every pinned shape gives the same bits, for the
+    Coulomb and the gauge kernel and both forms."""
+    torch = torch_cuda
+    p = synth.chain_problem(6, 3, seed=321, shells=(0, 1), nprim=2, blocks=("coulomb", "gaunt", "gauge"),
+                            tau=1e-12)
+    for prec in (0, 1):
+        ref = None
+        for shape in ("128,8,0", "256,4,1", "128,16,1", "256,8,0"):
+            monkeypatch.setenv("QDT_ERI_LAUNCH", shape)
+            _, got, _ = run_gpu(torch, p, list(p.blocks), 0, p.nK, p.tau, precision=prec)
+            if ref is None:
+                ref = got
+            else:
+                assert np.array_equal(got, ref), shape
+        monkeypatch.delenv("QDT_ERI_LAUNCH")
