@@ -50,6 +50,9 @@ def workload(name):
         return synth.tiny_dc()
     if name == "cluster64-sp":
         return synth.dcb_cluster()
+    if name.startswith("cluster") and "x" in name:       # clusterAxBxC-nK: the same recipe, smaller
+        dims, nk = name[7:].split("-")
+        return synth.dcb_cluster(dims=tuple(int(d) for d in dims.split("x")), nK=int(nk))
     if name.startswith("chain"):
         n = int(name[5:].split("-")[0])
         return synth.medium_dc(n_centers=n, nK=n)
