@@ -37,6 +37,23 @@ __device__ inline void atomic_max_nonneg(double *addr, double v) {
     atomicMax((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
 }
 
+// Maximum over a warp by shuffles, then over the block's warps (result in thread 0).
+__device__ inline double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ inline double block_max(double v) {
+    __shared__ double wm[32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    v = warp_max(v);
+    if (l == 0) wm[w] = v;
+    __syncthreads();
+    if (w == 0) v = warp_max(l < (int)(blockDim.x >> 5) ? wm[l] : 0.0);
+    return v;
+}
+
 // Coulomb: row (a,b) of a class-0 pair, columns (RS, part):
 //   A = D^{RS}_{ab} + D^{RS}_{ba},  B = D^{R'S}_{ab} + D^{R'S}_{ba}  (a != b; a == b: single term)
 //   D^{xy}_{ab} = sum_tau conj(C[a,tau,x]) C[b,tau,y];  for the partner R':
@@ -75,14 +92,8 @@ __global__ void density_coulomb_kernel(const PairDev *pairs, const int *bra_orde
         vmax = fmax(vmax, fmax(fmax(fabs(Av.re), fabs(Av.im)), fmax(fabs(Bv.re), fabs(Bv.im))));
     }
     // block max -> Dmax[sp]
-    __shared__ double red[256];
-    red[threadIdx.x] = vmax;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) atomic_max_nonneg(Dmax + sp, red[0]);
+    vmax = block_max(vmax);
+    if (threadIdx.x == 0) atomic_max_nonneg(Dmax + sp, vmax);
 }
 
 // sigma_J between the spin components: c = (conj(C[u,alpha,x]), conj(C[u,beta,x])),
@@ -126,14 +137,8 @@ __global__ void density_gaunt_kernel(const PairDev *pairs, const int *bra_order,
             vmax = fmax(vmax, fmax(fmax(fabs(Av.re), fabs(Av.im)), fmax(fabs(Bv.re), fabs(Bv.im))));
         }
     }
-    __shared__ double red[256];
-    red[threadIdx.x] = vmax;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) atomic_max_nonneg(Dmax + sp, red[0]);
+    vmax = block_max(vmax);
+    if (threadIdx.x == 0) atomic_max_nonneg(Dmax + sp, vmax);
 }
 
 void launch_density(bool gaunt, const PairDev *pairs, const int *bra_order, int nsp,
@@ -176,25 +181,39 @@ __global__ void ket_rank_kernel(const double *Q, const double *Dmax, int n, doub
     }
 }
 
-// exclusive prefix sums of nfp over the sorted ket order (single CTA)
+// exclusive prefix sums of nfp over the sorted ket order (single CTA): warp
+// scans by shuffles, then a scan of the warp totals by the first warp
 __global__ void ket_col_kernel(const PairDev *pairs, const int *ket_sp, int n, long long *col) {
-    __shared__ long long part[1024];
-    long long carry = 0;
-    for (int base = 0; base < n; base += 1024) {
-        int i = base + threadIdx.x;
-        long long v = (i < n) ? pairs[ket_sp[i]].nfp : 0;
-        part[threadIdx.x] = v;
-        __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            long long t = (threadIdx.x >= off) ? part[threadIdx.x - off] : 0;
-            __syncthreads();
-            part[threadIdx.x] += t;
-            __syncthreads();
+    __shared__ long long wsum[32];
+    __shared__ long long carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const long long v = (i < n) ? pairs[ket_sp[i]].nfp : 0;
+        long long x = v;                                   // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        if (i < n) col[i] = carry + part[threadIdx.x] - v;
-        long long tot = part[1023];
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
-        carry += tot;
+        if (w == 0) {                                      // inclusive scan of the warp totals
+            long long t = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            if (lane < nw) wsum[lane] = t;
+        }
+        __syncthreads();
+        if (i < n) col[i] = carry + (w > 0 ? wsum[w - 1] : 0) + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wsum[nw - 1];
+        __syncthreads();
     }
     if (threadIdx.x == 0) col[n] = carry;
 }

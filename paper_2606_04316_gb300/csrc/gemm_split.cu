@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "split.cuh"
@@ -39,6 +40,7 @@ constexpr int kBits = 7;
 constexpr int kFrac = kSlices * kBits;       // 42 fractional bits
 constexpr int SBM = 128, SBN = 64, SBK = 64;
 constexpr int kChunkSub = 4;                  // 4 x 64 = 256 K per exact chunk
+constexpr size_t kPlaneBudget = (size_t)16 << 30;   // digit planes of one second-half K chunk
 constexpr int kATile = SBM * SBK * 2;         // 16 KB: one A digit plane of a K subtile
 constexpr int kBTile = SBN * SBK * 2;         // 8 KB: one B digit plane
 constexpr int kBPanel = kSlices * kBTile;     // 48 KB: the six B planes of a K subtile
@@ -139,17 +141,24 @@ __device__ inline void digits7(double x, int e, __nv_bfloat16 *d, size_t plane) 
 __global__ void slice_rows_kernel(const double *X, long long ld, long long M, long long K,
                                   long long Mpad, long long Kpad, __nv_bfloat16 *out, int *rowexp) {
     long long r = blockIdx.x;
-    __shared__ double red[256];
+    __shared__ double wm[32];
+    __shared__ int e_sh;
     double m = 0.0;
     if (r < M)
         for (long long k = threadIdx.x; k < K; k += blockDim.x) m = fmax(m, fabs(X[r * ld + k]));
-    red[threadIdx.x] = m;
+    // row maximum: warp shuffles, then the warps' maxima in the first warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? wm[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) e_sh = exp_of_max(m);
     }
-    int e = exp_of_max(red[0]);
+    __syncthreads();
+    const int e = e_sh;
     if (threadIdx.x == 0) rowexp[r] = e;
     size_t plane = (size_t)Mpad * Kpad;
     for (long long k = threadIdx.x; k < Kpad; k += blockDim.x) {
@@ -292,10 +301,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     ozaki_umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       long long Mpad, long long Npad, const long long *__restrict__ ktile,
                       const int *__restrict__ rowexp, const int *__restrict__ colexp, double *C, long long ldc,
-                      long long Mvalid, long long Nvalid, int upper_only, int *status) {
+                      long long Mvalid, long long Nvalid, int flags, int *status) {
     extern __shared__ uint8_t smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long m0 = (long long)blockIdx.y * SBM, n0 = (long long)blockIdx.x * SBN;
+    const bool upper_only = (flags & 1) != 0, accumulate = (flags & 2) != 0;   // C += instead of C =
     if (upper_only && (m0 / 4) > (n0 + SBN - 1) / 4) return;   // below the block diagonal: unused
     if (*(volatile int *)status) return;                       // an earlier CTA gave up: skip the work
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -445,14 +455,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const float w = fmaf(v5[t], 0x1p-14f, fmaf(v4[t], 0x1p-7f, v3[t]));
                             const double v = fma((double)w, 0x1p-7, (double)acc[q * 16 + t]);
                             const int k = er + colexp[n] - 28;
-                            C[m * ldc + n] = (k > -1022 && k < 1023)
+                            const double r = (k > -1022 && k < 1023)
                                                  ? v * __longlong_as_double((long long)(k + 1023) << 52)
                                                  : ldexp(v, k);
+                            C[m * ldc + n] = accumulate ? C[m * ldc + n] + r : r;
                         }
                     }
                 }
             }
-        } else if (m < Mvalid) {
+        } else if (m < Mvalid && !accumulate) {
             for (int t = 0; t < SBN; ++t)
                 if (n0 + t < Nvalid) C[m * ldc + n0 + t] = 0.0;
         }
@@ -523,7 +534,7 @@ static void slice_cols(SplitWorkspace &w, int slot, const double *X, long long l
 
 static void run_umma(SplitWorkspace &w, void *Asl, long long Mpad, long long KpadA, void *Bsl, long long Npad,
                      long long KpadB, const long long *d_kt128, const int *rowexp, const int *colexp, double *C,
-                     long long ldc, long long M, long long N, int upper, cudaStream_t s) {
+                     long long ldc, long long M, long long N, int flags, cudaStream_t s) {
     CUtensorMap ta = make_map(Asl, kSlices * Mpad, KpadA, SBM);
     CUtensorMap tb = make_map(Bsl, kSlices * Npad, KpadB, SBN);
     int *status = (int *)ws_get(w, WS_STAT, 256);
@@ -531,7 +542,7 @@ static void run_umma(SplitWorkspace &w, void *Asl, long long Mpad, long long Kpa
     QDT_CUDA_TRY(cudaFuncSetAttribute(ozaki_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     dim3 grid((unsigned)(Npad / SBN), (unsigned)(Mpad / SBM));
     ozaki_umma_kernel<<<grid, kThreads, kSmemBytes, s>>>(ta, tb, Mpad, Npad, d_kt128, rowexp, colexp, C, ldc, M, N,
-                                                    upper, status);
+                                                    flags, status);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) {
         cudaFuncAttributes fa{};
@@ -635,17 +646,30 @@ void gemm_half2(SplitWorkspace &w, int precision, const double *A, long long lda
         return;
     }
     if (N <= 0) return;
-    const long long Mpad = rup(N, SBM), Npad = rup(N, SBN), Kpad = std::max<long long>(SBK, rup(K, SBK));
+    const long long Mpad = rup(N, SBM), Npad = rup(N, SBN);
+    // K in chunks whose digit planes (12 bytes per element of A and B) stay within
+    // kPlaneBudget; the chunks' products are summed in FP64 into C
+    long long kc_max = std::max<long long>(SBK, (long long)(kPlaneBudget / (12 * (size_t)(Mpad + Npad))) / SBK * SBK);
+    if (const char *e = std::getenv("QDT_SPLIT_KCHUNK")) {          // smaller chunks, to exercise this path
+        const long long v = std::atoll(e);
+        if (v <= 0 || v % SBK) throw Error{QDT_ERR_ARG, "QDT_SPLIT_KCHUNK must be a positive multiple of 64"};
+        kc_max = v;
+    }
     int *exps = (int *)ws_get(w, WS_EXP, (size_t)(Mpad + Npad + 64) * sizeof(int) * 2);
     int *aexp = exps, *bexp = exps + Mpad + 32;
-    slice_cols(w, WS_A2, A, lda, K, N, Kpad, Mpad, aexp, s);
-    slice_cols(w, WS_B2, B, ldb, K, N, Kpad, Npad, bexp, s);
     const long long nkt = Mpad / SBM;
-    long long *d_kt = (long long *)ws_get(w, WS_KT, std::max<size_t>(256, (size_t)nkt * sizeof(long long)));
-    tile_extent_kernel<<<(unsigned)((nkt + 127) / 128), 128, 0, s>>>(nullptr, 0, 1, d_kt, nkt, K);
-    QDT_CHECK_KERNEL("tile_extent_kernel");
-    // the split kernel overwrites C; C = A^T B is the whole second half here
-    run_umma(w, w.buf[WS_A2], Mpad, Kpad, w.buf[WS_B2], Npad, Kpad, d_kt, aexp, bexp, C, N, N, N, 1, s);
+    for (long long k0 = 0; k0 < std::max<long long>(K, 1); k0 += kc_max) {
+        const long long kc = std::min(kc_max, K - k0), Kpad = std::max<long long>(SBK, rup(kc, SBK));
+        slice_cols(w, WS_A2, A + k0 * lda, lda, kc, N, Kpad, Mpad, aexp, s);
+        slice_cols(w, WS_B2, B + k0 * ldb, ldb, kc, N, Kpad, Npad, bexp, s);
+        long long *d_kt = (long long *)ws_get(w, WS_KT, std::max<size_t>(256, (size_t)nkt * sizeof(long long)));
+        tile_extent_kernel<<<(unsigned)((nkt + 127) / 128), 128, 0, s>>>(nullptr, 0, 1, d_kt, nkt, kc);
+        QDT_CHECK_KERNEL("tile_extent_kernel");
+        // upper block tiles; the first chunk writes C, later ones add to it
+        run_umma(w, w.buf[WS_A2], Mpad, Kpad, w.buf[WS_B2], Npad, Kpad, d_kt, aexp, bexp, C, N, N, N,
+                 1 | (k0 > 0 ? 2 : 0), s);
+        if (K <= 0) break;
+    }
 }
 
 }  // namespace qdt

@@ -615,19 +615,36 @@ long long split_chunk_rows(long long ldw) {
     return r;
 }
 
-// V rows = W D_ket over `rows` W rows from row 0, in row chunks for the split
-// form (launches only).
+// V rows = W D_ket over `rows` W rows from row 0 (launches only).  Split form:
+// row chunks (digit planes of W within kSliceBudget) and, when the density's
+// digit planes (12 bytes x longest K x N) exceed kSliceBudget too, column
+// chunks outside them, so each column chunk of the density is sliced once.
 void half1_rows(qdt_ctx *ctx, int precision, const double *W, long long ldw, const double *B, long long ldb,
                 double *C, long long ldc, long long rows, long long N, const long long *d_kt,
                 const std::vector<long long> &kt, cudaStream_t s) {
     const int TMr = gemm_fp64_tile_m();
-    const long long chunk = precision == QDT_SPLIT ? split_chunk_rows(ldw) : std::max<long long>(rows, 1);
-    for (long long r0 = 0; r0 < rows; r0 += chunk) {
-        const long long m = std::min(chunk, rows - r0);
-        const size_t t0 = (size_t)(r0 / TMr), t1 = std::min(kt.size(), (size_t)((r0 + m + TMr - 1) / TMr));
-        const std::vector<long long> sub(kt.begin() + t0, kt.begin() + t1);
-        gemm_half1(ctx->split, precision, W + r0 * ldw, ldw, B, ldb, C + r0 * ldc, ldc, m, N, d_kt + t0, sub, s);
-        ctx->launches++;
+    const bool split = precision == QDT_SPLIT;
+    const long long chunk = split ? split_chunk_rows(ldw) : std::max<long long>(rows, 1);
+    long long kmax = 1;
+    for (long long k : kt) kmax = std::max(kmax, k);
+    long long ncols = N;
+    if (split && 12.0 * (double)kmax * (double)N > (double)kSliceBudget)
+        ncols = std::max<long long>(64, (long long)(kSliceBudget / (12 * (size_t)kmax)) / 64 * 64);
+    if (const char *e = std::getenv("QDT_SPLIT_CHUNK_COLS")) {       // smaller chunks, to exercise this path
+        const long long v = std::atoll(e);
+        if (v <= 0 || v % 64) throw Error{QDT_ERR_ARG, "QDT_SPLIT_CHUNK_COLS must be a positive multiple of 64"};
+        if (split) ncols = v;
+    }
+    for (long long n0 = 0; n0 < N; n0 += ncols) {
+        const long long nw = std::min(ncols, N - n0);
+        for (long long r0 = 0; r0 < rows; r0 += chunk) {
+            const long long m = std::min(chunk, rows - r0);
+            const size_t t0 = (size_t)(r0 / TMr), t1 = std::min(kt.size(), (size_t)((r0 + m + TMr - 1) / TMr));
+            const std::vector<long long> sub(kt.begin() + t0, kt.begin() + t1);
+            gemm_half1(ctx->split, precision, W + r0 * ldw, ldw, B + n0, ldb, C + r0 * ldc + n0, ldc, m, nw,
+                       d_kt + t0, sub, s);
+            ctx->launches++;
+        }
     }
 }
 

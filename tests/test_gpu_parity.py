@@ -195,20 +195,35 @@ def test_argument_errors(torch_cuda):
 
 
 def test_split_first_half_in_row_chunks(oracle, torch_cuda, monkeypatch):
-    """The split form's first half runs in row chunks when the digit planes of
-    all integral rows would exceed their budget; chunks of 128 rows must give
-    the same result as one call (same digits, same products)."""
+    """The split form bounds its digit planes: the first half runs in row chunks
+    of the integral rows and column chunks of the density, the second half in
+    K chunks summed in FP64.  Row and column chunks must give the same bits as
+    one call (same digits, same products); K chunks agree within the split
+    form's bound."""
     torch = torch_cuda
     p = synth.chain_problem(6, 4, seed=311, shells=(0, 1), nprim=2, blocks=("coulomb", "gaunt", "gauge"),
                             tau=1e-12)
     _, whole, _ = run_gpu(torch, p, list(p.blocks), 0, p.nK, p.tau, precision=1)
     monkeypatch.setenv("QDT_SPLIT_CHUNK_ROWS", "128")
     _, chunked, st = run_gpu(torch, p, list(p.blocks), 0, p.nK, p.tau, precision=1)
+    # column chunks of the density as well: the same tiles, the same products
+    monkeypatch.setenv("QDT_SPLIT_CHUNK_COLS", "64")
+    _, cols, _ = run_gpu(torch, p, list(p.blocks), 0, p.nK, p.tau, precision=1)
     monkeypatch.delenv("QDT_SPLIT_CHUNK_ROWS")
+    monkeypatch.delenv("QDT_SPLIT_CHUNK_COLS")
+    # second half in K chunks summed in FP64: a different summation order
+    monkeypatch.setenv("QDT_SPLIT_KCHUNK", "128")
+    _, kchunks, _ = run_gpu(torch, p, list(p.blocks), 0, p.nK, p.tau, precision=1)
+    monkeypatch.delenv("QDT_SPLIT_KCHUNK")
     assert np.array_equal(chunked, whole)
+    assert np.array_equal(cols, whole)
+    # each K chunk has its own power-of-two scales: a second split evaluation, so
+    # the two agree within the split form's bound, not bitwise
+    assert np.abs(kchunks - whole).max() <= 1e-10
     tr = oracle.Transform(p)
     for i, b in enumerate(p.blocks):
         assert np.abs(chunked[i] - tr.packed(b).reshape(-1)).max() <= 1e-10
+        assert np.abs(kchunks[i] - tr.packed(b).reshape(-1)).max() <= 1e-10
 
 
 def test_integral_launch_shapes_change_no_bit(torch_cuda, monkeypatch):
