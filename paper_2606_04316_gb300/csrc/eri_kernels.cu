@@ -327,6 +327,38 @@ __device__ __forceinline__ void ket_orders_df(int n0, int Ly, int tx, int ux, in
     }
 }
 
+// The same for two adjacent inner function pairs y, y + 1 at once (the second
+// when has1): R and the primitive-pair offsets are loaded once for both, and
+// the two accumulator chains are independent (gauge kernel, whose larger
+// plan leaves registers for the second chain).
+template <bool NEG>
+__device__ __forceinline__ void ket_orders_df2(int n0, int Ly, int tx, int ux, int vx, const int *trip,
+                                               const float2 *Rq, int nr, const float2 *ey, int nfpY,
+                                               const long long *eoff, int nk, bool has1, float &ah0, float &al0,
+                                               float &ah1, float &al1) {
+    for (int n = n0; n <= Ly; n += 2) {
+        const int hb = n ? nherm(n - 1) : 0, he = nherm(n);
+        for (int hp = hb; hp < he; ++hp) {
+            const int tq = trip[hp];
+            const int T0 = tx + (tq & 255), U0 = ux + ((tq >> 8) & 255), V0 = vx + (tq >> 16);
+            const int s = T0 + U0 + V0, w = U0 + V0;
+            const int i0 = s * (s + 1) * (s + 2) / 6 + w * (w + 1) / 2 + V0;
+            const float2 *e = ey + (size_t)hp * nfpY;
+            if (has1) {
+                for (int kl = 0; kl < nk; ++kl) {
+                    const float2 r = Rq[kl * nr + i0];
+                    const float2 *ek = e + eoff[kl];
+                    const float2 e0 = __ldg(ek), e1 = __ldg(ek + 1);
+                    df_madd<NEG>(r, e0, ah0, al0);
+                    df_madd<NEG>(r, e1, ah1, al1);
+                }
+            } else {
+                for (int kl = 0; kl < nk; ++kl) df_madd<NEG>(Rq[kl * nr + i0], __ldg(e + eoff[kl]), ah0, al0);
+            }
+        }
+    }
+}
+
 // One chunk (x in [x0,x1) of X, y in [y0,y1) of Y) of the block (X|Y);
 // results in b.G[comp][x][y].  NC = 1 (Coulomb) or 7 (gauge: [0] Coulomb,
 // [1..6] (xy|d_I d_J r|zw) for IJ = xx,xy,xz,yy,yz,zz).
@@ -425,6 +457,40 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
             }
             // T[ij][h][y] += sum_kl sum_h' (-1)^{|h'|} R[h+h'] E^{kl}[h'][y]: rows h < nhx
             // with the Coulomb tensor, then (gauge) rows g = 4.. with the r12 tensor
+            if constexpr (DF) {
+                // gauge kernel: pairs of adjacent y per thread when the chunk has enough
+                // of them to keep the lanes busy; single y otherwise (same sums either way)
+                const int yb = (GAUGE && ych >= 8) ? 2 : 1;
+                const int ych2 = (ych + yb - 1) / yb;
+                for (int it = tid; it < nij * nT * ych2; it += nt) {
+                    const int ijl = it / (nT * ych2);
+                    const int rem = it - ijl * nT * ych2;
+                    const int hh = rem / ych2, yy = yb * (rem - hh * ych2);
+                    const bool has1 = yb == 2 && yy + 1 < ych;
+                    const bool r12 = GAUGE && hh >= nhx;
+                    const int h = r12 ? hh - nhx + 4 : hh;
+                    const int tr = b.trip[h];
+                    const int tx = tr & 255, ux = (tr >> 8) & 255, vx = tr >> 16;
+                    float2 *T2 = reinterpret_cast<float2 *>(T + (size_t)ijl * tsz + (size_t)hh * ych + yy);
+                    float ah0 = T2[0].x, al0 = T2[0].y, ah1 = 0.f, al1 = 0.f;
+                    if (has1) { ah1 = T2[1].x; al1 = T2[1].y; }
+                    const float2 *R2 = reinterpret_cast<const float2 *>(r12 ? RR + (size_t)ijl * nk * nrR
+                                                                            : RC + (size_t)ijl * nk * nrC);
+                    const int nr = r12 ? nrR : nrC;
+                    const float2 *ey = E2 + (y0 + yy);
+                    if constexpr (GAUGE) {
+                        ket_orders_df2<false>(0, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, has1, ah0,
+                                              al0, ah1, al1);
+                        ket_orders_df2<true>(1, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, has1, ah0,
+                                             al0, ah1, al1);
+                    } else {
+                        ket_orders_df<false>(0, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, ah0, al0);
+                        ket_orders_df<true>(1, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, ah0, al0);
+                    }
+                    T2[0] = make_float2(ah0, al0);
+                    if (has1) T2[1] = make_float2(ah1, al1);
+                }
+            } else
             for (int it = tid; it < nij * nT * ych; it += nt) {
                 const int ijl = it / (nT * ych);
                 const int rem = it - ijl * nT * ych;
@@ -436,21 +502,11 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
                 double *Tq = T + (size_t)ijl * tsz + (size_t)hh * ych + yy;
                 const double *Rq = r12 ? RR + (size_t)ijl * nk * nrR : RC + (size_t)ijl * nk * nrC;
                 const int nr = r12 ? nrR : nrC;
-                if constexpr (DF) {
-                    float2 *T2 = reinterpret_cast<float2 *>(Tq);
-                    float ah = T2->x, al = T2->y;
-                    const float2 *R2 = reinterpret_cast<const float2 *>(Rq);
-                    const float2 *ey = E2 + (y0 + yy);
-                    ket_orders_df<false>(0, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, ah, al);
-                    ket_orders_df<true>(1, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, ah, al);
-                    *T2 = make_float2(ah, al);
-                } else {
-                    double acc = *Tq;
-                    const double *ey = E + (y0 + yy);
-                    ket_orders<false>(0, Ly, tx, ux, vx, b.trip, Rq, nr, ey, Y.nfp, b.eY + k0, nk, acc);
-                    ket_orders<true>(1, Ly, tx, ux, vx, b.trip, Rq, nr, ey, Y.nfp, b.eY + k0, nk, acc);
-                    *Tq = acc;
-                }
+                double acc = *Tq;
+                const double *ey = E + (y0 + yy);
+                ket_orders<false>(0, Ly, tx, ux, vx, b.trip, Rq, nr, ey, Y.nfp, b.eY + k0, nk, acc);
+                ket_orders<true>(1, Ly, tx, ux, vx, b.trip, Rq, nr, ey, Y.nfp, b.eY + k0, nk, acc);
+                *Tq = acc;
             }
             // the next group's header pass touches neither T nor R, and its
             // barrier orders this pass before the recursion overwrites R
