@@ -35,6 +35,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL = {"bf16": 2250.0, "fp64": 1.25}     # dense TF/s, for dtype ratios
 SMS = 152                 # streaming multiprocessors of a GB300
 DFMA_PER_CLK_SM = 2       # FP64 FMA lanes per clock per SM (ncu: dfma peak_sustained 2 inst/cycle/SM)
+FP32_PER_CLK_SM = 128     # FP32 lanes per clock per SM
+DF_OPS_PER_MADD = 12      # FP32 operations of one compensated FP32-pair multiply-add (split-form integrals)
 
 
 def fp64_alu_peak(clocks):
@@ -415,9 +417,16 @@ def main():
     fp64_note = "FP64 pipe: %d SMs x %d DFMA/clk x 2 flops x %.0f MHz sampled SM clock" % (SMS, DFMA_PER_CLK_SM, mhz)
     if dom == "ms_eri":
         achieved = st["flops_eri"] / (avg[dom] / 1e3) / 1e12
+        if prec == qdt.SPLIT:
+            # split form: the contractions run in compensated FP32 pairs on the FP32 pipe
+            peak = SMS * FP32_PER_CLK_SM * mhz * 1e6 / DF_OPS_PER_MADD * 2 / 1e12
+            note = ("FP32 pipe: %d SMs x %d lanes x %.0f MHz / %d FP32 ops per compensated multiply-add x 2 "
+                    "flops (FP64-equivalent)" % (SMS, FP32_PER_CLK_SM, mhz, DF_OPS_PER_MADD))
+        else:
+            peak, note = fp64_peak, fp64_note
         roof = {"kernel": "eri_rows_kernel", "bound": "alu", "achieved": achieved,
-                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "traffic": None, "peak_note": fp64_note,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_note": note,
                 "work": "E R E multiply-adds of the kept quartets (qdt_stats.flops_eri)"}
     else:
         fl = st["flops_half1"] if dom == "ms_half1" else st["flops_half2"]
