@@ -29,6 +29,11 @@ design notes):
     16 reals O[PQ,i][RS,j] = sum Dq[ab,PQ,i] G[ab,cd] Dq[cd,RS,j], with the 4
     real parts i of the symmetrised densities A = D^{PQ}, B = D^{P'Q}
     (P' = Kramers partner): (Re A, Im A, Re B, Im B).
+  * Kramers-unrestricted input (the paper's runs, Sec. 3): every spinor p has
+    its own coefficients C[a, tau, p], given per row as 4 reals (Re alpha,
+    Im alpha, Re beta, Im beta); the densities are those of spinor pairs p <= q
+    (D^{qp} = conj D^{pq} after symmetrisation), and the packed output holds 4
+    reals O[pq,i][rs,j] (i, j = Re, Im) per canonical pair of pairs pq <= rs.
 """
 from __future__ import annotations
 
@@ -286,6 +291,24 @@ def kramers_pairs(nKa):
     return [(P, Q) for P in range(nKa) for Q in range(P, nKa)]
 
 
+def spinor_coefficients_ku(C4, s_begin=0, s_end=None):
+    """Kramers-unrestricted coefficients [nrows, n, 4] (Re alpha, Im alpha,
+    Re beta, Im beta per spinor) -> complex two-spinor coefficients
+    [nrows, 2 (alpha, beta), s_end - s_begin]."""
+    if s_end is None:
+        s_end = C4.shape[1]
+    q = C4[:, s_begin:s_end, :]
+    C = np.zeros((q.shape[0], 2, q.shape[1]), dtype=np.complex128)
+    C[:, 0, :] = q[..., 0] + 1j * q[..., 1]
+    C[:, 1, :] = q[..., 2] + 1j * q[..., 3]
+    return C
+
+
+def spinor_pairs(n):
+    """Canonical spinor-pair list (p<=q), row-major."""
+    return [(p, q) for p in range(n) for q in range(p, n)]
+
+
 # ----------------------------------------------------------------- densities
 
 def quaternion_density_coulomb(ob, CL, CS):
@@ -326,6 +349,38 @@ def quaternion_density_gaunt(ob, CL, CS):
             d2 = np.einsum('ptk,tu,puk->pk', np.conj(CS[bS][:, :, rsp]), sg, CL[a][:, :, 2 * S])
             out[:, J, :, 2 * which] = (d1 + d2).real
             out[:, J, :, 2 * which + 1] = (d1 + d2).imag
+    return out.reshape(a.shape[0], 3, -1)
+
+
+def ku_density_coulomb(ob, CL, CS):
+    """Symmetrised spinor-pair density D[pair, pq*2 + part] over the class-0
+    pairs, parts (Re, Im) of D^{pq}_{ab} + D^{pq}_{ba} (a != b), p <= q (Eq. Den)."""
+    a, b, _ = ob.pairs(0)
+    C = np.concatenate([CL, CS], axis=0)
+    prs = spinor_pairs(C.shape[2])
+    P = np.array([p for p, _ in prs]); Q = np.array([q for _, q in prs])
+    Dab = np.einsum('ptk,ptk->pk', np.conj(C[a][:, :, P]), C[b][:, :, Q])
+    Dba = np.einsum('ptk,ptk->pk', np.conj(C[b][:, :, P]), C[a][:, :, Q])
+    sym = np.where((a == b)[:, None], Dab, Dab + Dba)
+    out = np.stack([sym.real, sym.imag], axis=-1)
+    return out.reshape(a.shape[0], -1)
+
+
+def ku_density_gaunt(ob, CL, CS):
+    """Folded L-S alpha-density of spinor pairs D[pair, J, pq*2 + part] over
+    the class-1 pairs (a in L, b in S), sigma_J between the spin components
+    (Eq. GauntInt)."""
+    a, b, _ = ob.pairs(1)
+    bS = b - ob.nL
+    prs = spinor_pairs(CL.shape[2])
+    P = np.array([p for p, _ in prs]); Q = np.array([q for _, q in prs])
+    out = np.zeros((a.shape[0], 3, len(prs), 2))
+    for J in range(3):
+        sg = SIGMA[J]
+        d1 = np.einsum('ptk,tu,puk->pk', np.conj(CL[a][:, :, P]), sg, CS[bS][:, :, Q])
+        d2 = np.einsum('ptk,tu,puk->pk', np.conj(CS[bS][:, :, P]), sg, CL[a][:, :, Q])
+        out[:, J, :, 0] = (d1 + d2).real
+        out[:, J, :, 1] = (d1 + d2).imag
     return out.reshape(a.shape[0], 3, -1)
 
 
@@ -514,6 +569,36 @@ class Transform:
         return out
 
 
+class TransformKU(Transform):
+    """The same transformation for Kramers-unrestricted input: problem.CL/CS
+    hold per-spinor coefficients [nrows, n, 4]; [s_begin, s_end) selects the
+    active spinors.  G, screening rule and the literal definition full() are
+    the Kramers-restricted ones; the densities are those of spinor pairs."""
+
+    def __init__(self, problem, s_begin=0, s_end=None, tau=None):
+        self.p = problem
+        self.ob = OracleBasis(problem.basis)
+        self.k_begin = s_begin
+        self.k_end = problem.CL.shape[1] if s_end is None else s_end
+        self.n = self.k_end - self.k_begin
+        self.tau = problem.tau if tau is None else tau
+        self.CL = spinor_coefficients_ku(problem.CL, self.k_begin, self.k_end)
+        self.CS = spinor_coefficients_ku(problem.CS, self.k_begin, self.k_end)
+        self._cache = {}
+
+    def density(self, block):
+        key = "D" + ("C" if block == "coulomb" else "G")
+        if key not in self._cache:
+            if block == "coulomb":
+                self._cache[key] = ku_density_coulomb(self.ob, self.CL, self.CS)
+            else:
+                self._cache[key] = ku_density_gaunt(self.ob, self.CL, self.CS)
+        return self._cache[key]
+
+    def packed(self, block, screened=True):
+        return pack_canonical_ku(self.packed_full(block, screened), self.n)
+
+
 # -------------------------------------------------------------- packing
 
 def pair_index(P, Q, n):
@@ -575,4 +660,36 @@ def unpack(packed, nKa, block):
                     t2 = -1.0 if c2 else 1.0
                     val = (o[re1, re2] - t1 * t2 * o[im1, im2]) + 1j * (t2 * o[re1, im2] + t1 * o[im1, re2])
                     out[p, q, r, s] = s1 * s2 * val
+    return out
+
+
+def pack_canonical_ku(Ofull, n):
+    """Symmetric O[(pq,i),(rs,j)] over spinor pairs -> packed [nP(nP+1)/2, 4]
+    over pq <= rs, nP = n(n+1)/2, entries (RR, RI, IR, II)."""
+    nP = n * (n + 1) // 2
+    O = Ofull.reshape(nP, 2, nP, 2)
+    iu, ju = np.triu_indices(nP)
+    return O[iu, :, ju, :].reshape(-1, 4).copy()
+
+
+def unpack_ku(packed, n):
+    """Packed Kramers-unrestricted array -> full complex (pq|rs) over n spinors:
+    D^{pq} = Dr + i c Di with the pair (min, max) and c = -1 when p > q."""
+    nP = n * (n + 1) // 2
+    O = np.zeros((nP, 2, nP, 2))
+    iu, ju = np.triu_indices(nP)
+    blk = packed.reshape(-1, 2, 2)
+    O[iu, :, ju, :] = blk
+    O[ju, :, iu, :] = blk.transpose(0, 2, 1)
+    out = np.zeros((n, n, n, n), dtype=np.complex128)
+    for p in range(n):
+        for q in range(n):
+            i1 = pair_index(min(p, q), max(p, q), n)
+            c1 = -1.0 if p > q else 1.0
+            for r in range(n):
+                for s_ in range(n):
+                    i2 = pair_index(min(r, s_), max(r, s_), n)
+                    c2 = -1.0 if r > s_ else 1.0
+                    o = O[i1, :, i2, :]
+                    out[p, q, r, s_] = (o[0, 0] - c1 * c2 * o[1, 1]) + 1j * (c2 * o[0, 1] + c1 * o[1, 0])
     return out

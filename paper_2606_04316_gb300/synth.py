@@ -59,6 +59,7 @@ class Problem:
     CS: np.ndarray             # [nS, nK, 4]
     blocks: tuple              # subset of ("coulomb", "gaunt", "gauge")
     tau: float                 # Schwarz threshold
+    kramers: bool = True       # False: CL/CS are per-spinor [nrows, n, 4] (Kramers-unrestricted)
 
     @property
     def nK(self) -> int:
@@ -126,6 +127,31 @@ def coefficients(rng, nL, nK):
     CL = np.ascontiguousarray(Q[:nL])
     CS = np.ascontiguousarray(Q[nL:] / (2.0 * C_LIGHT_GEN))
     return CL, CS
+
+
+def ku_coefficients(rng, nL, n):
+    """Kramers-unrestricted coefficients: n orthonormal complex two-spinor
+    columns over the nL large and 3 nL derivative rows (QR of a seeded complex
+    Gaussian matrix), the S rows scaled by 1/(2c); per row and spinor the 4
+    reals (Re alpha, Im alpha, Re beta, Im beta)."""
+    rows = 4 * nL
+    Z = rng.standard_normal((2 * rows, n)) + 1j * rng.standard_normal((2 * rows, n))
+    Qm, _ = np.linalg.qr(Z)
+    C = Qm.reshape(rows, 2, n)
+    C4 = np.stack([C[:, 0].real, C[:, 0].imag, C[:, 1].real, C[:, 1].imag], axis=-1)   # [rows, n, 4]
+    CL = np.ascontiguousarray(C4[:nL])
+    CS = np.ascontiguousarray(C4[nL:] / (2.0 * C_LIGHT_GEN))
+    return CL, CS
+
+
+def ku_chain_problem(n_centers, n_spinors, *, seed, shells=(0, 1), nprim=3, lo=0.1, hi=10.0,
+                     blocks=("coulomb",), tau=1e-12, name="ku-chain"):
+    """The chain recipe with Kramers-unrestricted coefficients."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xyz = chain_xyz(rng, n_centers)
+    basis = make_basis(rng, xyz, lambda i: shells, nprim, lo, hi)
+    CL, CS = ku_coefficients(rng, basis.nL, n_spinors)
+    return Problem(name, basis, CL, CS, tuple(blocks), float(tau), kramers=False)
 
 
 def chain_problem(n_centers, nK, *, seed, shells=(0, 1), nprim=3, lo=0.1, hi=10.0,

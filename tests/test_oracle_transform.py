@@ -14,39 +14,6 @@ def tiny(nK=2, seed=3, shells=(0, 0), ncent=2, nprim=1):
                                blocks=BLOCKS, tau=0.0, name="tiny")
 
 
-def full_eri4(O, tr, kernel):
-    """All-pairs 4-index tensor over F = L then S from the oracle's class
-    matrices (Coulomb: LL, SS and LS pairs; gauge: LS pairs only)."""
-    ob = tr.ob
-    nF = ob.nL + ob.nS
-    if kernel == 0:
-        T = np.zeros((nF,) * 4)
-        for cls in (0, 1):
-            a, b, _ = ob.pairs(cls)
-            for cls2 in (0, 1):
-                a2, b2, _ = ob.pairs(cls2)
-                G = np.zeros((len(a), len(a2)))
-                if cls == cls2:
-                    G = ob.pair_matrix(cls, 0)
-                else:
-                    G = ob.pair_rows(cls, 0, np.arange(len(a)))  # placeholder, replaced below
-                    G = None
-                if G is None:
-                    continue
-                for (x, y) in ((a, b), (b, a)):
-                    for (u, v) in ((a2, b2), (b2, a2)):
-                        T[x[:, None], y[:, None], u[None, :], v[None, :]] = G
-        return T
-    a, b, _ = ob.pairs(1)
-    G = ob.pair_matrix(1, 2)
-    T = np.zeros((6,) + (nF,) * 4)
-    for ij in range(6):
-        for (x, y) in ((a, b), (b, a)):
-            for (u, v) in ((a, b), (b, a)):
-                T[ij][x[:, None], y[:, None], u[None, :], v[None, :]] = G[ij]
-    return T
-
-
 def four_spinors(tr):
     """psi_p[f, c], c = (L alpha, L beta, S alpha, S beta)."""
     nL = tr.ob.nL
