@@ -125,6 +125,21 @@ def mo_integrals(nK, nblocks):
     return float((2 * nK) ** 4) * nblocks
 
 
+def mo_count(problem, nblocks):
+    """(pq|rs) over all spinors of the active range: 2 nK spinors for Kramers
+    pairs, nK spinors for Kramers-unrestricted input."""
+    n = problem.nK if not problem.kramers else 2 * problem.nK
+    return float(n) ** 4 * nblocks
+
+
+def as_unrestricted(problem):
+    """The same basis with seeded Kramers-unrestricted coefficients for as many
+    spinors (2 nK) as the Kramers-restricted workload has."""
+    rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 100))
+    CL, CS = synth.ku_coefficients(rng, problem.basis.nL, 2 * problem.nK)
+    return synth.Problem(problem.name + "-ku", problem.basis, CL, CS, problem.blocks, problem.tau, kramers=False)
+
+
 def run_reference(args, problem, blocks, rank):
     """CPU oracle on a bounded sample of the workload (rank 0 only)."""
     if rank != 0:
@@ -152,8 +167,10 @@ def cpu_oracle_rate(problem, blocks, budget_s=20.0):
     while True:
         p = synth.chain_problem(n, n, seed=synth.SEED_BASE + 1, shells=(0, 1), nprim=3,
                                 blocks=blocks, tau=problem.tau, name="sample")
+        if not problem.kramers:
+            p = as_unrestricted(p)
         t0 = time.perf_counter()
-        tr = O.Transform(p)
+        tr = O.Transform(p) if problem.kramers else O.TransformKU(p)
         for b in blocks:
             tr.packed(b)
         dt = time.perf_counter() - t0
@@ -163,18 +180,24 @@ def cpu_oracle_rate(problem, blocks, budget_s=20.0):
         n += 2
     n, dt = last
     rate = mo_integrals(n, len(blocks)) / dt
+    kind = "nK=%d" % n if problem.kramers else "%d unrestricted spinors" % (2 * n)
     return {"value": rate, "ms": dt * 1e3, "cores": cores,
-            "sample": "oracle, full transform of a %d-centre s+p chain (same recipe, nK=%d, blocks=%s) "
-                      "on %d host threads; %.1f s" % (n, n, "+".join(blocks), cores, dt)}
+            "sample": "oracle, full transform of a %d-centre s+p chain (same recipe, %s, blocks=%s) "
+                      "on %d host threads; %.1f s" % (n, kind, "+".join(blocks), cores, dt)}
 
 
 METRIC = "DCB AO->MO transform MO-integrals/s (split vs FP64 @1e-10 Eh)"
 
 
 def config_dict(args, problem, blocks):
-    return {"workload": args.workload, "nL": problem.basis.nL, "nS": problem.basis.nS,
-            "n_kramers": problem.nK, "blocks": "+".join(blocks), "schwarz_tau": problem.tau,
-            "precision": args.precision, "l2": "inputs larger than L2 (densities, integral rows)"}
+    d = {"workload": args.workload, "nL": problem.basis.nL, "nS": problem.basis.nS,
+         "n_kramers": problem.nK, "blocks": "+".join(blocks), "schwarz_tau": problem.tau,
+         "precision": args.precision, "l2": "inputs larger than L2 (densities, integral rows)"}
+    if not problem.kramers:
+        del d["n_kramers"]
+        d["n_spinors"] = problem.nK
+        d["input"] = "kramers-unrestricted"
+    return d
 
 
 def run_serving(args):
@@ -301,6 +324,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chain40-sp")
     ap.add_argument("--blocks", default="coulomb")
+    ap.add_argument("--input", default="kramers", choices=["kramers", "ku"],
+                    help="coefficients: quaternion (Kramers pairs) or Kramers-unrestricted spinors")
     ap.add_argument("--precision", default="split", choices=["split", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 form (0: skip)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -321,6 +346,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     problem = workload(args.workload)
+    if args.input == "ku":
+        problem = as_unrestricted(problem)
     if args.impl == "reference":
         return run_reference(args, problem, blocks, rank)
 
@@ -335,7 +362,8 @@ def main():
     ctx.set_basis(problem.basis)
     CLd = torch.from_numpy(problem.CL).cuda()
     CSd = torch.from_numpy(problem.CS).cuda()
-    ctx.set_coefficients(CLd, CSd)
+    set_coefs = ctx.set_coefficients if problem.kramers else ctx.set_spinor_coefficients
+    set_coefs(CLd, CSd)
     nK = problem.nK
     prec = qdt.SPLIT if args.precision == "split" else qdt.FP64
     nout = ctx.packed_size(blocks, 0, nK) // 8
@@ -370,7 +398,7 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    n_mo = mo_integrals(nK, len(blocks))
+    n_mo = mo_count(problem, len(blocks))
     value = n_mo * world / (ms / 1e3)
 
     # end to end through the public API with host buffers (pinned)
@@ -383,7 +411,7 @@ def main():
         ne = 1
         t0 = time.perf_counter()
         for _ in range(ne):
-            ctx.set_coefficients(CLh, CSh)
+            set_coefs(CLh, CSh)
             ctx.transform(blocks, 0, nK, tau, prec, outh)
         dt = (time.perf_counter() - t0) / ne
         e2e = {"value": n_mo * world / dt, "unit": "MO-integrals/s",
@@ -394,7 +422,7 @@ def main():
     other = None
     if prec == qdt.SPLIT and args.fp64_steps > 0:
         out64 = torch.zeros_like(out)
-        ctx.set_coefficients(CLd, CSd)
+        set_coefs(CLd, CSd)
         ctx.transform(blocks, 0, nK, tau, qdt.FP64, out64)
         ctx.transform(blocks, 0, nK, tau, prec, out)
         torch.cuda.synchronize()

@@ -136,7 +136,22 @@ int qdt_num_functions(const qdt_ctx *ctx);
  */
 int qdt_set_coefficients(qdt_ctx *ctx, int nK, const double *CL, const double *CS);
 
-/* Bytes of the packed output of qdt_transform for these blocks and range. */
+/*
+ * Kramers-unrestricted coefficients (the paper's own setting, Sec. 3): n
+ * spinors, each with its own two-spinor coefficients, no Kramers partner.
+ * CL: [nL][n][4], CS: [3 nL][n][4] doubles per row and spinor (Re alpha,
+ * Im alpha, Re beta, Im beta), row order as for qdt_set_coefficients; host or
+ * device, copied.  Replaces any coefficients set before.  qdt_transform then
+ * takes [k_begin, k_end) as a spinor range and writes, per block, 4 reals
+ * O[pq,i][rs,j] (i, j = Re, Im of the symmetrised spinor-pair densities
+ * D^{pq}, p <= q, Eq. Den) for every canonical pair of pairs pq <= rs,
+ * row-major over (pq, rs); D^{qp} = conj D^{pq} gives the rest (qdt_unpack).
+ * qdt_set_coefficients switches back to quaternion input.
+ */
+int qdt_set_spinor_coefficients(qdt_ctx *ctx, int n_spinors, const double *CL, const double *CS);
+
+/* Bytes of the packed output of qdt_transform for these blocks and range
+   (for the input kind last set: quaternion or Kramers-unrestricted). */
 size_t qdt_packed_size(const qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end);
 
 /*
@@ -153,8 +168,9 @@ int qdt_transform(qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end, double 
 /*
  * Expand one packed block (`block` = QDT_COULOMB, QDT_GAUNT or QDT_GAUGE) of n
  * Kramers pairs to the full complex array full[2n][2n][2n][2n] of
- * interleaved (re, im) doubles, on the context's GPU.  Both pointers are
- * device pointers.
+ * interleaved (re, im) doubles, on the context's GPU.  After
+ * qdt_set_spinor_coefficients n counts spinors and full is [n][n][n][n].
+ * Both pointers are device pointers.
  */
 int qdt_unpack(qdt_ctx *ctx, const double *packed, int n_kramers, unsigned block, double *full);
 

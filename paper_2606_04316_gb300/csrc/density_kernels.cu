@@ -58,6 +58,9 @@ __device__ inline double block_max(double v) {
 //   A = D^{RS}_{ab} + D^{RS}_{ba},  B = D^{R'S}_{ab} + D^{R'S}_{ba}  (a != b; a == b: single term)
 //   D^{xy}_{ab} = sum_tau conj(C[a,tau,x]) C[b,tau,y];  for the partner R':
 //   conj(C[a,alpha,R']) = -C[a,beta,R],  conj(C[a,beta,R']) = C[a,alpha,R].
+// KU (Kramers-unrestricted input): R, S are spinors with their own
+// coefficients; only A is formed, 2 parts (Re A, Im A) per spinor pair.
+template <bool KU>
 __global__ void density_coulomb_kernel(const PairDev *pairs, const int *bra_order,
                                        const ShellDev *shells, const double *Cq, int nK, int k0,
                                        const int *rsR, const int *rsS, int nRS, double *D,
@@ -65,7 +68,8 @@ __global__ void density_coulomb_kernel(const PairDev *pairs, const int *bra_orde
     const int sp = bra_order[blockIdx.x];
     const PairDev pr = pairs[sp];
     const ShellDev A = shells[pr.sa], B = shells[pr.sb];
-    const long long ld = 4LL * nRS;
+    constexpr int parts = KU ? 2 : 4;
+    const long long ld = (long long)parts * nRS;
     double vmax = 0.0;
     for (long long idx = threadIdx.x; idx < (long long)pr.nfp * nRS; idx += blockDim.x) {
         int fp = (int)(idx / nRS), rs = (int)(idx - (long long)fp * nRS);
@@ -78,18 +82,17 @@ __global__ void density_coulomb_kernel(const PairDev *pairs, const int *bra_orde
         spinor(Cq, nK, ia, S, aaS, abS);
         spinor(Cq, nK, ib, R, baR, bbR);
         spinor(Cq, nK, ib, S, baS, bbS);
-        cplx Dab = cadd(cmul(cconj(aaR), baS), cmul(cconj(abR), bbS));
-        cplx Bab = csub(cmul(aaR, bbS), cmul(abR, baS));
-        cplx Av = Dab, Bv = Bab;
-        if (ia != ib) {
-            cplx Dba = cadd(cmul(cconj(baR), aaS), cmul(cconj(bbR), abS));
-            cplx Bba = csub(cmul(baR, abS), cmul(bbR, aaS));
-            Av = cadd(Av, Dba);
-            Bv = cadd(Bv, Bba);
+        cplx Av = cadd(cmul(cconj(aaR), baS), cmul(cconj(abR), bbS));
+        if (ia != ib) Av = cadd(Av, cadd(cmul(cconj(baR), aaS), cmul(cconj(bbR), abS)));
+        double *o = D + (pr.rowoff + fp) * ld + (long long)parts * rs;
+        o[0] = Av.re; o[1] = Av.im;
+        vmax = fmax(vmax, fmax(fabs(Av.re), fabs(Av.im)));
+        if (!KU) {
+            cplx Bv = csub(cmul(aaR, bbS), cmul(abR, baS));
+            if (ia != ib) Bv = cadd(Bv, csub(cmul(baR, abS), cmul(bbR, aaS)));
+            o[2] = Bv.re; o[3] = Bv.im;
+            vmax = fmax(vmax, fmax(fabs(Bv.re), fabs(Bv.im)));
         }
-        double *o = D + (pr.rowoff + fp) * ld + 4LL * rs;
-        o[0] = Av.re; o[1] = Av.im; o[2] = Bv.re; o[3] = Bv.im;
-        vmax = fmax(vmax, fmax(fmax(fabs(Av.re), fabs(Av.im)), fmax(fabs(Bv.re), fabs(Bv.im))));
     }
     // block max -> Dmax[sp]
     vmax = block_max(vmax);
@@ -106,6 +109,7 @@ __device__ inline cplx sigma_form(int J, cplx c1, cplx c2, cplx d1, cplx d2) {
 
 // Gaunt / gauge: rows (a in L, b in S), columns (J, RS, part) of the folded
 // L-S alpha densities D^J_{ab} + D^J_{ba} (Eqs. GauntInt, gaugeInt).
+template <bool KU>
 __global__ void density_gaunt_kernel(const PairDev *pairs, const int *bra_order,
                                      const ShellDev *shells, const double *Cq, int nK, int k0,
                                      const int *rsR, const int *rsS, int nRS, double *D,
@@ -113,7 +117,8 @@ __global__ void density_gaunt_kernel(const PairDev *pairs, const int *bra_order,
     const int sp = bra_order[blockIdx.x];
     const PairDev pr = pairs[sp];
     const ShellDev A = shells[pr.sa], B = shells[pr.sb];
-    const long long ld = 12LL * nRS;
+    constexpr int parts = KU ? 2 : 4;
+    const long long ld = 3LL * parts * nRS;
     double vmax = 0.0;
     for (long long idx = threadIdx.x; idx < (long long)pr.nfp * nRS; idx += blockDim.x) {
         int fp = (int)(idx / nRS), rs = (int)(idx - (long long)fp * nRS);
@@ -129,26 +134,35 @@ __global__ void density_gaunt_kernel(const PairDev *pairs, const int *bra_order,
             // x = R: (conj alpha, conj beta); x = R': (-beta, alpha)
             cplx A1 = sigma_form(J, cconj(aaR), cconj(abR), baS, bbS);
             cplx A2 = sigma_form(J, cconj(baR), cconj(bbR), aaS, abS);
-            cplx B1 = sigma_form(J, cneg(abR), aaR, baS, bbS);
-            cplx B2 = sigma_form(J, cneg(bbR), baR, aaS, abS);
-            cplx Av = cadd(A1, A2), Bv = cadd(B1, B2);
-            double *o = D + (pr.rowoff + fp) * ld + (long long)J * 4 * nRS + 4LL * rs;
-            o[0] = Av.re; o[1] = Av.im; o[2] = Bv.re; o[3] = Bv.im;
-            vmax = fmax(vmax, fmax(fmax(fabs(Av.re), fabs(Av.im)), fmax(fabs(Bv.re), fabs(Bv.im))));
+            cplx Av = cadd(A1, A2);
+            double *o = D + (pr.rowoff + fp) * ld + (long long)J * parts * nRS + (long long)parts * rs;
+            o[0] = Av.re; o[1] = Av.im;
+            vmax = fmax(vmax, fmax(fabs(Av.re), fabs(Av.im)));
+            if (!KU) {
+                cplx B1 = sigma_form(J, cneg(abR), aaR, baS, bbS);
+                cplx B2 = sigma_form(J, cneg(bbR), baR, aaS, abS);
+                cplx Bv = cadd(B1, B2);
+                o[2] = Bv.re; o[3] = Bv.im;
+                vmax = fmax(vmax, fmax(fabs(Bv.re), fabs(Bv.im)));
+            }
         }
     }
     vmax = block_max(vmax);
     if (threadIdx.x == 0) atomic_max_nonneg(Dmax + sp, vmax);
 }
 
-void launch_density(bool gaunt, const PairDev *pairs, const int *bra_order, int nsp,
+void launch_density(bool gaunt, bool ku, const PairDev *pairs, const int *bra_order, int nsp,
                     const ShellDev *shells, const double *Cq, int nK, int k0, const int *rsR,
                     const int *rsS, int nRS, double *D, double *Dmax, cudaStream_t s) {
     if (nsp <= 0) return;
-    if (gaunt)
-        density_gaunt_kernel<<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
+    if (gaunt && ku)
+        density_gaunt_kernel<true><<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
+    else if (gaunt)
+        density_gaunt_kernel<false><<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
+    else if (ku)
+        density_coulomb_kernel<true><<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
     else
-        density_coulomb_kernel<<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
+        density_coulomb_kernel<false><<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
     QDT_CHECK_LAUNCH();
 }
 
@@ -302,25 +316,29 @@ void launch_zero(double *p, long long n, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- packing
-// out[t][16], t = pq nP - pq(pq-1)/2 + (rs - pq) for pq <= rs:
-// out[t][4i+j] = O[4 pq + i][4 rs + j]
+// out[t][parts^2], t = pq nP - pq(pq-1)/2 + (rs - pq) for pq <= rs:
+// out[t][parts i + j] = O[parts pq + i][parts rs + j]  (parts 4: Kramers pairs,
+// parts 2: spinor pairs of Kramers-unrestricted input)
+template <int PARTS>
 __global__ void pack_kernel(const double *O, long long ldo, int nP, double *out) {
     int pq = blockIdx.y;
     for (int rs = pq + blockIdx.x * blockDim.x + threadIdx.x; rs < nP; rs += gridDim.x * blockDim.x) {
         long long t = (long long)pq * nP - (long long)pq * (pq - 1) / 2 + (rs - pq);
-        double *o = out + t * 16;
-        for (int i = 0; i < 4; ++i) {
-            const double *src = O + (4LL * pq + i) * ldo + 4LL * rs;
-            for (int j = 0; j < 4; ++j) o[4 * i + j] = src[j];
+        double *o = out + t * PARTS * PARTS;
+#pragma unroll
+        for (int i = 0; i < PARTS; ++i) {
+            const double *src = O + ((long long)PARTS * pq + i) * ldo + (long long)PARTS * rs;
+#pragma unroll
+            for (int j = 0; j < PARTS; ++j) o[PARTS * i + j] = src[j];
         }
     }
 }
 
-void launch_pack(const double *O, long long ldo, int nKa, double *out, cudaStream_t s) {
-    int nP = nKa * (nKa + 1) / 2;
+void launch_pack(const double *O, long long ldo, int nP, int parts, double *out, cudaStream_t s) {
     if (nP <= 0) return;
     dim3 grid((nP + 255) / 256, nP);
-    pack_kernel<<<grid, 256, 0, s>>>(O, ldo, nP, out);
+    if (parts == 2) pack_kernel<2><<<grid, 256, 0, s>>>(O, ldo, nP, out);
+    else pack_kernel<4><<<grid, 256, 0, s>>>(O, ldo, nP, out);
     QDT_CHECK_LAUNCH();
 }
 
@@ -370,12 +388,33 @@ __global__ void unpack_kernel(const double *packed, int nKa, int alpha, double *
     }
 }
 
-void launch_unpack(const double *packed, int nKa, int gaunt_like, double *full, cudaStream_t s) {
-    long long n = 2LL * nKa, total = n * n * n * n;
+// Kramers-unrestricted input: D^{pq} = Dr + i c Di of the spinor pair
+// (min, max), c = -1 when p > q; (pq|rs) = (RR - c1 c2 II) + i (c2 RI + c1 IR).
+__global__ void unpack_ku_kernel(const double *packed, int n, double *full) {
+    const long long total = (long long)n * n * n * n;
+    const int nP = n * (n + 1) / 2;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+         id += (long long)gridDim.x * blockDim.x) {
+        int s = (int)(id % n), r = (int)((id / n) % n), q = (int)((id / n / n) % n), p = (int)(id / n / n / n);
+        const int a1 = min(p, q), b1 = max(p, q), a2 = min(r, s), b2 = max(r, s);
+        const int i1 = a1 * n - a1 * (a1 - 1) / 2 + (b1 - a1), i2 = a2 * n - a2 * (a2 - 1) / 2 + (b2 - a2);
+        const bool tr = i1 > i2;
+        const double *blk = tr ? packed + ((long long)i2 * nP - (long long)i2 * (i2 - 1) / 2 + (i1 - i2)) * 4
+                               : packed + ((long long)i1 * nP - (long long)i1 * (i1 - 1) / 2 + (i2 - i1)) * 4;
+        auto O = [&](int u, int v) { return tr ? blk[2 * v + u] : blk[2 * u + v]; };
+        const double c1 = p > q ? -1.0 : 1.0, c2 = r > s ? -1.0 : 1.0;
+        full[2 * id] = O(0, 0) - c1 * c2 * O(1, 1);
+        full[2 * id + 1] = c2 * O(0, 1) + c1 * O(1, 0);
+    }
+}
+
+void launch_unpack(const double *packed, int n_units, int gaunt_like, bool ku, double *full, cudaStream_t s) {
+    long long n = ku ? (long long)n_units : 2LL * n_units, total = n * n * n * n;
     if (total <= 0) return;
     long long blocks = (total + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    unpack_kernel<<<(unsigned)blocks, 256, 0, s>>>(packed, nKa, gaunt_like, full);
+    if (ku) unpack_ku_kernel<<<(unsigned)blocks, 256, 0, s>>>(packed, n_units, full);
+    else unpack_kernel<<<(unsigned)blocks, 256, 0, s>>>(packed, n_units, gaunt_like, full);
     QDT_CHECK_LAUNCH();
 }
 

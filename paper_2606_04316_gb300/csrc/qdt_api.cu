@@ -28,7 +28,7 @@ namespace qdt {
 void launch_prim_pairs_map(const ShellDev *shells, const PairDev *pairs, const int *pp_pair,
                            long long npp, const double *exps, const double *coefs,
                            const double *norms, PrimPairDev *pp, double *E, cudaStream_t s);
-void launch_density(bool gaunt, const PairDev *pairs, const int *bra_order, int nsp,
+void launch_density(bool gaunt, bool ku, const PairDev *pairs, const int *bra_order, int nsp,
                     const ShellDev *shells, const double *Cq, int nK, int k0, const int *rsR,
                     const int *rsS, int nRS, double *D, double *Dmax, cudaStream_t s);
 }  // namespace qdt
@@ -98,6 +98,7 @@ struct qdt_ctx {
     ClassBufs cb[2];
     // coefficients (internal rows: L functions, then the distinct derivative functions)
     bool has_coef = false;
+    bool ku = false;            // Kramers-unrestricted coefficients (per spinor) instead of quaternions
     int nK = 0;
     DBuf Cq, Craw, dsmap0, dsmap1;
     std::vector<int> smap0, smap1;
@@ -131,6 +132,14 @@ bool is_device_ptr(const void *p) {
 }
 
 int lcart(int l) { return (l + 1) * (l + 2) / 2; }
+
+// Doubles of one packed block over n active units (Kramers pairs: 16 per
+// canonical pair of Kramers pairs; spinors of unrestricted input: 4 per
+// canonical pair of spinor pairs).
+long long packed_block_elems(bool ku, long long n) {
+    const long long nP = n * (n + 1) / 2;
+    return nP * (nP + 1) / 2 * (ku ? 4 : 16);
+}
 
 // Rows of W per split-form first-half call: the digit planes of one call
 // (6 BF16 digits per element, 12 bytes) stay within kSliceBudget, so the
@@ -380,6 +389,7 @@ struct ClassPlan {
     int k0 = 0, nKa = 0, precision = 0, nRS = 0, mult = 1;
     double tau = 0;
     bool ls = false, one_batch = true;
+    bool ku = false;          // columns are spinor pairs with 2 parts (Kramers-unrestricted input)
     long long N4 = 0, ncolD = 0, M = 0, NV = 0;
     double *Dbra = nullptr, *Dmax = nullptr, *Dket = nullptr, *Vc = nullptr, *Vg = nullptr;
     int *prefix = nullptr, *ketsp = nullptr, *d_kpos = nullptr;
@@ -403,7 +413,8 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
     P.precision = precision;
     P.nRS = nKa * (nKa + 1) / 2;
     P.ls = cr.c == 1;
-    P.N4 = 4LL * P.nRS;                          // columns per J component
+    P.ku = ctx->ku;
+    P.N4 = (P.ku ? 2LL : 4LL) * P.nRS;          // columns per J component
     P.ncolD = P.ls ? 3 * P.N4 : P.N4;            // density row length
     P.NV = P.ls ? 3 * P.N4 : P.N4;               // V row length (Coulomb / Gaunt)
     P.M = pc.M;
@@ -419,7 +430,7 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
     P.Dbra = (double *)ctx->Dbra.get(std::max<long long>(1, P.M * P.ncolD) * sizeof(double));
     P.Dmax = (double *)ctx->Dmax.get(std::max(1, pc.nsp) * sizeof(double));
     QDT_CUDA_TRY(cudaMemsetAsync(P.Dmax, 0, pc.nsp * sizeof(double), s));
-    launch_density(P.ls, pc.d_pairs, pc.d_bra_order, pc.nsp, (const ShellDev *)ctx->shells.p,
+    launch_density(P.ls, P.ku, pc.d_pairs, pc.d_bra_order, pc.nsp, (const ShellDev *)ctx->shells.p,
                    (const double *)ctx->Cq.p, ctx->nK, k0, d_rsR, d_rsS, P.nRS, P.Dbra, P.Dmax, s);
     ctx->launches++;
     tm.mark();
@@ -681,7 +692,7 @@ struct Half2 {
 void half2_prepare(qdt_ctx *ctx, const ClassPlan &P, double *out_coul, double *out_gaunt, double *out_gauge,
                    Half2 &H) {
     H = Half2();
-    H.NO = 4LL * P.nRS;
+    H.NO = P.N4;
     H.O = (double *)ctx->O.get(std::max<long long>(1, H.NO * H.NO) * sizeof(double));
     H.pe = (size_t)std::max<long long>(1, H.NO * H.NO) * 8;
     if (H.pe * sizeof(double) > ((size_t)4 << 30))
@@ -700,7 +711,7 @@ void half2_job(qdt_ctx *ctx, const ClassPlan &P, const Half2 &H, const Half2::Jo
 }
 
 void half2_pack(qdt_ctx *ctx, const ClassPlan &P, const Half2 &H, const Half2::Job &j, cudaStream_t s) {
-    launch_pack(H.O, H.NO, P.nKa, j.out, s);
+    launch_pack(H.O, H.NO, P.nRS, P.ku ? 2 : 4, j.out, s);
     ctx->launches++;
 }
 
@@ -1192,12 +1203,16 @@ int qdt_set_basis(qdt_ctx *c, int n_centers, const double *xyz, int n_shells, co
 
 int qdt_num_functions(const qdt_ctx *c) { return (c && c->has_basis) ? c->nL : 0; }
 
-int qdt_set_coefficients(qdt_ctx *c, int nK, const double *CL, const double *CS) {
+}  // extern "C"
+
+namespace {
+int set_coefficients(qdt_ctx *c, int nK, const double *CL, const double *CS, bool ku, const char *who) {
     if (!c) return QDT_ERR_ARG;
     try {
         QDT_CUDA_TRY(cudaSetDevice(c->device));
-        if (!c->has_basis) throw Error{QDT_ERR_STATE, "qdt_set_coefficients: no basis"};
-        arg_check(nK > 0 && CL && CS, "qdt_set_coefficients: nK must be positive");
+        if (!c->has_basis) throw Error{QDT_ERR_STATE, std::string(who) + ": no basis"};
+        arg_check(nK > 0 && CL && CS, std::string(who) + ": the count must be positive and the arrays non-null");
+        c->has_coef = false;
         // CL as given; CS (3 nL rows) merged onto the internal derivative functions
         size_t nl = (size_t)c->nL * nK * 4, ns_in = (size_t)3 * c->nL * nK * 4, ns = (size_t)c->nS * nK * 4;
         double *d = (double *)c->Cq.get((nl + ns) * sizeof(double));
@@ -1207,6 +1222,7 @@ int qdt_set_coefficients(qdt_ctx *c, int nK, const double *CL, const double *CS)
         launch_merge_rows(raw, (const int *)c->dsmap0.p, (const int *)c->dsmap1.p, c->nS, nK * 4, d + nl, c->stream);
         QDT_CUDA_TRY(cudaStreamSynchronize(c->stream));
         c->nK = nK;
+        c->ku = ku;
         c->has_coef = true;
     } catch (const Error &e) {
         return fail(c, e);
@@ -1214,13 +1230,23 @@ int qdt_set_coefficients(qdt_ctx *c, int nK, const double *CL, const double *CS)
     c->err.clear();
     return QDT_OK;
 }
+}  // namespace
+
+extern "C" {
+
+int qdt_set_coefficients(qdt_ctx *c, int nK, const double *CL, const double *CS) {
+    return set_coefficients(c, nK, CL, CS, false, "qdt_set_coefficients");
+}
+
+int qdt_set_spinor_coefficients(qdt_ctx *c, int n_spinors, const double *CL, const double *CS) {
+    return set_coefficients(c, n_spinors, CL, CS, true, "qdt_set_spinor_coefficients");
+}
 
 size_t qdt_packed_size(const qdt_ctx *c, unsigned blocks, int k_begin, int k_end) {
-    (void)c;
     if (k_end <= k_begin) return 0;
-    long long n = k_end - k_begin, nP = n * (n + 1) / 2;
+    const bool ku = c && c->has_coef && c->ku;
     int nb = ((blocks & QDT_COULOMB) ? 1 : 0) + ((blocks & QDT_GAUNT) ? 1 : 0) + ((blocks & QDT_GAUGE) ? 1 : 0);
-    return (size_t)(nP * (nP + 1) / 2) * 16 * sizeof(double) * nb;
+    return (size_t)packed_block_elems(ku, k_end - k_begin) * sizeof(double) * nb;
 }
 
 int qdt_transform(qdt_ctx *c, unsigned blocks, int k_begin, int k_end, double tau, int precision,
@@ -1231,13 +1257,13 @@ int qdt_transform(qdt_ctx *c, unsigned blocks, int k_begin, int k_end, double ta
         QDT_CUDA_TRY(cudaSetDevice(c->device));
         if (!c->has_basis || !c->has_coef) throw Error{QDT_ERR_STATE, "qdt_transform: basis or coefficients not set"};
         arg_check(blocks != 0 && (blocks & ~7u) == 0, "qdt_transform: blocks must be a non-empty subset of COULOMB|GAUNT|GAUGE");
-        arg_check(k_begin >= 0 && k_end > k_begin && k_end <= c->nK, "qdt_transform: bad Kramers range");
+        arg_check(k_begin >= 0 && k_end > k_begin && k_end <= c->nK, "qdt_transform: bad Kramers-pair (or spinor) range");
         arg_check(tau >= 0.0, "qdt_transform: negative Schwarz threshold");
         arg_check(precision == QDT_FP64 || precision == QDT_SPLIT, "qdt_transform: bad precision");
         size_t need = qdt_packed_size(c, blocks, k_begin, k_end);
         arg_check(out != nullptr && out_bytes >= need, "qdt_transform: output buffer too small");
         const int nKa = k_end - k_begin;
-        const long long nP = (long long)nKa * (nKa + 1) / 2, per = nP * (nP + 1) / 2 * 16;
+        const long long per = packed_block_elems(c->ku, nKa);
         bool dev_out = is_device_ptr(out);
         double *dst = out;
         if (!dev_out) dst = (double *)c->stage.get(need);
@@ -1301,7 +1327,7 @@ int qdt_transform_batch(qdt_batch_item *items, int n, unsigned flags) {
             r.need = qdt_packed_size(r.c, it.blocks, it.k_begin, it.k_end);
             arg_check(it.out != nullptr && it.out_bytes >= r.need, "qdt_transform_batch: output buffer too small");
             r.nKa = it.k_end - it.k_begin;
-            const long long nP = (long long)r.nKa * (r.nKa + 1) / 2, per = nP * (nP + 1) / 2 * 16;
+            const long long per = packed_block_elems(r.c->ku, r.nKa);
             r.dev_out = is_device_ptr(it.out);
             r.dst = r.dev_out ? it.out : (double *)r.c->stage.get(r.need);
             double *cur = r.dst;
@@ -1370,7 +1396,7 @@ int qdt_unpack(qdt_ctx *c, const double *packed, int n_kramers, unsigned block, 
         arg_check(packed && full && n_kramers > 0, "qdt_unpack: bad arguments");
         arg_check(block == QDT_COULOMB || block == QDT_GAUNT || block == QDT_GAUGE, "qdt_unpack: one block");
         arg_check(is_device_ptr(packed) && is_device_ptr(full), "qdt_unpack: device pointers required");
-        launch_unpack(packed, n_kramers, block != QDT_COULOMB, full, c->stream);
+        launch_unpack(packed, n_kramers, block != QDT_COULOMB, c->ku, full, c->stream);
         QDT_CUDA_TRY(cudaStreamSynchronize(c->stream));
     } catch (const Error &e) {
         return fail(c, e);

@@ -199,8 +199,10 @@ void gemm_fp64_tn_sym(const double *A, long long lda, const double *B, long long
 int gemm_fp64_tile_m();
 
 // packing
-void launch_pack(const double *O, long long ldo, int nKa, double *out, cudaStream_t s);
-void launch_unpack(const double *packed, int nKa, int gaunt_like, double *full, cudaStream_t s);
+// parts: 4 (Kramers pairs) or 2 (spinor pairs, Kramers-unrestricted input); nP units
+void launch_pack(const double *O, long long ldo, int nP, int parts, double *out, cudaStream_t s);
+// n_units: Kramers pairs (ku false, 2 n spinors) or spinors (ku true)
+void launch_unpack(const double *packed, int n_units, int gaunt_like, bool ku, double *full, cudaStream_t s);
 void launch_zero(double *p, long long n, cudaStream_t s);
 // coefficient rows of the internal small-component basis: row r = in[m0[r]] (+ in[m1[r]])
 void launch_merge_rows(const double *in, const int *m0, const int *m1, int nrows, int rowlen, double *out,

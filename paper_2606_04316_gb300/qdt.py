@@ -22,7 +22,8 @@ ERRORS = {-1: "QDT_ERR_ARG", -2: "QDT_ERR_OOM", -3: "QDT_ERR_CUDA", -4: "QDT_ERR
 EXPORTS = ["qdt_create", "qdt_destroy", "qdt_set_basis", "qdt_num_functions", "qdt_set_coefficients",
            "qdt_packed_size", "qdt_transform", "qdt_unpack", "qdt_last_error", "qdt_version",
            "qdt_footprint", "qdt_server_create", "qdt_server_destroy", "qdt_submit", "qdt_poll", "qdt_wait",
-           "qdt_second_half_noalloc", "qdt_transform_batch", "qdt_graph_counts"]
+           "qdt_second_half_noalloc", "qdt_transform_batch", "qdt_graph_counts",
+           "qdt_set_spinor_coefficients"]
 BATCH_GRAPH = 1
 
 
@@ -91,6 +92,7 @@ def load(build_if_missing=True):
     L.qdt_set_basis.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, vp]
     L.qdt_num_functions.argtypes = [vp]
     L.qdt_set_coefficients.argtypes = [vp, ctypes.c_int, vp, vp]
+    L.qdt_set_spinor_coefficients.argtypes = [vp, ctypes.c_int, vp, vp]
     L.qdt_packed_size.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int]
     L.qdt_packed_size.restype = ctypes.c_size_t
     L.qdt_transform.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -181,6 +183,15 @@ class Context:
         nK = int(CL.shape[1])
         self._check(self.L.qdt_set_coefficients(self.h, nK, _ptr(CL), _ptr(CS)))
 
+    def set_spinor_coefficients(self, CL, CS):
+        """Kramers-unrestricted input: CL [nL, n, 4], CS [3 nL, n, 4] float64
+        (Re alpha, Im alpha, Re beta, Im beta per row and spinor)."""
+        if isinstance(CL, np.ndarray):
+            CL = np.ascontiguousarray(CL, np.float64)
+            CS = np.ascontiguousarray(CS, np.float64)
+        n = int(CL.shape[1])
+        self._check(self.L.qdt_set_spinor_coefficients(self.h, n, _ptr(CL), _ptr(CS)))
+
     def packed_size(self, blocks, k_begin, k_end):
         return int(self.L.qdt_packed_size(self.h, blocks_mask(blocks), int(k_begin), int(k_end)))
 
@@ -194,7 +205,8 @@ class Context:
         return st.as_dict()
 
     def unpack(self, packed, n_kramers, block, full):
-        """packed/full: torch cuda float64 tensors; full holds (2n)^4 complex values."""
+        """packed/full: torch cuda float64 tensors; full holds (2n)^4 complex values
+        (n^4 after set_spinor_coefficients, n counting spinors)."""
         self._check(self.L.qdt_unpack(self.h, _ptr(packed), int(n_kramers), blocks_mask([block]), _ptr(full)))
 
 
