@@ -286,6 +286,25 @@ def spinor_coefficients(Cq, k_begin=0, k_end=None):
     return C
 
 
+def rkb_to_derivative(CS4, c_light, spinors=False):
+    """Restricted kinetic balance (Eq. RKB): chi^S_mu = (1/2c) sigma.p chi^L_mu
+    with p = -i grad, so sum_mu chi^S_mu c^S_mu = sum_{mu,K} d_K chi_mu
+    Ct[(mu,K)] with Ct[(mu,K)] = (-i/2c) sigma_K c^S_mu.  Small-component
+    coefficients [nL, n, 4] -> derivative-basis coefficients [3 nL, n, 4]
+    (rows 3 mu + K).  spinors=False: quaternion columns (the Kramers partner
+    maps to the partner of the image, so the unbarred member carries it);
+    spinors=True: per-spinor (Re a, Im a, Re b, Im b)."""
+    if spinors:
+        C = np.stack([CS4[..., 0] + 1j * CS4[..., 1], CS4[..., 2] + 1j * CS4[..., 3]], axis=1)
+    else:
+        C = spinor_coefficients(CS4)[:, :, 0::2]                   # the unbarred spinors
+    nL, n = C.shape[0], C.shape[2]
+    Ct = np.einsum('Kuv,mvp->mKup', SIGMA, C) * (-1j / (2.0 * c_light))
+    Ct = Ct.reshape(3 * nL, 2, n)
+    a, b = Ct[:, 0], Ct[:, 1]
+    return np.ascontiguousarray(np.stack([a.real, a.imag, b.real, b.imag], axis=-1))
+
+
 def kramers_pairs(nKa):
     """Canonical Kramers-pair list (P<=Q), row-major."""
     return [(P, Q) for P in range(nKa) for Q in range(P, nKa)]

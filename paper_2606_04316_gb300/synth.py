@@ -60,6 +60,7 @@ class Problem:
     blocks: tuple              # subset of ("coulomb", "gaunt", "gauge")
     tau: float                 # Schwarz threshold
     kramers: bool = True       # False: CL/CS are per-spinor [nrows, n, 4] (Kramers-unrestricted)
+    rkb: bool = False          # True: CS holds nL restricted-kinetic-balance rows c^S [nL, n, 4]
 
     @property
     def nK(self) -> int:
@@ -152,6 +153,27 @@ def ku_chain_problem(n_centers, n_spinors, *, seed, shells=(0, 1), nprim=3, lo=0
     basis = make_basis(rng, xyz, lambda i: shells, nprim, lo, hi)
     CL, CS = ku_coefficients(rng, basis.nL, n_spinors)
     return Problem(name, basis, CL, CS, tuple(blocks), float(tau), kramers=False)
+
+
+def rkb_chain_problem(n_centers, n, *, seed, shells=(0, 1), nprim=3, lo=0.1, hi=10.0,
+                      blocks=("coulomb",), tau=1e-12, kramers=True, name="rkb-chain"):
+    """The chain recipe with restricted-kinetic-balance small components: CS
+    has nL rows (c^S of the large-component functions, not yet scaled by
+    1/2c).  Coefficient scale as in the derivative-basis recipe: columns
+    orthonormal over 4 nL rows, of which the first nL give c^L and the next
+    nL give c^S."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xyz = chain_xyz(rng, n_centers)
+    basis = make_basis(rng, xyz, lambda i: shells, nprim, lo, hi)
+    nL = basis.nL
+    if kramers:
+        Q = quaternion_mos(rng, 4 * nL, n)
+    else:
+        Z = rng.standard_normal((8 * nL, n)) + 1j * rng.standard_normal((8 * nL, n))
+        C = np.linalg.qr(Z)[0].reshape(4 * nL, 2, n)
+        Q = np.stack([C[:, 0].real, C[:, 0].imag, C[:, 1].real, C[:, 1].imag], axis=-1)
+    CL, CS = np.ascontiguousarray(Q[:nL]), np.ascontiguousarray(Q[nL:2 * nL])
+    return Problem(name, basis, CL, CS, tuple(blocks), float(tau), kramers=kramers, rkb=True)
 
 
 def chain_problem(n_centers, nK, *, seed, shells=(0, 1), nprim=3, lo=0.1, hi=10.0,
