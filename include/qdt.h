@@ -150,6 +150,20 @@ int qdt_set_coefficients(qdt_ctx *ctx, int nK, const double *CL, const double *C
  */
 int qdt_set_spinor_coefficients(qdt_ctx *ctx, int n_spinors, const double *CL, const double *CS);
 
+/*
+ * Restricted-kinetic-balance input (Eq. RKB, Sec. 2): the small component of
+ * each spinor is (1/2c) sigma.p applied to large-component functions, so CS
+ * has nL rows, CS[nL][n][4], like CL.  The library expands it over the
+ * derivative functions d_K chi_mu (p = -i grad) with coefficients
+ * (-i/2c) sigma_K c^S_mu on the device; the transform is then the same as
+ * for the expanded coefficients.  spinors = 0: quaternion columns (as
+ * qdt_set_coefficients, n = nK Kramers pairs); spinors != 0: unrestricted
+ * spinors (as qdt_set_spinor_coefficients).  c_light > 0 (atomic units:
+ * 137.035999084).  QDT_ERR_ARG on bad sizes or c; host or device, copied.
+ */
+int qdt_set_rkb_coefficients(qdt_ctx *ctx, int n, const double *CL, const double *CS, double c_light,
+                             int spinors);
+
 /* Bytes of the packed output of qdt_transform for these blocks and range
    (for the input kind last set: quaternion or Kramers-unrestricted). */
 size_t qdt_packed_size(const qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end);

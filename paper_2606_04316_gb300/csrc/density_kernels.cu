@@ -301,6 +301,39 @@ void launch_merge_rows(const double *in, const int *m0, const int *m1, int nrows
     QDT_CHECK_LAUNCH();
 }
 
+// Restricted kinetic balance (Eq. RKB): the small-component spinor
+// (1/2c) sigma.p chi_mu c_mu, p = -i grad, expands over the derivative
+// functions d_K chi_mu with coefficients (-i/2c) sigma_K c_mu.  in[nL][n][4]
+// holds (Re a, Im a, Re b, Im b) of each two-spinor c_mu; out[3 nL][n][4]
+// rows 3 mu + K.  sigma.p commutes with time reversal, so quaternion columns
+// (one spinor of a Kramers pair) map the same way as unrestricted spinors.
+__global__ void rkb_map_kernel(const double *in, long long nL, long long n, double h, double *out) {
+    const long long total = nL * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long mu = e / n, p = e - mu * n;
+        const double ar = in[4 * e], ai = in[4 * e + 1], br = in[4 * e + 2], bi = in[4 * e + 3];
+        double *o = out + 4 * (3 * mu * n + p);
+        // x: sigma_x (a, b) = (b, a);  y: (-i b, i a);  z: (a, -b); then times -i h
+        const double v[3][4] = {{bi * h, -br * h, ai * h, -ar * h},
+                                {-br * h, -bi * h, ar * h, ai * h},
+                                {ai * h, -ar * h, -bi * h, br * h}};
+#pragma unroll
+        for (int K = 0; K < 3; ++K)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[4 * K * n + j] = v[K][j];
+    }
+}
+
+void launch_rkb_map(const double *in, long long nL, long long n, double c_light, double *out,
+                    cudaStream_t s) {
+    if (nL <= 0 || n <= 0) return;
+    long long blocks = (nL * n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    rkb_map_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, nL, n, 0.5 / c_light, out);
+    QDT_CHECK_LAUNCH();
+}
+
 __global__ void zero_kernel(double *p, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)

@@ -11,6 +11,7 @@
 //   4. O = D^T V over all rows (second half, Eq. secondhalf, real form);
 //   5. pack the canonical Kramers quadruples.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -1206,19 +1207,29 @@ int qdt_num_functions(const qdt_ctx *c) { return (c && c->has_basis) ? c->nL : 0
 }  // extern "C"
 
 namespace {
-int set_coefficients(qdt_ctx *c, int nK, const double *CL, const double *CS, bool ku, const char *who) {
+// c_light > 0: CS holds nL restricted-kinetic-balance rows (Eq. RKB), mapped
+// onto the 3 nL derivative-function rows on the device first.
+int set_coefficients(qdt_ctx *c, int nK, const double *CL, const double *CS, bool ku, double c_light,
+                     const char *who) {
     if (!c) return QDT_ERR_ARG;
     try {
         QDT_CUDA_TRY(cudaSetDevice(c->device));
         if (!c->has_basis) throw Error{QDT_ERR_STATE, std::string(who) + ": no basis"};
         arg_check(nK > 0 && CL && CS, std::string(who) + ": the count must be positive and the arrays non-null");
+        arg_check(c_light >= 0.0 && std::isfinite(c_light), std::string(who) + ": c must be positive and finite");
         c->has_coef = false;
         // CL as given; CS (3 nL rows) merged onto the internal derivative functions
+        const bool rkb = c_light > 0.0;
         size_t nl = (size_t)c->nL * nK * 4, ns_in = (size_t)3 * c->nL * nK * 4, ns = (size_t)c->nS * nK * 4;
         double *d = (double *)c->Cq.get((nl + ns) * sizeof(double));
-        double *raw = (double *)c->Craw.get(ns_in * sizeof(double));
+        double *raw = (double *)c->Craw.get((ns_in + (rkb ? nl : 0)) * sizeof(double));
         QDT_CUDA_TRY(cudaMemcpyAsync(d, CL, nl * sizeof(double), cudaMemcpyDefault, c->stream));
-        QDT_CUDA_TRY(cudaMemcpyAsync(raw, CS, ns_in * sizeof(double), cudaMemcpyDefault, c->stream));
+        if (rkb) {
+            QDT_CUDA_TRY(cudaMemcpyAsync(raw + ns_in, CS, nl * sizeof(double), cudaMemcpyDefault, c->stream));
+            launch_rkb_map(raw + ns_in, c->nL, nK, c_light, raw, c->stream);
+        } else {
+            QDT_CUDA_TRY(cudaMemcpyAsync(raw, CS, ns_in * sizeof(double), cudaMemcpyDefault, c->stream));
+        }
         launch_merge_rows(raw, (const int *)c->dsmap0.p, (const int *)c->dsmap1.p, c->nS, nK * 4, d + nl, c->stream);
         QDT_CUDA_TRY(cudaStreamSynchronize(c->stream));
         c->nK = nK;
@@ -1235,11 +1246,20 @@ int set_coefficients(qdt_ctx *c, int nK, const double *CL, const double *CS, boo
 extern "C" {
 
 int qdt_set_coefficients(qdt_ctx *c, int nK, const double *CL, const double *CS) {
-    return set_coefficients(c, nK, CL, CS, false, "qdt_set_coefficients");
+    return set_coefficients(c, nK, CL, CS, false, 0.0, "qdt_set_coefficients");
 }
 
 int qdt_set_spinor_coefficients(qdt_ctx *c, int n_spinors, const double *CL, const double *CS) {
-    return set_coefficients(c, n_spinors, CL, CS, true, "qdt_set_spinor_coefficients");
+    return set_coefficients(c, n_spinors, CL, CS, true, 0.0, "qdt_set_spinor_coefficients");
+}
+
+int qdt_set_rkb_coefficients(qdt_ctx *c, int n, const double *CL, const double *CS, double c_light,
+                             int spinors) {
+    if (!(c_light > 0.0)) {
+        if (c) c->err = "qdt_set_rkb_coefficients: c must be positive";
+        return QDT_ERR_ARG;
+    }
+    return set_coefficients(c, n, CL, CS, spinors != 0, c_light, "qdt_set_rkb_coefficients");
 }
 
 size_t qdt_packed_size(const qdt_ctx *c, unsigned blocks, int k_begin, int k_end) {

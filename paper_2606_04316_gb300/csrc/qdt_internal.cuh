@@ -205,6 +205,9 @@ void launch_pack(const double *O, long long ldo, int nP, int parts, double *out,
 void launch_unpack(const double *packed, int n_units, int gaunt_like, bool ku, double *full, cudaStream_t s);
 void launch_zero(double *p, long long n, cudaStream_t s);
 // coefficient rows of the internal small-component basis: row r = in[m0[r]] (+ in[m1[r]])
+// Eq. RKB: c^S[nL][n][4] -> derivative-function coefficients [3 nL][n][4].
+void launch_rkb_map(const double *in, long long nL, long long n, double c_light, double *out,
+                    cudaStream_t s);
 void launch_merge_rows(const double *in, const int *m0, const int *m1, int nrows, int rowlen, double *out,
                        cudaStream_t s);
 
