@@ -440,6 +440,30 @@ def density_max(ob, cls, Dq):
     return Dm
 
 
+def coefficient_bound_max(ob, CL4, CS4):
+    """Screening bound of the O(N^5) quarter route (Sec. 2.2), which forms no
+    density: per Coulomb-class shell pair, 2 m_A m_B with m_F the largest
+    two-spinor norm |C_{fk}| over the shell's functions f and the given columns
+    (CL4 [nL, n, 4], CS4 [nS, n, 4]: Re a, Im a, Re b, Im b per column, Kramers
+    pairs or spinors alike).  By Cauchy-Schwarz it bounds every entry of the
+    symmetrised density of the pair (Eq. Den), partner columns included.  Rows
+    of identical derivative functions are summed first, as in density_max."""
+    nL = ob.nL
+    merged = np.zeros((ob.nS,) + CS4.shape[1:])
+    np.add.at(merged, ob.s_canonical, CS4)
+    C = np.concatenate([CL4, merged], axis=0)
+    sq = C[..., 0] ** 2 + C[..., 1] ** 2 + C[..., 2] ** 2 + C[..., 3] ** 2
+    m2 = sq.max(axis=1) if sq.shape[1] else np.zeros(sq.shape[0])
+    a, b, sp = ob.pairs(0)
+    ca = np.where(a >= nL, nL + ob.s_canonical[np.clip(a - nL, 0, None)], a)
+    cb = np.where(b >= nL, nL + ob.s_canonical[np.clip(b - nL, 0, None)], b)
+    ma = np.zeros(ob.n_shell_pairs(0))
+    mb = np.zeros(ob.n_shell_pairs(0))
+    np.maximum.at(ma, sp, m2[ca])
+    np.maximum.at(mb, sp, m2[cb])
+    return 2.0 * np.sqrt(ma) * np.sqrt(mb)
+
+
 def screen_mask(Q, Dmax, tau):
     """keep[AB, CD] = Q_AB * (Q_CD * Dmax_CD) >= tau (Eq. SchwarzDen)."""
     w = Q * Dmax
@@ -474,9 +498,10 @@ def apply_screen(ob, cls, G, mask):
 class Transform:
     """Everything the oracle knows about one transformation request."""
 
-    def __init__(self, problem, k_begin=0, k_end=None, tau=None):
+    def __init__(self, problem, k_begin=0, k_end=None, tau=None, bound="density"):
         self.p = problem
         self.ob = OracleBasis(problem.basis)
+        self.bound = bound       # Coulomb screening weight: "density" or "coefficients"
         self.k_begin = k_begin
         self.k_end = problem.nK if k_end is None else k_end
         self.nKa = self.k_end - self.k_begin
@@ -510,7 +535,11 @@ class Transform:
         key = "mask%d" % cls
         if key not in self._cache:
             Q = schwarz_q(self.ob, cls)
-            Dm = density_max(self.ob, cls, self.density(block))
+            if cls == 0 and self.bound == "coefficients":
+                ks = slice(self.k_begin, self.k_end)
+                Dm = coefficient_bound_max(self.ob, self.p.CL[:, ks], self.p.CS[:, ks])
+            else:
+                Dm = density_max(self.ob, cls, self.density(block))
             self._cache[key] = screen_mask(Q, Dm, self.tau)
             self._cache["Q%d" % cls] = Q
             self._cache["Dmax%d" % cls] = Dm
@@ -594,9 +623,10 @@ class TransformKU(Transform):
     active spinors.  G, screening rule and the literal definition full() are
     the Kramers-restricted ones; the densities are those of spinor pairs."""
 
-    def __init__(self, problem, s_begin=0, s_end=None, tau=None):
+    def __init__(self, problem, s_begin=0, s_end=None, tau=None, bound="density"):
         self.p = problem
         self.ob = OracleBasis(problem.basis)
+        self.bound = bound
         self.k_begin = s_begin
         self.k_end = problem.CL.shape[1] if s_end is None else s_end
         self.n = self.k_end - self.k_begin
