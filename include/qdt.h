@@ -81,6 +81,8 @@ extern "C" {
 #define QDT_FP64 0                  /* all-FP64 contractions                        */
 #define QDT_SPLIT 1                 /* Ozaki BF16 slices, exact FP32 chunks, FP64 recombination */
 
+#define QDT_ROUTE_DENSITY 0         /* first half through the pair density (Eq. firsthalf) */
+#define QDT_ROUTE_QUARTER 1         /* Coulomb first half by two O(N^5) quarter steps      */
 #define QDT_MAX_L 2                 /* largest large-component shell order accepted */
 
 typedef struct qdt_ctx qdt_ctx;
@@ -163,6 +165,20 @@ int qdt_set_spinor_coefficients(qdt_ctx *ctx, int n_spinors, const double *CL, c
  */
 int qdt_set_rkb_coefficients(qdt_ctx *ctx, int n, const double *CL, const double *CS, double c_light,
                              int spinors);
+
+/*
+ * First-half route of the Coulomb block for later qdt_transform calls
+ * (Sec. 2.2 and the appendix's operation counts): QDT_ROUTE_DENSITY (default)
+ * contracts the integrals with the pair density (Eq. firsthalf);
+ * QDT_ROUTE_QUARTER, a comparator, contracts one AO index at a time with the
+ * coefficients, T1 = sum_d (ab|cd) C_d then V = sum_c C*_c T1, and screens
+ * on coefficient bounds (2 max|C_c| max|C_d| per ket shell pair) since it
+ * forms no density.  Same output layout and second half; the Gaunt and gauge
+ * blocks always take the density route.  qdt_transform_batch rejects contexts
+ * on the quarter route (QDT_ERR_UNIMPLEMENTED).  QDT_ERR_ARG on an unknown
+ * route.
+ */
+int qdt_set_route(qdt_ctx *ctx, int route);
 
 /* Bytes of the packed output of qdt_transform for these blocks and range
    (for the input kind last set: quaternion or Kramers-unrestricted). */

@@ -107,6 +107,10 @@ struct qdt_ctx {
     DBuf Dbra, Dket, V, Vg, W, Wc, Dmax, wsort, ketsp, ketcol, prefix, ktile, tasks, O, partial,
         stage, rsR, rsS, kpos, prms, next, ktile2;
     SplitWorkspace split;
+    // first-half route of the Coulomb block: density (Eq. firsthalf) or the
+    // two-quarter comparator, and the comparator's workspace
+    int route = QDT_ROUTE_DENSITY;
+    DBuf qcols, qWL, qWS, qT1, qT, qVf, qCr1, qCr2, qkt[3];
     cudaEvent_t ev[16];
     int launches = 0;
     // batches owned by this context (its stream carries the fused launches)
@@ -146,6 +150,8 @@ long long packed_block_elems(bool ku, long long n) {
 // (6 BF16 digits per element, 12 bytes) stay within kSliceBudget, so the
 // integral rows themselves decide whether a class fits one row batch.
 constexpr size_t kSliceBudget = (size_t)8 << 30;
+// FP64 intermediates of one row chunk of the quarter route
+constexpr size_t kQuarterBudget = (size_t)4 << 30;
 
 // FP64 multiply-adds of the E R E contraction of one shell quartet with X as
 // the outer (per primitive pair) side: the ket pass over T rows (X's Hermite
@@ -391,6 +397,8 @@ struct ClassPlan {
     double tau = 0;
     bool ls = false, one_batch = true;
     bool ku = false;          // columns are spinor pairs with 2 parts (Kramers-unrestricted input)
+    bool quarter = false;     // Coulomb first half by two quarter steps (no ket density)
+    int2 *qcols = nullptr;    // function indices of the ket-ordered integral columns
     long long N4 = 0, ncolD = 0, M = 0, NV = 0;
     double *Dbra = nullptr, *Dmax = nullptr, *Dket = nullptr, *Vc = nullptr, *Vg = nullptr;
     int *prefix = nullptr, *ketsp = nullptr, *d_kpos = nullptr;
@@ -415,6 +423,7 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
     P.nRS = nKa * (nKa + 1) / 2;
     P.ls = cr.c == 1;
     P.ku = ctx->ku;
+    P.quarter = !P.ls && ctx->route == QDT_ROUTE_QUARTER;
     P.N4 = (P.ku ? 2LL : 4LL) * P.nRS;          // columns per J component
     P.ncolD = P.ls ? 3 * P.N4 : P.N4;            // density row length
     P.NV = P.ls ? 3 * P.N4 : P.N4;               // V row length (Coulomb / Gaunt)
@@ -434,6 +443,11 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
     launch_density(P.ls, P.ku, pc.d_pairs, pc.d_bra_order, pc.nsp, (const ShellDev *)ctx->shells.p,
                    (const double *)ctx->Cq.p, ctx->nK, k0, d_rsR, d_rsS, P.nRS, P.Dbra, P.Dmax, s);
     ctx->launches++;
+    if (P.quarter) {   // the quarter route screens on coefficient bounds, not on the density
+        launch_coef_bound(pc.d_pairs, (const ShellDev *)ctx->shells.p, (const double *)ctx->Cq.p, ctx->nK, k0,
+                          nKa, pc.nsp, P.Dmax, s);
+        ctx->launches++;
+    }
     tm.mark();
     // 2. ket order and prefixes
     double *wsort = (double *)ctx->wsort.get(std::max(1, pc.nsp) * sizeof(double));
@@ -450,9 +464,20 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
     QDT_CUDA_TRY(cudaMemcpyAsync(P.h_prefix.data(), P.prefix, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
     QDT_CUDA_TRY(cudaMemcpyAsync(P.h_col.data(), P.ketcol, (pc.nsp + 1) * sizeof(long long), cudaMemcpyDeviceToHost, s));
     QDT_CUDA_TRY(cudaMemcpyAsync(P.h_ketsp.data(), P.ketsp, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
-    // 3. ket-ordered density copy
-    P.Dket = (double *)ctx->Dket.get(std::max<long long>(1, P.M * P.ncolD) * sizeof(double));
-    launch_gather_rows(P.Dbra, pc.d_pairs, P.ketsp, P.ketcol, pc.nsp, P.ncolD, P.Dket, s);
+    // 3. ket-ordered density copy (density route) or the function indices of
+    // the ket-ordered columns (quarter route)
+    if (P.quarter) {
+        P.qcols = (int2 *)ctx->qcols.get(std::max<long long>(1, P.M) * sizeof(int2));
+        launch_ket_functions(pc.d_pairs, (const ShellDev *)ctx->shells.p, P.ketsp, P.ketcol, pc.nsp, P.qcols, s);
+        const long long nX = ctx->nL + ctx->nS, Pp = P.ku ? 2 : 4;
+        double *Cr1 = (double *)ctx->qCr1.get((size_t)nX * 4 * nKa * sizeof(double));
+        double *Cr2 = (double *)ctx->qCr2.get((size_t)4 * nX * Pp * nKa * sizeof(double));
+        launch_quarter_coefs((const double *)ctx->Cq.p, ctx->nK, k0, nKa, (int)nX, (int)Pp, Cr1, Cr2, s);
+        ctx->launches++;
+    } else {
+        P.Dket = (double *)ctx->Dket.get(std::max<long long>(1, P.M * P.ncolD) * sizeof(double));
+        launch_gather_rows(P.Dbra, pc.d_pairs, P.ketsp, P.ketcol, pc.nsp, P.ncolD, P.Dket, s);
+    }
     ctx->launches++;
     tm.mark();
 }
@@ -487,7 +512,8 @@ void class_finish(qdt_ctx *ctx, ClassPlan &P, qdt_stats *st) {
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
     const size_t usable = (size_t)(0.7 * (double)(fr + ctx->W.n + ctx->Wc.n + split_held_bytes(ctx->split)));
     const double wfac = (P.ls && P.cr.gauge && P.cr.gaunt) ? 1.12 : 1.0;
-    const double slices = P.precision == QDT_SPLIT ? 1.1 * (double)kSliceBudget : 0.0;
+    const double slices = (P.precision == QDT_SPLIT ? 1.1 * (double)kSliceBudget : 0.0) +
+                          (P.quarter ? 1.1 * (double)kQuarterBudget : 0.0);
     P.one_batch = (double)wall * wfac + slices <= (double)usable;
     // what the decision counted as reusable is handed back first
     if (P.one_batch && (double)wall * wfac + slices > 0.7 * (double)(fr + ctx->W.n + ctx->Wc.n)) split_release(ctx->split);
@@ -602,6 +628,7 @@ void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, qdt_stats 
     }
     st->eri_values += v * (B.prm.gauge ? 6 : 1);
     st->flops_eri += fl;
+    if (P.quarter) return;   // counted by quarter_half1
     const long long Wrows = B.rows * P.mult;
     double f = 0;
     for (long long t = 0; t < (long long)B.kt.size(); ++t) f += (double)std::min<long long>(TMr, Wrows - t * TMr) * B.kt[t];
@@ -681,6 +708,69 @@ void batch_half1(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, cudaStream
     }
 }
 
+// Rows per chunk of the quarter route: its FP64 intermediates within
+// kQuarterBudget, the split form's digit planes of the largest A operand within
+// kSliceBudget, and grid rows of the contraction within range.
+long long quarter_chunk_rows(const qdt_ctx *ctx, const ClassPlan &P, long long rows) {
+    const long long nL = ctx->nL, nS = ctx->nS, nX = nL + nS, n = P.nKa, Pp = P.ku ? 2 : 4;
+    const double per = 8.0 * (double)(nL * nL + nS * nS + 2 * nX * 4 * n + n * Pp * n);
+    long long rc = (long long)((double)kQuarterBudget / per);
+    if (P.precision == QDT_SPLIT) {
+        const double a = 12.0 * (double)std::max(nS * ((nS + 63) / 64 * 64), n * ((4 * nX + 63) / 64 * 64));
+        rc = std::min(rc, (long long)((double)kSliceBudget / a));
+    }
+    rc = std::min(rc, (long long)(65535LL * 64 / std::max(nX, n)));
+    if (const char *e = std::getenv("QDT_QUARTER_CHUNK_ROWS")) {      // smaller chunks, to exercise them
+        const long long v = std::atoll(e);
+        if (v <= 0) throw Error{QDT_ERR_ARG, "QDT_QUARTER_CHUNK_ROWS must be positive"};
+        rc = std::min(rc, v);
+    }
+    return std::max<long long>(1, std::min(rc, rows));
+}
+
+// First half of a Coulomb batch by two quarter steps (launches only): integral
+// rows -> square blocks, T1 = W C (quarter 1, L and S blocks), re-lay, V =
+// T1 Cr2 (quarter 2), gather of the canonical column pairs into V.
+void quarter_half1(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, qdt_stats *st, cudaStream_t s) {
+    const int TMr = gemm_fp64_tile_m();
+    const long long nL = ctx->nL, nS = ctx->nS, nX = nL + nS, n = P.nKa, Pp = P.ku ? 2 : 4;
+    const long long rc = quarter_chunk_rows(ctx, P, B.rows);
+    double *WL = (double *)ctx->qWL.get((size_t)rc * nL * nL * sizeof(double));
+    double *WS = (double *)ctx->qWS.get((size_t)rc * nS * nS * sizeof(double));
+    double *T1 = (double *)ctx->qT1.get((size_t)rc * nX * 4 * n * sizeof(double));
+    double *T = (double *)ctx->qT.get((size_t)rc * n * 4 * nX * sizeof(double));
+    double *Vf = (double *)ctx->qVf.get((size_t)rc * n * Pp * n * sizeof(double));
+    double *Cr1 = (double *)ctx->qCr1.p, *Cr2 = (double *)ctx->qCr2.p;
+    // K extents per 64-row tile: constant for each of the three contractions
+    const long long Ks[3] = {nL, nS, 4 * nX}, Ms[3] = {rc * nL, rc * nS, rc * n};
+    std::vector<long long> hk[3];
+    long long *dk[3];
+    for (int g = 0; g < 3; ++g) {
+        hk[g].assign((size_t)((Ms[g] + TMr - 1) / TMr), Ks[g]);
+        dk[g] = dcopy(ctx->qkt[g], hk[g], s);
+    }
+    auto sub = [&](int g, long long m) {
+        return std::vector<long long>(hk[g].begin(), hk[g].begin() + (m + TMr - 1) / TMr);
+    };
+    const long long ncols = P.M;   // every ket column of the class
+    for (long long r0 = 0; r0 < B.rows; r0 += rc) {
+        const long long m = std::min(rc, B.rows - r0);
+        launch_square_rows(B.W + r0 * B.ldw, B.ldw, P.qcols, ncols, (int)nL, (int)nS, m, WL, WS, s);
+        gemm_half1(ctx->split, P.precision, WL, nL, Cr1, 4 * n, T1, 4 * n, m * nL, 4 * n, dk[0], sub(0, m * nL), s);
+        gemm_half1(ctx->split, P.precision, WS, nS, Cr1 + nL * 4 * n, 4 * n, T1 + m * nL * 4 * n, 4 * n, m * nS,
+                   4 * n, dk[1], sub(1, m * nS), s);
+        launch_t1_transpose(T1, T1 + m * nL * 4 * n, (int)nL, (int)nS, (int)n, m, T, s);
+        gemm_half1(ctx->split, P.precision, T, 4 * nX, Cr2, Pp * n, Vf, Pp * n, m * n, Pp * n, dk[2],
+                   sub(2, m * n), s);
+        launch_quarter_gather(Vf, (int)n, (int)Pp, (const int *)ctx->rsR.p, (const int *)ctx->rsS.p, P.nRS, m,
+                              P.Vc + (B.row0 + r0) * P.N4, s);
+        ctx->launches += 6;
+        if (st)
+            st->flops_half1 += 2.0 * (double)m * (double)(nL * nL + nS * nS) * (double)(4 * n) +
+                               2.0 * (double)(m * n) * (double)(4 * nX) * (double)(Pp * n);
+    }
+}
+
 // Second-half operands of a class: the jobs (V, K, packed output) and buffers.
 struct Half2 {
     struct Job { const double *V; long long K; double *out; };
@@ -751,7 +841,10 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
         ctx->launches += 2 + (B.Wc ? 1 : 0);
         batch_stats(ctx, P, B, st);
         int th = tm.n; tm.mark();
-        batch_half1(ctx, P, B, s);
+        if (P.quarter)
+            quarter_half1(ctx, P, B, st, s);
+        else
+            batch_half1(ctx, P, B, s);
         int tend = tm.n; tm.mark();
         QDT_CUDA_TRY(cudaStreamSynchronize(s));
         ms_eri += tm.ms(te, th);
@@ -1099,7 +1192,9 @@ void qdt_destroy(qdt_ctx *c) {
                     &c->prefix, &c->ktile, &c->tasks, &c->O, &c->partial, &c->stage, &c->rsR, &c->rsS,
                     &c->kpos, &c->prms, &c->next, &c->ktile2, &c->bprms[0], &c->bprms[1],
                     &c->bprms[2], &c->bprms[3], &c->btasks[0], &c->btasks[1], &c->btasks[2],
-                    &c->btasks[3], &c->bnext[0], &c->bnext[1], &c->bnext[2], &c->bnext[3]};
+                    &c->btasks[3], &c->bnext[0], &c->bnext[1], &c->bnext[2], &c->bnext[3], &c->qcols,
+                    &c->qWL, &c->qWS, &c->qT1, &c->qT, &c->qVf, &c->qCr1, &c->qCr2, &c->qkt[0],
+                    &c->qkt[1], &c->qkt[2]};
     for (DBuf *b : bufs) b->release();
     for (int k = 0; k < 2; ++k) {
         c->cb[k].pairs.release(); c->cb[k].pp.release(); c->cb[k].E.release(); c->cb[k].E2.release();
@@ -1262,6 +1357,17 @@ int qdt_set_rkb_coefficients(qdt_ctx *c, int n, const double *CL, const double *
     return set_coefficients(c, n, CL, CS, spinors != 0, c_light, "qdt_set_rkb_coefficients");
 }
 
+int qdt_set_route(qdt_ctx *c, int route) {
+    if (!c) return QDT_ERR_ARG;
+    if (route != QDT_ROUTE_DENSITY && route != QDT_ROUTE_QUARTER) {
+        c->err = "qdt_set_route: route must be QDT_ROUTE_DENSITY or QDT_ROUTE_QUARTER";
+        return QDT_ERR_ARG;
+    }
+    c->route = route;
+    c->err.clear();
+    return QDT_OK;
+}
+
 size_t qdt_packed_size(const qdt_ctx *c, unsigned blocks, int k_begin, int k_end) {
     if (k_end <= k_begin) return 0;
     const bool ku = c && c->has_coef && c->ku;
@@ -1339,6 +1445,8 @@ int qdt_transform_batch(qdt_batch_item *items, int n, unsigned flags) {
             QDT_CUDA_TRY(cudaSetDevice(r.c->device));
             cudaGetLastError();
             if (!r.c->has_basis || !r.c->has_coef) throw Error{QDT_ERR_STATE, "qdt_transform_batch: basis or coefficients not set"};
+            if (r.c->route != QDT_ROUTE_DENSITY)
+                throw Error{QDT_ERR_UNIMPLEMENTED, "qdt_transform_batch: the quarter-transform route runs through qdt_transform only"};
             const qdt_batch_item &it = items[i];
             arg_check(it.blocks != 0 && (it.blocks & ~7u) == 0, "qdt_transform_batch: blocks must be a non-empty subset of COULOMB|GAUNT|GAUGE");
             arg_check(it.k_begin >= 0 && it.k_end > it.k_begin && it.k_end <= r.c->nK, "qdt_transform_batch: bad Kramers range");

@@ -208,6 +208,19 @@ void launch_zero(double *p, long long n, cudaStream_t s);
 // Eq. RKB: c^S[nL][n][4] -> derivative-function coefficients [3 nL][n][4].
 void launch_rkb_map(const double *in, long long nL, long long n, double c_light, double *out,
                     cudaStream_t s);
+// Quarter-transform comparator of the Coulomb first half (quarter_kernels.cu).
+void launch_ket_functions(const PairDev *pairs, const ShellDev *shells, const int *ket_sp,
+                          const long long *ket_col, int nsp, int2 *cols, cudaStream_t s);
+void launch_coef_bound(const PairDev *pairs, const ShellDev *shells, const double *Cq, int nK, int k0,
+                       int nKa, int nsp, double *Dmax, cudaStream_t s);
+void launch_quarter_coefs(const double *Cq, int nK, int k0, int n, int nX, int P, double *Cr1, double *Cr2,
+                          cudaStream_t s);
+void launch_square_rows(const double *W, long long ldw, const int2 *cols, long long ncols, int nL, int nS,
+                        long long rows, double *WL, double *WS, cudaStream_t s);
+void launch_t1_transpose(const double *TL, const double *TS, int nL, int nS, int n, long long rows, double *T,
+                         cudaStream_t s);
+void launch_quarter_gather(const double *Vf, int n, int P, const int *rsR, const int *rsS, int nRS,
+                           long long rows, double *V, cudaStream_t s);
 void launch_merge_rows(const double *in, const int *m0, const int *m1, int nrows, int rowlen, double *out,
                        cudaStream_t s);
 
