@@ -577,6 +577,48 @@ class Transform:
     def packed(self, block, screened=True):
         return pack_canonical(self.packed_full(block, screened), self.nKa)
 
+    # MO-driven route (Sec. 3.3) ----------------------------------------------
+    def _n_parts(self):
+        return self.nKa, 4
+
+    def mask_columns(self, block, c0, c1):
+        """Screening mask from the density maximum over the columns [c0, c1)
+        only (every J component of an L-S density)."""
+        cls = 0 if block == "coulomb" else 1
+        Q = schwarz_q(self.ob, cls)
+        Dm = density_max(self.ob, cls, self.density(block)[..., c0:c1])
+        return screen_mask(Q, Dm, self.tau)
+
+    def packed_full_mo(self, block, nb):
+        """O of the MO-driven route: the outer MO index r runs in blocks of nb;
+        the density columns (r, s >= r, part) of a block are contracted with
+        the integrals that the block's own density maximum keeps."""
+        n, parts = self._n_parts()
+        cls = 0 if block == "coulomb" else 1
+        D = self.density(block)
+        ncol = D.shape[-1]
+        out = np.zeros((ncol, ncol))
+        for r0 in range(0, n, nb):
+            r1 = min(n, r0 + nb)
+            c0 = parts * pair_index(r0, r0, n)
+            c1 = parts * pair_index(r1, r1, n) if r1 < n else ncol
+            G = apply_screen(self.ob, cls, self.G(block), self.mask_columns(block, c0, c1))
+            if block == "coulomb":
+                out[:, c0:c1] = D.T @ (G @ D[:, c0:c1])
+            elif block == "gaunt":
+                for J in range(3):
+                    out[:, c0:c1] += D[:, J, :].T @ (G @ D[:, J, c0:c1])
+            else:
+                for ij, (I, J) in enumerate(IJ6):
+                    K = G[ij]
+                    out[:, c0:c1] += D[:, I, :].T @ (K @ D[:, J, c0:c1])
+                    if I != J:
+                        out[:, c0:c1] += D[:, J, :].T @ (K.T @ D[:, I, c0:c1])
+        return out
+
+    def packed_mo(self, block, nb):
+        return pack_canonical(self.packed_full_mo(block, nb), self.nKa)
+
     # plain definition: full complex (pq|rs) ---------------------------------
     def full(self, block, screened=True):
         """(pq|rs) over all 2 nKa spinors by the literal sum over ordered AO
@@ -646,6 +688,12 @@ class TransformKU(Transform):
 
     def packed(self, block, screened=True):
         return pack_canonical_ku(self.packed_full(block, screened), self.n)
+
+    def _n_parts(self):
+        return self.n, 2
+
+    def packed_mo(self, block, nb):
+        return pack_canonical_ku(self.packed_full_mo(block, nb), self.n)
 
 
 # -------------------------------------------------------------- packing
