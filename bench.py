@@ -195,6 +195,8 @@ def config_dict(args, problem, blocks):
          "precision": args.precision, "l2": "inputs larger than L2 (densities, integral rows)"}
     if getattr(args, "route", "density") != "density":
         d["route"] = args.route
+        if args.route == "mo":
+            d["mo_block"] = args.mo_block
     if not problem.kramers:
         del d["n_kramers"]
         d["n_spinors"] = problem.nK
@@ -329,8 +331,9 @@ def main():
     ap.add_argument("--input", default="kramers", choices=["kramers", "ku"],
                     help="coefficients: quaternion (Kramers pairs) or Kramers-unrestricted spinors")
     ap.add_argument("--precision", default="split", choices=["split", "fp64"])
-    ap.add_argument("--route", default="density", choices=["density", "quarter"],
-                    help="Coulomb first half: density contraction or the O(N^5) two-quarter comparator")
+    ap.add_argument("--route", default="density", choices=["density", "quarter", "mo"],
+                    help="density (AO-driven), quarter (O(N^5) Coulomb first half) or mo (MO-driven comparator)")
+    ap.add_argument("--mo-block", type=int, default=8, help="MO-driven route: outer MO indices per block")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 form (0: skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -368,7 +371,7 @@ def main():
     CSd = torch.from_numpy(problem.CS).cuda()
     set_coefs = ctx.set_coefficients if problem.kramers else ctx.set_spinor_coefficients
     set_coefs(CLd, CSd)
-    ctx.set_route(args.route)
+    ctx.set_route(args.route, args.mo_block if args.route == "mo" else 0)
     nK = problem.nK
     prec = qdt.SPLIT if args.precision == "split" else qdt.FP64
     nout = ctx.packed_size(blocks, 0, nK) // 8

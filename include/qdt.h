@@ -83,6 +83,7 @@ extern "C" {
 
 #define QDT_ROUTE_DENSITY 0         /* first half through the pair density (Eq. firsthalf) */
 #define QDT_ROUTE_QUARTER 1         /* Coulomb first half by two O(N^5) quarter steps      */
+#define QDT_ROUTE_MO 2              /* MO-driven: integrals recomputed per outer-MO block   */
 #define QDT_MAX_L 2                 /* largest large-component shell order accepted */
 
 typedef struct qdt_ctx qdt_ctx;
@@ -167,18 +168,25 @@ int qdt_set_rkb_coefficients(qdt_ctx *ctx, int n, const double *CL, const double
                              int spinors);
 
 /*
- * First-half route of the Coulomb block for later qdt_transform calls
- * (Sec. 2.2 and the appendix's operation counts): QDT_ROUTE_DENSITY (default)
- * contracts the integrals with the pair density (Eq. firsthalf);
- * QDT_ROUTE_QUARTER, a comparator, contracts one AO index at a time with the
- * coefficients, T1 = sum_d (ab|cd) C_d then V = sum_c C*_c T1, and screens
- * on coefficient bounds (2 max|C_c| max|C_d| per ket shell pair) since it
- * forms no density.  Same output layout and second half; the Gaunt and gauge
- * blocks always take the density route.  qdt_transform_batch rejects contexts
- * on the quarter route (QDT_ERR_UNIMPLEMENTED).  QDT_ERR_ARG on an unknown
- * route.
+ * Transformation route for later qdt_transform calls (Sec. 2.2, Sec. 3.3 and
+ * the appendix's operation counts):
+ *   QDT_ROUTE_DENSITY (default): AO-driven; every kept integral is computed
+ *     once and contracted with the pair density (Eq. firsthalf).
+ *   QDT_ROUTE_QUARTER, a comparator for the Coulomb block: the first half
+ *     contracts one AO index at a time with the coefficients, T1 = sum_d
+ *     (ab|cd) C_d then V = sum_c C*_c T1, and screens on coefficient bounds
+ *     (2 max|C_c| max|C_d| per ket shell pair) since it forms no density.
+ *     The Gaunt and gauge blocks take the density route.
+ *   QDT_ROUTE_MO, a comparator for every block: MO-driven; the outer MO index
+ *     r (Kramers pair or spinor of the active range) runs in blocks of
+ *     mo_block, and each block screens on the density of its own columns
+ *     (r, s >= r) and recomputes every integral it keeps.
+ * The output layout and the second half are the same on every route.
+ * mo_block is read for QDT_ROUTE_MO only (> 0).  qdt_transform_batch rejects
+ * contexts on the comparator routes (QDT_ERR_UNIMPLEMENTED).  QDT_ERR_ARG on
+ * an unknown route or a bad block size.
  */
-int qdt_set_route(qdt_ctx *ctx, int route);
+int qdt_set_route(qdt_ctx *ctx, int route, int mo_block);
 
 /* Bytes of the packed output of qdt_transform for these blocks and range
    (for the input kind last set: quaternion or Kramers-unrestricted). */

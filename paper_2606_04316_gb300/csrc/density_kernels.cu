@@ -166,6 +166,29 @@ void launch_density(bool gaunt, bool ku, const PairDev *pairs, const int *bra_or
     QDT_CHECK_LAUNCH();
 }
 
+// Dmax of one MO block (MO-driven route): the largest |entry| of the density
+// rows of each shell pair over the block's columns [c0, c1) of each of the nJ
+// column groups (row length ld, group stride N4).
+__global__ void block_dmax_kernel(const PairDev *pairs, const double *D, long long ld, int nJ, long long N4,
+                                  long long c0, long long c1, double *Dmax) {
+    const PairDev pr = pairs[blockIdx.x];
+    const long long w = c1 - c0, per_row = (long long)nJ * w;
+    double vmax = 0.0;
+    for (long long i = threadIdx.x; i < (long long)pr.nfp * per_row; i += blockDim.x) {
+        const long long r = i / per_row, rem = i - r * per_row, J = rem / w, c = rem - J * w;
+        vmax = fmax(vmax, fabs(D[(pr.rowoff + r) * ld + J * N4 + c0 + c]));
+    }
+    vmax = block_max(vmax);
+    if (threadIdx.x == 0) Dmax[blockIdx.x] = vmax;
+}
+
+void launch_block_dmax(const PairDev *pairs, int nsp, const double *D, long long ld, int nJ, long long N4,
+                       long long c0, long long c1, double *Dmax, cudaStream_t s) {
+    if (nsp <= 0) return;
+    block_dmax_kernel<<<nsp, 256, 0, s>>>(pairs, D, ld, nJ, N4, c0, c1, Dmax);
+    QDT_CHECK_LAUNCH();
+}
+
 // ----------------------------------------------------------- ket ordering
 // w_CD = Q_CD * Dmax_CD; ket positions sorted by w descending (ties: pair id
 // ascending) by rank counting.  A bra pair AB keeps exactly the ket prefix

@@ -110,6 +110,7 @@ struct qdt_ctx {
     // first-half route of the Coulomb block: density (Eq. firsthalf) or the
     // two-quarter comparator, and the comparator's workspace
     int route = QDT_ROUTE_DENSITY;
+    int mo_block = 0;           // outer MO indices per block of the MO-driven route
     DBuf qcols, qWL, qWS, qT1, qT, qVf, qCr1, qCr2, qkt[3];
     cudaEvent_t ev[16];
     int launches = 0;
@@ -408,6 +409,43 @@ struct ClassPlan {
     size_t wbudget = 0;
 };
 
+// Steps 2-3 for the current P.Dmax: ket order and kept prefixes (copied to
+// the host), then the ket-ordered density copy (density route) or the
+// function indices of the ket-ordered columns (quarter route).
+void order_kets(qdt_ctx *ctx, ClassPlan &P, cudaStream_t s) {
+    PairClass &pc = ctx->cls[P.cr.c];
+    const double tau = P.tau;
+    double *wsort = (double *)ctx->wsort.get(std::max(1, pc.nsp) * sizeof(double));
+    P.ketsp = (int *)ctx->ketsp.get(std::max(1, pc.nsp) * sizeof(int));
+    P.ketcol = (long long *)ctx->ketcol.get((pc.nsp + 1) * sizeof(long long));
+    P.prefix = (int *)ctx->prefix.get(std::max(1, pc.nsp) * sizeof(int));
+    launch_ket_order(pc.d_Q, P.Dmax, pc.nsp, wsort, P.ketsp, s);
+    launch_ket_columns(pc.d_pairs, P.ketsp, pc.nsp, P.ketcol, s);
+    launch_prefix_lengths(pc.d_Q, wsort, pc.nsp, tau, P.prefix, s);
+    ctx->launches += 3;
+    P.h_prefix.resize(pc.nsp);
+    P.h_col.resize(pc.nsp + 1);
+    P.h_ketsp.resize(pc.nsp);
+    QDT_CUDA_TRY(cudaMemcpyAsync(P.h_prefix.data(), P.prefix, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
+    QDT_CUDA_TRY(cudaMemcpyAsync(P.h_col.data(), P.ketcol, (pc.nsp + 1) * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    QDT_CUDA_TRY(cudaMemcpyAsync(P.h_ketsp.data(), P.ketsp, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
+    // 3. ket-ordered density copy (density route) or the function indices of
+    // the ket-ordered columns (quarter route)
+    if (P.quarter) {
+        P.qcols = (int2 *)ctx->qcols.get(std::max<long long>(1, P.M) * sizeof(int2));
+        launch_ket_functions(pc.d_pairs, (const ShellDev *)ctx->shells.p, P.ketsp, P.ketcol, pc.nsp, P.qcols, s);
+        const long long nX = ctx->nL + ctx->nS, Pp = P.ku ? 2 : 4;
+        double *Cr1 = (double *)ctx->qCr1.get((size_t)nX * 4 * P.nKa * sizeof(double));
+        double *Cr2 = (double *)ctx->qCr2.get((size_t)4 * nX * Pp * P.nKa * sizeof(double));
+        launch_quarter_coefs((const double *)ctx->Cq.p, ctx->nK, P.k0, P.nKa, (int)nX, (int)Pp, Cr1, Cr2, s);
+        ctx->launches++;
+    } else {
+        P.Dket = (double *)ctx->Dket.get(std::max<long long>(1, P.M * P.ncolD) * sizeof(double));
+        launch_gather_rows(P.Dbra, pc.d_pairs, P.ketsp, P.ketcol, pc.nsp, P.ncolD, P.Dket, s);
+    }
+    ctx->launches++;
+}
+
 // Steps 1-3 on the context's stream: density in bra order and Dmax, ket order
 // and kept prefixes (copied to the host), ket-ordered density copy.
 void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, int precision, ClassPlan &P,
@@ -449,36 +487,7 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
         ctx->launches++;
     }
     tm.mark();
-    // 2. ket order and prefixes
-    double *wsort = (double *)ctx->wsort.get(std::max(1, pc.nsp) * sizeof(double));
-    P.ketsp = (int *)ctx->ketsp.get(std::max(1, pc.nsp) * sizeof(int));
-    P.ketcol = (long long *)ctx->ketcol.get((pc.nsp + 1) * sizeof(long long));
-    P.prefix = (int *)ctx->prefix.get(std::max(1, pc.nsp) * sizeof(int));
-    launch_ket_order(pc.d_Q, P.Dmax, pc.nsp, wsort, P.ketsp, s);
-    launch_ket_columns(pc.d_pairs, P.ketsp, pc.nsp, P.ketcol, s);
-    launch_prefix_lengths(pc.d_Q, wsort, pc.nsp, tau, P.prefix, s);
-    ctx->launches += 3;
-    P.h_prefix.resize(pc.nsp);
-    P.h_col.resize(pc.nsp + 1);
-    P.h_ketsp.resize(pc.nsp);
-    QDT_CUDA_TRY(cudaMemcpyAsync(P.h_prefix.data(), P.prefix, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
-    QDT_CUDA_TRY(cudaMemcpyAsync(P.h_col.data(), P.ketcol, (pc.nsp + 1) * sizeof(long long), cudaMemcpyDeviceToHost, s));
-    QDT_CUDA_TRY(cudaMemcpyAsync(P.h_ketsp.data(), P.ketsp, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
-    // 3. ket-ordered density copy (density route) or the function indices of
-    // the ket-ordered columns (quarter route)
-    if (P.quarter) {
-        P.qcols = (int2 *)ctx->qcols.get(std::max<long long>(1, P.M) * sizeof(int2));
-        launch_ket_functions(pc.d_pairs, (const ShellDev *)ctx->shells.p, P.ketsp, P.ketcol, pc.nsp, P.qcols, s);
-        const long long nX = ctx->nL + ctx->nS, Pp = P.ku ? 2 : 4;
-        double *Cr1 = (double *)ctx->qCr1.get((size_t)nX * 4 * nKa * sizeof(double));
-        double *Cr2 = (double *)ctx->qCr2.get((size_t)4 * nX * Pp * nKa * sizeof(double));
-        launch_quarter_coefs((const double *)ctx->Cq.p, ctx->nK, k0, nKa, (int)nX, (int)Pp, Cr1, Cr2, s);
-        ctx->launches++;
-    } else {
-        P.Dket = (double *)ctx->Dket.get(std::max<long long>(1, P.M * P.ncolD) * sizeof(double));
-        launch_gather_rows(P.Dbra, pc.d_pairs, P.ketsp, P.ketcol, pc.nsp, P.ncolD, P.Dket, s);
-    }
-    ctx->launches++;
+    order_kets(ctx, P, s);
     tm.mark();
 }
 
@@ -607,7 +616,7 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
 }
 
 // Integral values, E R E flops and first-half flops of a batch.
-void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, qdt_stats *st) {
+void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, long long width, qdt_stats *st) {
     if (!st) return;
     PairClass &pc = ctx->cls[P.cr.c];
     const int TMr = gemm_fp64_tile_m();
@@ -632,12 +641,12 @@ void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, qdt_stats 
     const long long Wrows = B.rows * P.mult;
     double f = 0;
     for (long long t = 0; t < (long long)B.kt.size(); ++t) f += (double)std::min<long long>(TMr, Wrows - t * TMr) * B.kt[t];
-    const double ncols = (double)(P.ls ? (P.cr.gauge ? P.N4 : 0) : P.N4);
+    const double ncols = (double)(P.ls ? (P.cr.gauge ? width : 0) : width);
     st->flops_half1 += 2.0 * f * ncols;
     if (P.ls && P.cr.gaunt) {
         double fg = 0;
         for (int k = B.b0; k < B.b1; ++k) fg += (double)pc.h_pairs[pc.bra_order[k]].nfp * P.Krow[pc.bra_order[k]];
-        st->flops_half1 += 2.0 * fg * 3 * P.N4;
+        st->flops_half1 += 2.0 * fg * 3 * width;
     }
 }
 
@@ -687,24 +696,34 @@ void half1_rows(qdt_ctx *ctx, int precision, const double *W, long long ldw, con
     }
 }
 
-// First half of a batch: V rows = W D_ket (launches only).
-void batch_half1(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, cudaStream_t s) {
-    const long long N4 = P.N4;
+// First half of a batch: V rows = W D_ket over the density columns [c0, c1)
+// of each column group (launches only; the MO-driven route passes one MO
+// block, the others all columns).
+void batch_half1(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, long long c0, long long c1,
+                 cudaStream_t s) {
+    const long long N4 = P.N4, w = c1 - c0;
     if (!P.ls) {
-        half1_rows(ctx, P.precision, B.W, B.ldw, P.Dket, N4, P.Vc + B.row0 * N4, N4, B.rows, N4, B.d_kt, B.kt, s);
+        half1_rows(ctx, P.precision, B.W, B.ldw, P.Dket + c0, N4, P.Vc + B.row0 * N4 + c0, N4, B.rows, w, B.d_kt,
+                   B.kt, s);
         return;
     }
     if (P.cr.gauge) {
         // gauge: rows (ab, I), K (cd, J): D_ket viewed as [(cd, J)][4 nRS]
-        half1_rows(ctx, P.precision, B.W, B.ldw, P.Dket, N4, P.Vg + B.row0 * 3 * N4, N4, B.rows * 3, N4, B.d_kt,
-                   B.kt, s);
+        half1_rows(ctx, P.precision, B.W, B.ldw, P.Dket + c0, N4, P.Vg + B.row0 * 3 * N4 + c0, N4, B.rows * 3, w,
+                   B.d_kt, B.kt, s);
     }
     if (P.cr.gaunt) {
-        // Gaunt: Coulomb integrals over L-S pairs, N = 12 nRS
+        // Gaunt: Coulomb integrals over L-S pairs, columns (J, RS, part)
         const double *Wg = P.cr.gauge ? B.Wc : B.W;
         const long long ldg = P.cr.gauge ? B.ldwc : B.ldw;
-        half1_rows(ctx, P.precision, Wg, ldg, P.Dket, 3 * N4, P.Vc + B.row0 * 3 * N4, 3 * N4, B.rows, 3 * N4,
-                   B.d_kg, B.kg, s);
+        if (w == N4) {
+            half1_rows(ctx, P.precision, Wg, ldg, P.Dket, 3 * N4, P.Vc + B.row0 * 3 * N4, 3 * N4, B.rows, 3 * N4,
+                       B.d_kg, B.kg, s);
+        } else {
+            for (int J = 0; J < 3; ++J)
+                half1_rows(ctx, P.precision, Wg, ldg, P.Dket + J * N4 + c0, 3 * N4,
+                           P.Vc + B.row0 * 3 * N4 + J * N4 + c0, 3 * N4, B.rows, w, B.d_kg, B.kg, s);
+        }
     }
 }
 
@@ -811,18 +830,13 @@ void half2_stats(const Half2 &H, qdt_stats *st) {
     for (const Half2::Job &j : H.jobs) st->flops_half2 += 2.0 * (double)j.K * (H.NO * (H.NO + 1) / 2.0);
 }
 
-void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, int precision,
-               double *out_coul, double *out_gaunt, double *out_gauge, qdt_stats *st, Timer &tm,
-               double acc_ms[6]) {
-    PairClass &pc = ctx->cls[cr.c];
+// Step 4 for the current ket order: batches of bra rows, integral rows then
+// the first half over the density columns [c0, c1).
+void run_batches(qdt_ctx *ctx, ClassPlan &P, long long c0, long long c1, qdt_stats *st, Timer &tm,
+                 double &ms_eri, double &ms_h1) {
+    PairClass &pc = ctx->cls[P.cr.c];
     cudaStream_t s = ctx->stream;
-    ClassPlan P;
-    const int t0 = tm.n;
-    class_issue(ctx, cr, k0, nKa, tau, precision, P, tm);
-    class_finish(ctx, P, st);
-    // 4. batches of bra rows: integral rows, then the first half
     int b0 = 0;
-    double ms_eri = 0, ms_h1 = 0;
     while (b0 < pc.nsp) {
         RowBatch B;
         batch_prepare(ctx, P, b0, B);
@@ -839,18 +853,50 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
         launch_eri(d_prm, d_tk, (int)tk.size(), (int *)ctx->next.get(sizeof(int)), shape, B.prm.gauge != 0, df, how,
                    s);
         ctx->launches += 2 + (B.Wc ? 1 : 0);
-        batch_stats(ctx, P, B, st);
+        batch_stats(ctx, P, B, c1 - c0, st);
         int th = tm.n; tm.mark();
         if (P.quarter)
             quarter_half1(ctx, P, B, st, s);
         else
-            batch_half1(ctx, P, B, s);
+            batch_half1(ctx, P, B, c0, c1, s);
         int tend = tm.n; tm.mark();
         QDT_CUDA_TRY(cudaStreamSynchronize(s));
         ms_eri += tm.ms(te, th);
         ms_h1 += tm.ms(th, tend);
         tm.n = te;   // reuse the batch's events
         b0 = B.b1;
+    }
+}
+
+void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, int precision,
+               double *out_coul, double *out_gaunt, double *out_gauge, qdt_stats *st, Timer &tm,
+               double acc_ms[6]) {
+    PairClass &pc = ctx->cls[cr.c];
+    cudaStream_t s = ctx->stream;
+    ClassPlan P;
+    const int t0 = tm.n;
+    class_issue(ctx, cr, k0, nKa, tau, precision, P, tm);
+    double ms_eri = 0, ms_h1 = 0;
+    const int parts = P.ku ? 2 : 4;
+    const int nb = ctx->route == QDT_ROUTE_MO ? std::max(1, ctx->mo_block) : nKa;
+    if (nb >= nKa) {
+        class_finish(ctx, P, st);
+        run_batches(ctx, P, 0, P.N4, st, tm, ms_eri, ms_h1);
+    } else {
+        // MO-driven: the outer MO index r runs in blocks; each block of density
+        // columns (r, s >= r) is screened on its own Dmax and recomputes every
+        // integral it keeps
+        auto col = [&](int r) { return (long long)parts * (r * (long long)nKa - (long long)r * (r - 1) / 2); };
+        for (int r0 = 0; r0 < nKa; r0 += nb) {
+            const int r1 = std::min(nKa, r0 + nb);
+            const long long c0 = col(r0), c1 = r1 < nKa ? col(r1) : P.N4;
+            launch_block_dmax(pc.d_pairs, pc.nsp, P.Dbra, P.ncolD, P.ls ? 3 : 1, P.N4, c0, c1, P.Dmax, s);
+            ctx->launches++;
+            order_kets(ctx, P, s);
+            split_invalidate(ctx->split);
+            class_finish(ctx, P, st);
+            run_batches(ctx, P, c0, c1, st, tm, ms_eri, ms_h1);
+        }
     }
     acc_ms[2] += ms_eri;
     acc_ms[3] += ms_h1;
@@ -964,7 +1010,7 @@ void issue_round(qdt_ctx *owner, const std::vector<BatchReq *> &fz, const EriPar
     for (BatchReq *r : fz) {
         cudaStream_t cs = r->c->stream;
         if (cs != s0) QDT_CUDA_TRY(cudaStreamWaitEvent(cs, owner->fork_ev, 0));
-        batch_half1(r->c, r->P, r->B, cs);
+        batch_half1(r->c, r->P, r->B, 0, r->P.N4, cs);
         for (const Half2::Job &j : r->H.jobs) {
             half2_job(r->c, r->P, r->H, j, cs);
             half2_pack(r->c, r->P, r->H, j, cs);
@@ -1018,7 +1064,7 @@ void batch_round(qdt_ctx *owner, std::vector<BatchReq> &R, int round, unsigned f
             r.fused = r.B.b1 == r.c->cls[r.P.cr.c].nsp;     // the whole class in one row batch
             if (r.fused) {
                 half2_prepare(r.c, r.P, r.o[0], r.o[1], r.o[2], r.H);
-                batch_stats(r.c, r.P, r.B, &r.st);
+                batch_stats(r.c, r.P, r.B, r.P.N4, &r.st);
                 half2_stats(r.H, &r.st);
                 fz.push_back(&r);
             } else {
@@ -1357,13 +1403,18 @@ int qdt_set_rkb_coefficients(qdt_ctx *c, int n, const double *CL, const double *
     return set_coefficients(c, n, CL, CS, spinors != 0, c_light, "qdt_set_rkb_coefficients");
 }
 
-int qdt_set_route(qdt_ctx *c, int route) {
+int qdt_set_route(qdt_ctx *c, int route, int mo_block) {
     if (!c) return QDT_ERR_ARG;
-    if (route != QDT_ROUTE_DENSITY && route != QDT_ROUTE_QUARTER) {
-        c->err = "qdt_set_route: route must be QDT_ROUTE_DENSITY or QDT_ROUTE_QUARTER";
+    if (route != QDT_ROUTE_DENSITY && route != QDT_ROUTE_QUARTER && route != QDT_ROUTE_MO) {
+        c->err = "qdt_set_route: route must be QDT_ROUTE_DENSITY, QDT_ROUTE_QUARTER or QDT_ROUTE_MO";
+        return QDT_ERR_ARG;
+    }
+    if (route == QDT_ROUTE_MO && mo_block <= 0) {
+        c->err = "qdt_set_route: the MO-driven route needs a positive block size";
         return QDT_ERR_ARG;
     }
     c->route = route;
+    c->mo_block = route == QDT_ROUTE_MO ? mo_block : 0;
     c->err.clear();
     return QDT_OK;
 }
@@ -1446,7 +1497,7 @@ int qdt_transform_batch(qdt_batch_item *items, int n, unsigned flags) {
             cudaGetLastError();
             if (!r.c->has_basis || !r.c->has_coef) throw Error{QDT_ERR_STATE, "qdt_transform_batch: basis or coefficients not set"};
             if (r.c->route != QDT_ROUTE_DENSITY)
-                throw Error{QDT_ERR_UNIMPLEMENTED, "qdt_transform_batch: the quarter-transform route runs through qdt_transform only"};
+                throw Error{QDT_ERR_UNIMPLEMENTED, "qdt_transform_batch: the quarter and MO-driven routes run through qdt_transform only"};
             const qdt_batch_item &it = items[i];
             arg_check(it.blocks != 0 && (it.blocks & ~7u) == 0, "qdt_transform_batch: blocks must be a non-empty subset of COULOMB|GAUNT|GAUGE");
             arg_check(it.k_begin >= 0 && it.k_end > it.k_begin && it.k_end <= r.c->nK, "qdt_transform_batch: bad Kramers range");

@@ -208,6 +208,9 @@ void launch_zero(double *p, long long n, cudaStream_t s);
 // Eq. RKB: c^S[nL][n][4] -> derivative-function coefficients [3 nL][n][4].
 void launch_rkb_map(const double *in, long long nL, long long n, double c_light, double *out,
                     cudaStream_t s);
+// Dmax over the columns [c0, c1) of each of nJ column groups (MO-driven route).
+void launch_block_dmax(const PairDev *pairs, int nsp, const double *D, long long ld, int nJ, long long N4,
+                       long long c0, long long c1, double *Dmax, cudaStream_t s);
 // Quarter-transform comparator of the Coulomb first half (quarter_kernels.cu).
 void launch_ket_functions(const PairDev *pairs, const ShellDev *shells, const int *ket_sp,
                           const long long *ket_col, int nsp, int2 *cols, cudaStream_t s);

@@ -94,7 +94,7 @@ def load(build_if_missing=True):
     L.qdt_set_coefficients.argtypes = [vp, ctypes.c_int, vp, vp]
     L.qdt_set_spinor_coefficients.argtypes = [vp, ctypes.c_int, vp, vp]
     L.qdt_set_rkb_coefficients.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_int]
-    L.qdt_set_route.argtypes = [vp, ctypes.c_int]
+    L.qdt_set_route.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.qdt_packed_size.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int]
     L.qdt_packed_size.restype = ctypes.c_size_t
     L.qdt_transform.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -204,10 +204,11 @@ class Context:
         self._check(self.L.qdt_set_rkb_coefficients(self.h, n, _ptr(CL), _ptr(CS), float(c_light),
                                                     1 if spinors else 0))
 
-    def set_route(self, route):
-        """'density' (default) or 'quarter' (two-quarter Coulomb first half)."""
-        code = {"density": 0, "quarter": 1}[route]
-        self._check(self.L.qdt_set_route(self.h, code))
+    def set_route(self, route, mo_block=0):
+        """'density' (default), 'quarter' (two-quarter Coulomb first half) or
+        'mo' (MO-driven, integrals recomputed per block of mo_block outer MOs)."""
+        code = {"density": 0, "quarter": 1, "mo": 2}[route]
+        self._check(self.L.qdt_set_route(self.h, code, int(mo_block)))
 
     def packed_size(self, blocks, k_begin, k_end):
         return int(self.L.qdt_packed_size(self.h, blocks_mask(blocks), int(k_begin), int(k_end)))

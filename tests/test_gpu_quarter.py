@@ -136,4 +136,5 @@ def test_route_leaves_gaunt_gauge_and_refuses_batches(torch_cuda):
     out = torch.zeros_like(oq)
     with pytest.raises(qdt.QdtError):
         qdt.transform_batch([(q, ["gaunt", "gauge"], 0, 2, p.tau, 0, out)])
-    assert q.L.qdt_set_route(q.h, 7) == -1
+    assert q.L.qdt_set_route(q.h, 7, 0) == -1
+    assert q.L.qdt_set_route(q.h, 2, 0) == -1
