@@ -313,7 +313,7 @@ __device__ __forceinline__ void ket_orders(int n0, int Ly, int tx, int ux, int v
 template <bool NEG>
 __device__ __forceinline__ void ket_orders_df(int n0, int Ly, int tx, int ux, int vx, const int *trip,
                                               const float2 *Rq, int nr, const float2 *ey, int nfpY,
-                                              const long long *eoff, int nk, float &ah, float &al) {
+                                              long long sE, int nk, float &ah, float &al) {
     for (int n = n0; n <= Ly; n += 2) {
         const int hb = n ? nherm(n - 1) : 0, he = nherm(n);
         for (int hp = hb; hp < he; ++hp) {
@@ -322,7 +322,13 @@ __device__ __forceinline__ void ket_orders_df(int n0, int Ly, int tx, int ux, in
             const int s = T0 + U0 + V0, w = U0 + V0;
             const int i0 = s * (s + 1) * (s + 2) / 6 + w * (w + 1) / 2 + V0;
             const float2 *e = ey + (size_t)hp * nfpY;
-            for (int kl = 0; kl < nk; ++kl) df_madd<NEG>(Rq[kl * nr + i0], __ldg(e + eoff[kl]), ah, al);
+            const float2 *rk = Rq + i0;
+#pragma unroll 4
+            for (int kl = 0; kl < nk; ++kl) {
+                df_madd<NEG>(*rk, __ldg(e), ah, al);
+                rk += nr;
+                e += sE;
+            }
         }
     }
 }
@@ -334,7 +340,7 @@ __device__ __forceinline__ void ket_orders_df(int n0, int Ly, int tx, int ux, in
 template <bool NEG>
 __device__ __forceinline__ void ket_orders_df2(int n0, int Ly, int tx, int ux, int vx, const int *trip,
                                                const float2 *Rq, int nr, const float2 *ey, int nfpY,
-                                               const long long *eoff, int nk, bool has1, float &ah0, float &al0,
+                                               long long sE, int nk, bool has1, float &ah0, float &al0,
                                                float &ah1, float &al1) {
     for (int n = n0; n <= Ly; n += 2) {
         const int hb = n ? nherm(n - 1) : 0, he = nherm(n);
@@ -344,16 +350,23 @@ __device__ __forceinline__ void ket_orders_df2(int n0, int Ly, int tx, int ux, i
             const int s = T0 + U0 + V0, w = U0 + V0;
             const int i0 = s * (s + 1) * (s + 2) / 6 + w * (w + 1) / 2 + V0;
             const float2 *e = ey + (size_t)hp * nfpY;
+            const float2 *rk = Rq + i0;
             if (has1) {
+#pragma unroll 2
                 for (int kl = 0; kl < nk; ++kl) {
-                    const float2 r = Rq[kl * nr + i0];
-                    const float2 *ek = e + eoff[kl];
-                    const float2 e0 = __ldg(ek), e1 = __ldg(ek + 1);
+                    const float2 r = *rk;
+                    const float2 e0 = __ldg(e), e1 = __ldg(e + 1);
                     df_madd<NEG>(r, e0, ah0, al0);
                     df_madd<NEG>(r, e1, ah1, al1);
+                    rk += nr;
+                    e += sE;
                 }
             } else {
-                for (int kl = 0; kl < nk; ++kl) df_madd<NEG>(Rq[kl * nr + i0], __ldg(e + eoff[kl]), ah0, al0);
+                for (int kl = 0; kl < nk; ++kl) {
+                    df_madd<NEG>(*rk, __ldg(e), ah0, al0);
+                    rk += nr;
+                    e += sE;
+                }
             }
         }
     }
@@ -375,6 +388,10 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
     const int hs = header_len(L, GAUGE), perq = quartet_len(L, GAUGE);
     const int xch = x1 - x0, ych = y1 - y0;
     const int nT = t_rows(Lx, GAUGE);                   // T rows per outer primitive pair
+    // the E matrices of a pair's primitive pairs are stored back to back,
+    // nherm(L) x nfp each: inner primitive kl starts kl sE past the first (the
+    // compensated-FP32 ket pass walks them by this stride)
+    const long long sE = (long long)Y.nfp * nherm(Ly);
     const int tsz = nT * ych;                           // T doubles per outer primitive pair
 
     // primitive grouping: nij outer pairs x nkl inner pairs at a time
@@ -477,15 +494,15 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
                     const float2 *R2 = reinterpret_cast<const float2 *>(r12 ? RR + (size_t)ijl * nk * nrR
                                                                             : RC + (size_t)ijl * nk * nrC);
                     const int nr = r12 ? nrR : nrC;
-                    const float2 *ey = E2 + (y0 + yy);
+                    const float2 *ey = E2 + b.eY[k0] + (y0 + yy);
                     if constexpr (GAUGE) {
-                        ket_orders_df2<false>(0, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, has1, ah0,
+                        ket_orders_df2<false>(0, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, sE, nk, has1, ah0,
                                               al0, ah1, al1);
-                        ket_orders_df2<true>(1, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, has1, ah0,
+                        ket_orders_df2<true>(1, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, sE, nk, has1, ah0,
                                              al0, ah1, al1);
                     } else {
-                        ket_orders_df<false>(0, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, ah0, al0);
-                        ket_orders_df<true>(1, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, b.eY + k0, nk, ah0, al0);
+                        ket_orders_df<false>(0, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, sE, nk, ah0, al0);
+                        ket_orders_df<true>(1, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, sE, nk, ah0, al0);
                     }
                     T2[0] = make_float2(ah0, al0);
                     if (has1) T2[1] = make_float2(ah1, al1);
@@ -522,6 +539,7 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
             for (int c = 0; c < NC; ++c) { s[c] = 0.0; sh[c] = 0.f; sl[c] = 0.f; }
             for (int ijl = 0; ijl < nij; ++ijl) {
                 const size_t off = (size_t)ijl * tsz + yy;
+#pragma unroll 4
                 for (int h = 0; h < nhx; ++h) {
                     int g[6] = {0, 0, 0, 0, 0, 0};               // r12 rows, offset by nhx - 4
                     if (GAUGE) {
