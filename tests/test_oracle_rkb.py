@@ -73,3 +73,38 @@ def test_rkb_spinor_form_matches_quaternion_form(oracle):
     z = lambda f: np.stack([f[..., 0] + 1j * f[..., 1], f[..., 2] + 1j * f[..., 3]], axis=1)
     assert np.abs(z(s_even) - qimg[:, :, 0::2]).max() <= 1e-16
     assert np.abs(z(s_odd) - qimg[:, :, 1::2]).max() <= 1e-16
+
+
+def test_rkb_reproduces_the_quaternion_first_half(oracle):
+    """Eq. firsthalf, small-component ket term, for one spinor pair (r, t): with
+    D_s = sum_tau c*_k c_l and D_M = c*_k sigma_M c_l (quaternion density of the
+    RKB coefficients c^S, Eq. QuaternionScatter read with sigma_M between the
+    spinors), V_s(mu nu) = (1/2c^2) sum [D_s (mu nu|grad k . grad l) +
+    i sum_M D_M (mu nu|(grad k x grad l)_M)].  The same quantity through the
+    derivative-function expansion: the bra spin trace (V_aa + V_bb) of
+    sum_cd (mu nu|cd) D_cd with the expanded coefficients."""
+    p = synth.rkb_chain_problem(2, 2, seed=614, shells=(0, 1), nprim=1, kramers=False)
+    ob = oracle.OracleBasis(p.basis)
+    nL = ob.nL
+    T = oracle._expand_full(ob, 0, ob.pair_matrix(0, 0))            # (ab|cd) over F = L, S
+    S = lambda k, K: nL + 3 * k + K
+    cS = np.stack([p.CS[..., 0] + 1j * p.CS[..., 1], p.CS[..., 2] + 1j * p.CS[..., 3]], axis=1)   # [nL, 2, n]
+    r, t = 0, 1
+    # route A: expansion over the derivative functions, then the plain density sum
+    Ct4 = oracle.rkb_to_derivative(p.CS, C_LIGHT, spinors=True)
+    Ct = np.stack([Ct4[..., 0] + 1j * Ct4[..., 1], Ct4[..., 2] + 1j * Ct4[..., 3]], axis=1)     # [3 nL, 2, n]
+    Dd = np.einsum('ct,dt->cd', np.conj(Ct[:, :, r]), Ct[:, :, t])
+    VA = 2.0 * np.einsum('mncd,cd->mn', T[:nL, :nL, nL:, nL:], Dd)
+    # route B: the quaternion formula from scalar integrals of dot and cross products
+    Ds = np.einsum('kt,lt->kl', np.conj(cS[:, :, r]), cS[:, :, t])
+    DM = np.einsum('kt,Mtu,lu->Mkl', np.conj(cS[:, :, r]), oracle.SIGMA, cS[:, :, t])
+    idx = np.array([[S(k, K) for K in range(3)] for k in range(nL)])                      # [nL, 3]
+    Tb = T[:nL, :nL][:, :, idx[:, :, None, None], idx[None, None, :, :]]                  # [m, n, k, K, l, L]
+    dot = np.einsum('mnkKlK->mnkl', Tb)
+    eps = np.zeros((3, 3, 3))
+    for (a, b, c) in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        eps[a, b, c], eps[b, a, c] = 1.0, -1.0
+    cross = np.einsum('KLM,mnkKlL->Mmnkl', eps, Tb)
+    VB = (np.einsum('kl,mnkl->mn', Ds, dot) + 1j * np.einsum('Mkl,Mmnkl->mn', DM, cross)) / (2.0 * C_LIGHT ** 2)
+    assert np.abs(VB).max() > 0 and np.abs(np.einsum('Mkl,Mmnkl->mn', DM, cross)).max() > 1e-6 * np.abs(VB).max() * C_LIGHT ** 2
+    assert np.abs(VA - VB).max() <= 1e-13 * np.abs(VB).max()
