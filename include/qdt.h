@@ -162,7 +162,8 @@ int qdt_set_spinor_coefficients(qdt_ctx *ctx, int n_spinors, const double *CL, c
  * for the expanded coefficients.  spinors = 0: quaternion columns (as
  * qdt_set_coefficients, n = nK Kramers pairs); spinors != 0: unrestricted
  * spinors (as qdt_set_spinor_coefficients).  c_light > 0 (atomic units:
- * 137.035999084).  QDT_ERR_ARG on bad sizes or c; host or device, copied.
+ * 137.035999084 by CODATA 2018; the paper's runs use 137.035999074).  QDT_ERR_ARG
+ * on bad sizes or c; host or device, copied.
  */
 int qdt_set_rkb_coefficients(qdt_ctx *ctx, int n, const double *CL, const double *CS, double c_light,
                              int spinors);

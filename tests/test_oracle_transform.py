@@ -297,3 +297,23 @@ def test_screened_fraction_grows_with_chain_and_ssss_most(oracle):
         fr_ssss.append(1 - m[ns:, ns:].mean())
     assert all(b > a for a, b in zip(fr, fr[1:]))
     assert all(s > f for s, f in zip(fr_ssss, fr))
+
+
+def test_noise_floor_of_a_second_summation_order(oracle):
+    """The oracle's fixed order (D^T (G D)) against a second order ((D^T G) D):
+    the FP64 noise floor sits far below the 1e-12 parity bar."""
+    p = synth.chain_problem(4, 3, seed=655, shells=(0, 1), nprim=2, blocks=BLOCKS, tau=0.0)
+    tr = oracle.Transform(p)
+    for b in BLOCKS:
+        O1 = tr.packed_full(b, screened=False)
+        G, D = tr.G(b), tr.density(b)
+        if b == "coulomb":
+            O2 = (D.T @ G) @ D
+        elif b == "gaunt":
+            O2 = sum((D[:, J, :].T @ G) @ D[:, J, :] for J in range(3))
+        else:
+            O2 = 0
+            for ij, (I, J) in enumerate(oracle.IJ6):
+                t = (D[:, I, :].T @ G[ij]) @ D[:, J, :]
+                O2 = O2 + (t if I == J else t + t.T)
+        assert np.abs(O1 - O2).max() <= 1e-14 * max(1.0, np.abs(O1).max())
