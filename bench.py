@@ -140,6 +140,23 @@ def as_unrestricted(problem):
     return synth.Problem(problem.name + "-ku", problem.basis, CL, CS, problem.blocks, problem.tau, kramers=False)
 
 
+def max_over_ranks(ms, world, device):
+    """The step time of the job: the slowest rank's (every rank calls this)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_mo, world, ms):
+    """Whole-job throughput: every rank transforms its own replica of the
+    workload (weak scaling), all within the slowest rank's step time."""
+    return n_mo * world / (ms / 1e3)
+
+
 def run_reference(args, problem, blocks, rank):
     """CPU oracle on a bounded sample of the workload (rank 0 only)."""
     if rank != 0:
@@ -402,12 +419,9 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, "cuda")
     n_mo = mo_count(problem, len(blocks))
-    value = n_mo * world / (ms / 1e3)
+    value = job_value(n_mo, world, ms)
 
     # end to end through the public API with host buffers (pinned)
     e2e = None
