@@ -189,6 +189,16 @@ int qdt_set_rkb_coefficients(qdt_ctx *ctx, int n, const double *CL, const double
  */
 int qdt_set_route(qdt_ctx *ctx, int route, int mo_block);
 
+/*
+ * Failure-detection self-check: runs the bounded wait that guards every
+ * tensor-core pipeline wait on an mbarrier that nothing arrives at, with the
+ * given limit (0 < limit_s <= 2).  Returns QDT_ERR_TIMEOUT when the wait gave
+ * up and reported it through the device status word (the expected outcome;
+ * the context stays usable), QDT_ERR_CUDA if it did not, QDT_ERR_ARG on a bad
+ * limit.
+ */
+int qdt_check_bounded_wait(qdt_ctx *ctx, double limit_s);
+
 /* Bytes of the packed output of qdt_transform for these blocks and range
    (for the input kind last set: quaternion or Kramers-unrestricted). */
 size_t qdt_packed_size(const qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end);

@@ -222,8 +222,8 @@ __device__ inline void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
 
-// bounded wait for phase `parity` of an mbarrier; false on timeout
-__device__ inline bool mbar_wait(uint64_t *b, uint32_t parity) {
+// bounded wait for phase `parity` of an mbarrier; false after limit_ns
+__device__ inline bool mbar_wait_for(uint64_t *b, uint32_t parity, long long limit_ns) {
     uint32_t a = su32(b);
     unsigned long long t0 = gtimer();
     while (true) {
@@ -234,8 +234,22 @@ __device__ inline bool mbar_wait(uint64_t *b, uint32_t parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
-        if ((long long)(gtimer() - t0) > kWaitNs) return false;
+        if ((long long)(gtimer() - t0) > limit_ns) return false;
     }
+}
+
+__device__ inline bool mbar_wait(uint64_t *b, uint32_t parity) { return mbar_wait_for(b, parity, kWaitNs); }
+
+// Self-check of the bounded wait: one thread waits on an mbarrier that
+// nothing arrives at; the wait must give up after limit_ns and record it.
+__global__ void wait_probe_kernel(long long limit_ns, int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_for(&bar, 0, limit_ns)) atomicExch(status, 1);
 }
 
 __device__ inline void tma_load(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
@@ -565,6 +579,18 @@ static void run_umma(SplitWorkspace &w, void *Asl, long long Mpad, long long Kpa
     QDT_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     QDT_CUDA_TRY(cudaStreamSynchronize(s));
     if (h) throw Error{QDT_ERR_TIMEOUT, "split contraction: a bounded tensor-core wait gave up"};
+}
+
+bool split_wait_probe(SplitWorkspace &w, double limit_s, cudaStream_t s) {
+    int *status = (int *)ws_get(w, WS_STAT, 256);
+    QDT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    wait_probe_kernel<<<1, 32, 0, s>>>((long long)(limit_s * 1e9), status);
+    QDT_CHECK_KERNEL("wait_probe_kernel");
+    int h = 0;
+    QDT_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    QDT_CUDA_TRY(cudaStreamSynchronize(s));
+    QDT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    return h != 0;
 }
 
 // Extents of the 128-row tensor-core tiles: the maximum over the 64-row tiles

@@ -1409,6 +1409,24 @@ int qdt_set_rkb_coefficients(qdt_ctx *c, int n, const double *CL, const double *
     return set_coefficients(c, n, CL, CS, spinors != 0, c_light, "qdt_set_rkb_coefficients");
 }
 
+int qdt_check_bounded_wait(qdt_ctx *c, double limit_s) {
+    if (!c) return QDT_ERR_ARG;
+    if (!(limit_s > 0.0 && limit_s <= 2.0)) {
+        c->err = "qdt_check_bounded_wait: the limit must be in (0, 2] seconds";
+        return QDT_ERR_ARG;
+    }
+    try {
+        QDT_CUDA_TRY(cudaSetDevice(c->device));
+        if (split_wait_probe(c->split, limit_s, c->stream)) {
+            c->err = "qdt_check_bounded_wait: the wait gave up after its limit, as it should";
+            return QDT_ERR_TIMEOUT;
+        }
+        throw Error{QDT_ERR_CUDA, "qdt_check_bounded_wait: a wait on an mbarrier nothing arrives at completed"};
+    } catch (const Error &e) {
+        return fail(c, e);
+    }
+}
+
 int qdt_set_route(qdt_ctx *c, int route, int mo_block) {
     if (!c) return QDT_ERR_ARG;
     if (route != QDT_ROUTE_DENSITY && route != QDT_ROUTE_QUARTER && route != QDT_ROUTE_MO) {

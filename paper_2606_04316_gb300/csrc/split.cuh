@@ -38,6 +38,9 @@ void split_invalidate(SplitWorkspace &w);
 void split_begin_deferred(SplitWorkspace &w, cudaStream_t s);
 void split_clear_status(SplitWorkspace &w, cudaStream_t s);
 void split_end_deferred(SplitWorkspace &w, cudaStream_t s);
+// Runs one bounded wait on an mbarrier that nothing arrives at, with the
+// given limit; true when the wait gave up and reported it (the expected case).
+bool split_wait_probe(SplitWorkspace &w, double limit_s, cudaStream_t s);
 
 // C[M x N] = A[M x K_t] B[K_t x N], K_t from the per-64-row-tile extents.
 void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B,

@@ -23,7 +23,8 @@ EXPORTS = ["qdt_create", "qdt_destroy", "qdt_set_basis", "qdt_num_functions", "q
            "qdt_packed_size", "qdt_transform", "qdt_unpack", "qdt_last_error", "qdt_version",
            "qdt_footprint", "qdt_server_create", "qdt_server_destroy", "qdt_submit", "qdt_poll", "qdt_wait",
            "qdt_second_half_noalloc", "qdt_transform_batch", "qdt_graph_counts",
-           "qdt_set_spinor_coefficients", "qdt_set_rkb_coefficients", "qdt_set_route"]
+           "qdt_set_spinor_coefficients", "qdt_set_rkb_coefficients", "qdt_set_route",
+           "qdt_check_bounded_wait"]
 BATCH_GRAPH = 1
 
 
@@ -95,6 +96,7 @@ def load(build_if_missing=True):
     L.qdt_set_spinor_coefficients.argtypes = [vp, ctypes.c_int, vp, vp]
     L.qdt_set_rkb_coefficients.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_int]
     L.qdt_set_route.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.qdt_check_bounded_wait.argtypes = [vp, ctypes.c_double]
     L.qdt_packed_size.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int]
     L.qdt_packed_size.restype = ctypes.c_size_t
     L.qdt_transform.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -209,6 +211,10 @@ class Context:
         'mo' (MO-driven, integrals recomputed per block of mo_block outer MOs)."""
         code = {"density": 0, "quarter": 1, "mo": 2}[route]
         self._check(self.L.qdt_set_route(self.h, code, int(mo_block)))
+
+    def check_bounded_wait(self, limit_s=0.05):
+        """Status code of the bounded-wait self-check (QDT_ERR_TIMEOUT = -6 expected)."""
+        return int(self.L.qdt_check_bounded_wait(self.h, float(limit_s)))
 
     def packed_size(self, blocks, k_begin, k_end):
         return int(self.L.qdt_packed_size(self.h, blocks_mask(blocks), int(k_begin), int(k_end)))
