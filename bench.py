@@ -468,10 +468,15 @@ def main():
     if dom == "ms_eri":
         achieved = st["flops_eri"] / (avg[dom] / 1e3) / 1e12
         if prec == qdt.SPLIT:
-            # split form: the contractions run in compensated FP32 pairs on the FP32 pipe
-            peak = SMS * FP32_PER_CLK_SM * mhz * 1e6 / DF_OPS_PER_MADD * 2 / 1e12
-            note = ("FP32 pipe: %d SMs x %d lanes x %.0f MHz / %d FP32 ops per compensated multiply-add x 2 "
-                    "flops (FP64-equivalent)" % (SMS, FP32_PER_CLK_SM, mhz, DF_OPS_PER_MADD))
+            # split form: the contractions run in compensated FP32 pairs (12 FP32 operations per
+            # multiply-add) or, for the quartets within the FP32 error budget, in plain FP32 (one
+            # FMA); the bound weighs the two by their share of the flops
+            f32 = st.get("flops_eri_f32", 0.0) / st["flops_eri"] if st["flops_eri"] else 0.0
+            ops = DF_OPS_PER_MADD * (1.0 - f32) + 1.0 * f32
+            peak = SMS * FP32_PER_CLK_SM * mhz * 1e6 / ops * 2 / 1e12
+            note = ("FP32 pipe: %d SMs x %d lanes x %.0f MHz / %.2f FP32 ops per multiply-add (%d for "
+                    "compensated pairs, 1 for the %.1f %% of flops in plain FP32) x 2 flops (FP64-equivalent)"
+                    % (SMS, FP32_PER_CLK_SM, mhz, ops, DF_OPS_PER_MADD, 100.0 * f32))
         else:
             peak, note = fp64_peak, fp64_note
         roof = {"kernel": "eri_rows_kernel", "bound": "alu", "achieved": achieved,

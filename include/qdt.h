@@ -106,6 +106,10 @@ typedef struct {
     int precision;              /* QDT_FP64 or QDT_SPLIT                              */
     int slices;                 /* BF16 slices per operand in the split form          */
     double flops_eri;           /* FP64 flops of the integral contractions (E R E)    */
+    long long quartets_f32[3];  /* split form: kept quartets whose integrals ran in   */
+                                /* plain FP32 under the error budget                  */
+    double f32_bound;           /* bound on their summed effect on any output element */
+    double flops_eri_f32;       /* the part of flops_eri that ran in plain FP32       */
 } qdt_stats;
 
 /*
@@ -188,6 +192,17 @@ int qdt_set_rkb_coefficients(qdt_ctx *ctx, int n, const double *CL, const double
  * an unknown route or a bad block size.
  */
 int qdt_set_route(qdt_ctx *ctx, int route, int mo_block);
+
+/*
+ * Check of the split form's FP32 error model: for each requested class
+ * (ratio[0] Coulomb, ratio[1] the L-S class of Gaunt/gauge) the kept
+ * integral rows are computed twice, in compensated FP32 pairs and in plain
+ * FP32, and ratio[c] = max |difference| / (Q_A Q_C) over all entries (Q the
+ * Schwarz factors of the bra and ket shell pairs).  The split form lets a
+ * quartet run in plain FP32 assuming this ratio stays below 1024 x 2^-24.
+ * Small inputs only: each class must fit one row batch (QDT_ERR_ARG).
+ */
+int qdt_f32_error_ratio(qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end, double tau, double ratio[2]);
 
 /*
  * Failure-detection self-check: runs the bounded wait that guards every

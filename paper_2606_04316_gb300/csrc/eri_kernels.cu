@@ -32,6 +32,8 @@
 // operations, which issue 64 times faster than FP64 on this part.
 #include <math.h>
 
+#include <algorithm>
+
 #include "qdt_internal.cuh"
 
 namespace qdt {
@@ -151,9 +153,13 @@ __device__ __forceinline__ float2 df_rec(float2 x, float2 a, float cf, float2 c)
     return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, t)));
 }
 
-__global__ void split_pairs_kernel(const double *E, long long n, float2 *E2) {
+__global__ void split_pairs_kernel(const double *E, long long n, float2 *E2, float *E1) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) E2[i] = df_split(E[i]);
+    if (i < n) {
+        const float2 v = df_split(E[i]);
+        E2[i] = v;
+        E1[i] = v.x;
+    }
 }
 
 // Doubles of one primitive quartet's header: X_PQ (3), R^n_000 of the Coulomb
@@ -333,6 +339,33 @@ __device__ __forceinline__ void ket_orders_df(int n0, int Ly, int tx, int ux, in
     }
 }
 
+// The same in plain FP32 (the high parts of R and E): quartets whose error
+// bound the host has admitted to the FP32 budget.
+template <bool NEG>
+__device__ __forceinline__ void ket_orders_f32(int n0, int Ly, int tx, int ux, int vx, const int *trip,
+                                               const float2 *Rq, int nr, const float *ey, int nfpY,
+                                               long long sE, int nk, float &acc) {
+    for (int n = n0; n <= Ly; n += 2) {
+        const int hb = n ? nherm(n - 1) : 0, he = nherm(n);
+        for (int hp = hb; hp < he; ++hp) {
+            const int tq = trip[hp];
+            const int T0 = tx + (tq & 255), U0 = ux + ((tq >> 8) & 255), V0 = vx + (tq >> 16);
+            const int s = T0 + U0 + V0, w = U0 + V0;
+            const int i0 = s * (s + 1) * (s + 2) / 6 + w * (w + 1) / 2 + V0;
+            const float *e = ey + (size_t)hp * nfpY;
+            const float *rk = reinterpret_cast<const float *>(Rq + i0);
+            float a = acc;
+#pragma unroll 4
+            for (int kl = 0; kl < nk; ++kl) {
+                a = NEG ? fmaf(-*rk, __ldg(e), a) : fmaf(*rk, __ldg(e), a);
+                rk += 2 * nr;
+                e += sE;
+            }
+            acc = a;
+        }
+    }
+}
+
 // The same for two adjacent inner function pairs y, y + 1 at once (the second
 // when has1): R and the primitive-pair offsets are loaded once for both, and
 // the two accumulator chains are independent (gauge kernel, whose larger
@@ -375,8 +408,9 @@ __device__ __forceinline__ void ket_orders_df2(int n0, int Ly, int tx, int ux, i
 // One chunk (x in [x0,x1) of X, y in [y0,y1) of Y) of the block (X|Y);
 // results in b.G[comp][x][y].  NC = 1 (Coulomb) or 7 (gauge: [0] Coulomb,
 // [1..6] (xy|d_I d_J r|zw) for IJ = xx,xy,xz,yy,yz,zz).
-template <bool GAUGE, bool DF>
-__device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2 *E2, const double *boys,
+template <bool GAUGE, bool DF, bool F32 = false>
+__device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2 *E2, const float *E1,
+                            const double *boys,
                             const PairDev &X, const PairDev &Y, int x0, int x1, int y0, int y1, const Plan &pl,
                             BlockSmem &b) {
     constexpr int NC = GAUGE ? 7 : 1;
@@ -451,7 +485,17 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
                         src = RR + ((size_t)prv * nq + q) * nrR;
                         i0h = 4 + L + m;
                     }
-                    if constexpr (DF) {
+                    if constexpr (DF && F32) {
+                        const float2 *hd2 = reinterpret_cast<const float2 *>(hd);
+                        const float2 *src2 = reinterpret_cast<const float2 *>(src);
+                        float r = hd2[i0h].x;
+                        if (h > 0) {
+                            const int sw = b.src[h];
+                            r = fmaf(hd2[sw & 3].x, src2[(sw >> 2) & 1023].x,
+                                     (float)((sw >> 22) & 15) * src2[(sw >> 12) & 1023].x);
+                        }
+                        reinterpret_cast<float2 *>(dst)[h] = make_float2(r, 0.f);
+                    } else if constexpr (DF) {
                         const float2 *hd2 = reinterpret_cast<const float2 *>(hd);
                         const float2 *src2 = reinterpret_cast<const float2 *>(src);
                         float2 r = hd2[i0h];
@@ -474,7 +518,26 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
             }
             // T[ij][h][y] += sum_kl sum_h' (-1)^{|h'|} R[h+h'] E^{kl}[h'][y]: rows h < nhx
             // with the Coulomb tensor, then (gauge) rows g = 4.. with the r12 tensor
-            if constexpr (DF) {
+            if constexpr (DF && F32) {
+                for (int it = tid; it < nij * nT * ych; it += nt) {
+                    const int ijl = it / (nT * ych);
+                    const int rem = it - ijl * nT * ych;
+                    const int hh = rem / ych, yy = rem - hh * ych;
+                    const bool r12 = GAUGE && hh >= nhx;
+                    const int h = r12 ? hh - nhx + 4 : hh;
+                    const int tr = b.trip[h];
+                    const int tx = tr & 255, ux = (tr >> 8) & 255, vx = tr >> 16;
+                    float2 *T2 = reinterpret_cast<float2 *>(T + (size_t)ijl * tsz + (size_t)hh * ych + yy);
+                    float acc = T2[0].x;
+                    const float2 *R2 = reinterpret_cast<const float2 *>(r12 ? RR + (size_t)ijl * nk * nrR
+                                                                            : RC + (size_t)ijl * nk * nrC);
+                    const int nr = r12 ? nrR : nrC;
+                    const float *ey = E1 + b.eY[k0] + (y0 + yy);
+                    ket_orders_f32<false>(0, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, sE, nk, acc);
+                    ket_orders_f32<true>(1, Ly, tx, ux, vx, b.trip, R2, nr, ey, Y.nfp, sE, nk, acc);
+                    T2[0] = make_float2(acc, 0.f);
+                }
+            } else if constexpr (DF) {
                 // gauge kernel: pairs of adjacent y per thread when the chunk has enough
                 // of them to keep the lanes busy; single y otherwise (same sums either way)
                 const int yb = (GAUGE && ych >= 8) ? 2 : 1;
@@ -554,7 +617,14 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
                         g[4] = g[3] + 1;
                         g[5] = g[3] + 2;
                     }
-                    if constexpr (DF) {
+                    if constexpr (DF && F32) {
+                        const float *T1 = reinterpret_cast<const float *>(reinterpret_cast<const float2 *>(T) + off);
+                        const float ev = __ldg(E1 + b.eX[i0 + ijl] + (x0 + xx) + (size_t)h * X.nfp);
+                        sh[0] = fmaf(ev, T1[2 * (size_t)h * ych], sh[0]);
+                        if (GAUGE)
+#pragma unroll
+                            for (int c = 1; c < NC; ++c) sh[c] = fmaf(ev, T1[2 * (size_t)g[c - 1] * ych], sh[c]);
+                    } else if constexpr (DF) {
                         const float2 *T2 = reinterpret_cast<const float2 *>(T) + off;
                         const float2 ev = __ldg(E2 + b.eX[i0 + ijl] + (x0 + xx) + (size_t)h * X.nfp);
                         df_madd<false>(ev, T2[(size_t)h * ych], sh[0], sl[0]);
@@ -618,7 +688,16 @@ __global__ void __launch_bounds__(256, 2) eri_rows_kernel(const EriParams *prms,
                 const int x1 = min(X.nfp, x0 + pl.ach);
                 for (int y0 = 0; y0 < Y.nfp; y0 += pl.cch) {
                     const int y1 = min(Y.nfp, y0 + pl.cch);
-                    block_chunk<GAUGE, DF>(prm.pp, prm.E, prm.E2, prm.boys, X, Y, x0, x1, y0, y1, pl, b);
+                    if constexpr (DF) {
+                        if (tk.f32)
+                            block_chunk<GAUGE, true, true>(prm.pp, prm.E, prm.E2, prm.E1, prm.boys, X, Y, x0, x1, y0, y1,
+                                                           pl, b);
+                        else
+                            block_chunk<GAUGE, true, false>(prm.pp, prm.E, prm.E2, prm.E1, prm.boys, X, Y, x0, x1, y0,
+                                                            y1, pl, b);
+                    } else {
+                        block_chunk<GAUGE, false>(prm.pp, prm.E, prm.E2, prm.E1, prm.boys, X, Y, x0, x1, y0, y1, pl, b);
+                    }
                     const int xch = x1 - x0, ych = y1 - y0;
                     for (int idx = threadIdx.x; idx < xch * ych; idx += blockDim.x) {
                         const int xx = idx / ych, yy = idx - xx * ych;
@@ -743,9 +822,36 @@ void launch_eri(const EriParams *prms, const EriTask *tasks, int ntasks, int *ne
     QDT_CHECK_KERNEL("eri_rows_kernel");
 }
 
-void launch_split_pairs(const double *E, long long n, float2 *E2, cudaStream_t s) {
+// max over the entries of two integral-row blocks of |A - B| / (Q_row Q_col),
+// rows and columns mapped to their shell pairs (mult 3: gauge rows (ab, I)).
+__global__ void ratio_kernel(const double *A, const double *B, long long rows, long long ldw, int mult,
+                             const int *row_pair, const int *col_pair, long long ncols, const double *Q,
+                             double *out) {
+    double m = 0.0;
+    const long long total = rows * ldw;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / ldw, c = e - r * ldw;
+        if (c / mult >= ncols) continue;
+        const double q = Q[row_pair[r / mult]] * Q[col_pair[c / mult]];
+        const double d = fabs(A[e] - B[e]);
+        if (d > 0.0) m = fmax(m, q > 0.0 ? d / q : INFINITY);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long *)out, (unsigned long long)__double_as_longlong(m));
+}
+
+void launch_ratio(const double *A, const double *B, long long rows, long long ldw, int mult, const int *row_pair,
+                  const int *col_pair, long long ncols, const double *Q, double *out, cudaStream_t s) {
+    if (rows <= 0 || ldw <= 0) return;
+    long long blocks = std::min<long long>((rows * ldw + 255) / 256, 152 * 8);
+    ratio_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, B, rows, ldw, mult, row_pair, col_pair, ncols, Q, out);
+    QDT_CHECK_LAUNCH();
+}
+
+void launch_split_pairs(const double *E, long long n, float2 *E2, float *E1, cudaStream_t s) {
     if (n <= 0) return;
-    split_pairs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E, n, E2);
+    split_pairs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E, n, E2, E1);
     QDT_CHECK_KERNEL("split_pairs_kernel");
 }
 
@@ -759,7 +865,7 @@ __global__ void __launch_bounds__(256, 2) schwarz_kernel(const PrimPairDev *pp, 
     double qmax = 0.0;
     for (int a0 = 0; a0 < AB.nfp; a0 += pl.ach) {
         const int a1 = min(AB.nfp, a0 + pl.ach);
-        block_chunk<false, false>(pp, E, nullptr, boys, AB, AB, a0, a1, a0, a1, pl, b);
+        block_chunk<false, false>(pp, E, nullptr, nullptr, boys, AB, AB, a0, a1, a0, a1, pl, b);
         const int ach = a1 - a0;
         if (threadIdx.x == 0)
             for (int a = 0; a < ach; ++a) qmax = fmax(qmax, sqrt(fabs(b.G[(size_t)a * ach + a])));

@@ -72,7 +72,7 @@ T *dcopy(DBuf &b, const std::vector<T> &v, cudaStream_t s) {
 }
 
 struct ClassBufs {
-    DBuf pairs, pp, E, E2, Q, bra, pp_pair;
+    DBuf pairs, pp, E, E2, E1, Q, bra, pp_pair;
 };
 
 // Instantiated graph of a batch round and the signature it was captured for.
@@ -179,10 +179,15 @@ std::vector<int> tile_order(const PairClass &pc, std::vector<int> v, int order) 
 }
 
 // Tiles: each bra pair's kept ket prefix cut into runs of `kets` positions.
+// Tiles of `kets` sorted ket positions per bra pair; with `split`, positions
+// [0, split) and [split, prefix) are tiled apart, the second set in plain FP32.
 void build_tiles(const std::vector<int> &bras, const std::vector<int> &prefix, int kets, int req,
-                 std::vector<EriTask> &out) {
-    for (int sp : bras)
-        for (int q = 0; q < prefix[sp]; q += kets) out.push_back({sp, q, std::min(prefix[sp], q + kets), req});
+                 std::vector<EriTask> &out, const std::vector<int> *split = nullptr) {
+    for (int sp : bras) {
+        const int mid = split ? (*split)[sp] : prefix[sp];
+        for (int q = 0; q < mid; q += kets) out.push_back({sp, q, std::min(mid, q + kets), req, 0});
+        for (int q = mid; q < prefix[sp]; q += kets) out.push_back({sp, q, std::min(prefix[sp], q + kets), req, 1});
+    }
 }
 
 // ---------------------------------------------------------------- autotuner
@@ -347,7 +352,8 @@ void build_class(qdt_ctx *ctx, int c) {
                           pc.npp_total, (const double *)ctx->exps.p, (const double *)ctx->coefs.p,
                           (const double *)ctx->norms.p, pc.d_pp, pc.d_E, s);
     pc.d_E2 = (float2 *)b.E2.get(std::max<long long>(1, eoff) * sizeof(float2));
-    launch_split_pairs(pc.d_E, eoff, pc.d_E2, s);
+    pc.d_E1 = (float *)b.E1.get(std::max<long long>(1, eoff) * sizeof(float));
+    launch_split_pairs(pc.d_E, eoff, pc.d_E2, pc.d_E1, s);
     ctx->launches += 2;
     // Schwarz diagonals, then the bra order (Q descending, ties by id)
     pc.d_Q = (double *)b.Q.get(std::max(1, pc.nsp) * sizeof(double));
@@ -411,6 +417,8 @@ struct ClassPlan {
     int *prefix = nullptr, *ketsp = nullptr, *d_kpos = nullptr;
     long long *ketcol = nullptr;
     std::vector<int> h_prefix, h_ketsp, h_kpos;
+    std::vector<int> h_split;     // per bra pair: kept ket positions [h_split, h_prefix) run in plain FP32
+    std::vector<double> h_Dmax;
     std::vector<long long> h_col, Krow;
     size_t wbudget = 0;
 };
@@ -435,6 +443,8 @@ void order_kets(qdt_ctx *ctx, ClassPlan &P, cudaStream_t s) {
     QDT_CUDA_TRY(cudaMemcpyAsync(P.h_prefix.data(), P.prefix, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
     QDT_CUDA_TRY(cudaMemcpyAsync(P.h_col.data(), P.ketcol, (pc.nsp + 1) * sizeof(long long), cudaMemcpyDeviceToHost, s));
     QDT_CUDA_TRY(cudaMemcpyAsync(P.h_ketsp.data(), P.ketsp, pc.nsp * sizeof(int), cudaMemcpyDeviceToHost, s));
+    P.h_Dmax.resize(pc.nsp);
+    QDT_CUDA_TRY(cudaMemcpyAsync(P.h_Dmax.data(), P.Dmax, pc.nsp * sizeof(double), cudaMemcpyDeviceToHost, s));
     // 3. ket-ordered density copy (density route) or the function indices of
     // the ket-ordered columns (quarter route)
     if (P.quarter) {
@@ -497,6 +507,80 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
     tm.mark();
 }
 
+// Split form: which kept quartets may have their integrals in plain FP32.
+// An integral computed in FP32 from FP64 Boys values and prefactors is taken
+// to be within kF32Rel Q_A Q_C of its FP64 value (kF32Rel = 1024 x 2^-24;
+// `tests/test_gpu_dynprec.py` measures the actual ratio).  An error d in
+// (ab|cd) moves a packed output element by at most |D_ab| d |D_cd| (times
+// g: 1 Coulomb, 3 Gaunt (three J), 18 gauge (nine IJ, two terms)), so the
+// FP32 quartets of a class add at most
+//     sum g kF32Rel (Q_A Dmax_A nfp_A) (Q_C Dmax_C nfp_C)
+// over its ordered kept pairs (A, C).  With w = Q Dmax the FP32 set is
+// {w_A w_C <= t}, a suffix of every bra row's w-sorted ket list (and the
+// same decision for (C, A), so bra-ket symmetry is kept); t is the largest
+// threshold whose bound stays within kF32Budget.  QDT_F32_BUDGET overrides
+// the budget (0 turns the FP32 quartets off).
+constexpr double kF32Rel = 1024.0 / 16777216.0;
+constexpr double kF32Budget = 1e-11;
+
+double f32_budget() {
+    if (const char *e = std::getenv("QDT_F32_BUDGET")) {
+        const double v = std::atof(e);
+        if (!(v >= 0.0)) throw Error{QDT_ERR_ARG, "QDT_F32_BUDGET must be >= 0"};
+        return v;
+    }
+    return kF32Budget;
+}
+
+void f32_split(qdt_ctx *ctx, ClassPlan &P, double &bound_out) {
+    PairClass &pc = ctx->cls[P.cr.c];
+    const int n = pc.nsp;
+    P.h_split = P.h_prefix;
+    bound_out = 0.0;
+    const double budget = P.precision == QDT_SPLIT ? f32_budget() : 0.0;
+    if (budget <= 0.0 || n == 0) return;
+    const double g = !P.ls ? 1.0 : (P.cr.gauge ? 18.0 : 3.0);
+    std::vector<double> w(n), ws(n), S(n + 1, 0.0);      // w per pair; sorted w and prefix sums of w nfp
+    for (int i = 0; i < n; ++i) w[i] = pc.h_Q[i] * P.h_Dmax[i];
+    for (int q = 0; q < n; ++q) {
+        const int id = P.h_ketsp[q];
+        ws[q] = w[id];
+        S[q + 1] = S[q] + ws[q] * (double)pc.h_pairs[id].nfp;
+    }
+    // first kept position of row a whose product with w_a is <= t
+    auto start = [&](int a, double t) {
+        int lo = 0, hi = P.h_prefix[a];
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (w[a] * ws[mid] <= t) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    };
+    auto total = [&](double t) {
+        double b = 0.0;
+        for (int a = 0; a < n; ++a) {
+            const int s0 = start(a, t), e = P.h_prefix[a];
+            if (s0 < e) b += w[a] * (double)pc.h_pairs[a].nfp * (S[e] - S[s0]);
+        }
+        return g * kF32Rel * b;
+    };
+    double lo = 0.0, hi = 0.0;                           // total(lo) within budget, search up to w_max^2
+    for (int i = 0; i < n; ++i) hi = std::max(hi, w[i]);
+    hi = hi * hi;
+    if (total(hi) <= budget) {
+        lo = hi;
+    } else {
+        if (total(lo) > budget) return;                  // zero products alone exceed the budget
+        for (int it = 0; it < 60; ++it) {                // bisection on the exponent scale
+            const double mid = lo > 0.0 ? std::sqrt(lo * hi) : hi * 1e-30;
+            if (mid <= lo || mid >= hi) break;
+            if (total(mid) <= budget) lo = mid; else hi = mid;
+        }
+    }
+    for (int a = 0; a < n; ++a) P.h_split[a] = start(a, lo);
+    bound_out = total(lo);
+}
+
 // Waits for class_issue; kept-quartet statistics, V buffers and the row-batch
 // decision: one batch (and bra-ket symmetry) when the integral block (plus the
 // split form's digit planes of one row chunk) fits in 70 % of the device
@@ -505,15 +589,21 @@ void class_finish(qdt_ctx *ctx, ClassPlan &P, qdt_stats *st) {
     PairClass &pc = ctx->cls[P.cr.c];
     cudaStream_t s = ctx->stream;
     QDT_CUDA_TRY(cudaStreamSynchronize(s));
-    long long kept = 0;
+    long long kept = 0, f32 = 0;
     for (int i = 0; i < pc.nsp; ++i) kept += P.h_prefix[i];
+    double bound = 0.0;
+    f32_split(ctx, P, bound);
+    for (int i = 0; i < pc.nsp; ++i) f32 += P.h_prefix[i] - P.h_split[i];
     if (st) {
         int slot = P.ls ? 1 : 0;
         st->quartets_total[slot] += (long long)pc.nsp * pc.nsp;
         st->quartets_kept[slot] += kept;
+        st->quartets_f32[slot] += f32;
+        st->f32_bound = std::max(st->f32_bound, bound);
         if (P.ls && P.cr.gauge) {
             st->quartets_total[2] += (long long)pc.nsp * pc.nsp;
             st->quartets_kept[2] += kept;
+            st->quartets_f32[2] += f32;
         }
     }
     P.Krow.assign(pc.nsp, 0);
@@ -583,6 +673,7 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
     prm.pp = pc.d_pp;
     prm.E = pc.d_E;
     prm.E2 = P.precision == QDT_SPLIT ? pc.d_E2 : nullptr;
+    prm.E1 = P.precision == QDT_SPLIT ? pc.d_E1 : nullptr;
     prm.boys = (const double *)ctx->boys.p;
     prm.ket_sp = P.ketsp;
     prm.ket_col = P.ketcol;
@@ -627,7 +718,7 @@ void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, long long 
     PairClass &pc = ctx->cls[P.cr.c];
     const int TMr = gemm_fp64_tile_m();
     long long v = 0;
-    double fl = 0.0;
+    double fl = 0.0, fl32 = 0.0;
     const bool gauge = B.prm.gauge != 0;
     for (int k = B.b0; k < B.b1; ++k) {
         int sp = pc.bra_order[k];
@@ -638,11 +729,14 @@ void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, long long 
             const int cid = P.h_ketsp[q];
             const PairDev &cd = pc.h_pairs[cid];
             if (P.one_batch && cid < sp && P.h_kpos[sp] < P.h_prefix[cid]) continue;
-            fl += 2.0 * std::min(orient_cost_h(ab, cd, gauge), orient_cost_h(cd, ab, gauge));
+            const double f = 2.0 * std::min(orient_cost_h(ab, cd, gauge), orient_cost_h(cd, ab, gauge));
+            fl += f;
+            if (B.prm.E2 && q >= P.h_split[sp]) fl32 += f;
         }
     }
     st->eri_values += v * (B.prm.gauge ? 6 : 1);
     st->flops_eri += fl;
+    st->flops_eri_f32 += fl32;
     if (P.quarter) return;   // counted by quarter_half1
     const long long Wrows = B.rows * P.mult;
     double f = 0;
@@ -851,7 +945,7 @@ void run_batches(qdt_ctx *ctx, ClassPlan &P, long long c0, long long c1, qdt_sta
         const bool df = B.prm.E2 != nullptr;
         const EriLaunch how = eri_launch_for(ctx, pc, shape, B.prm.gauge != 0, df, d_prm, B.bras, P.h_prefix, s);
         std::vector<EriTask> tk;
-        build_tiles(tile_order(pc, B.bras, how.order), P.h_prefix, how.kets, 0, tk);
+        build_tiles(tile_order(pc, B.bras, how.order), P.h_prefix, how.kets, 0, tk, df ? &P.h_split : nullptr);
         EriTask *d_tk = dcopy(ctx->tasks, tk, s);
         int te = tm.n; tm.mark();
         launch_zero(B.W, B.rows * P.mult * B.ldw, s);
@@ -1120,8 +1214,11 @@ void batch_round(qdt_ctx *owner, std::vector<BatchReq> &R, int round, unsigned f
                 std::stable_sort(order.begin(), order.end(), [](const Key &a, const Key &b) { return a.cost > b.cost; });
             for (const Key &o : order) {
                 const std::vector<int> &pre = fz[o.i]->P.h_prefix;
-                for (int q = 0; q < pre[o.sp]; q += how[k].kets)
-                    tiles[k].push_back({o.sp, q, std::min(pre[o.sp], q + how[k].kets), req_of[o.i]});
+                const int mid = (k & 1) ? fz[o.i]->P.h_split[o.sp] : pre[o.sp];    // FP32 tail (split form)
+                for (int q = 0; q < mid; q += how[k].kets)
+                    tiles[k].push_back({o.sp, q, std::min(mid, q + how[k].kets), req_of[o.i], 0});
+                for (int q = mid; q < pre[o.sp]; q += how[k].kets)
+                    tiles[k].push_back({o.sp, q, std::min(pre[o.sp], q + how[k].kets), req_of[o.i], 1});
             }
             d_tiles[k] = dcopy(owner->btasks[k], tiles[k], s0);
             ntiles[k] = (int)tiles[k].size();
@@ -1249,7 +1346,7 @@ void qdt_destroy(qdt_ctx *c) {
                     &c->qkt[1], &c->qkt[2]};
     for (DBuf *b : bufs) b->release();
     for (int k = 0; k < 2; ++k) {
-        c->cb[k].pairs.release(); c->cb[k].pp.release(); c->cb[k].E.release(); c->cb[k].E2.release();
+        c->cb[k].pairs.release(); c->cb[k].pp.release(); c->cb[k].E.release(); c->cb[k].E2.release(); c->cb[k].E1.release();
         c->cb[k].Q.release(); c->cb[k].bra.release(); c->cb[k].pp_pair.release();
     }
     split_release(c->split);
@@ -1407,6 +1504,68 @@ int qdt_set_rkb_coefficients(qdt_ctx *c, int n, const double *CL, const double *
         return QDT_ERR_ARG;
     }
     return set_coefficients(c, n, CL, CS, spinors != 0, c_light, "qdt_set_rkb_coefficients");
+}
+
+int qdt_f32_error_ratio(qdt_ctx *c, unsigned blocks, int k_begin, int k_end, double tau, double *ratio) {
+    if (!c || !ratio) return QDT_ERR_ARG;
+    try {
+        QDT_CUDA_TRY(cudaSetDevice(c->device));
+        if (!c->has_basis || !c->has_coef) throw Error{QDT_ERR_STATE, "qdt_f32_error_ratio: basis or coefficients not set"};
+        arg_check(blocks != 0 && (blocks & ~7u) == 0 && k_begin >= 0 && k_end > k_begin && k_end <= c->nK &&
+                      tau >= 0.0, "qdt_f32_error_ratio: bad blocks, range or threshold");
+        cudaStream_t s = c->stream;
+        for (int cls = 0; cls < 2; ++cls) {
+            ratio[cls] = 0.0;
+            const bool want = cls == 0 ? (blocks & QDT_COULOMB) != 0 : (blocks & (QDT_GAUNT | QDT_GAUGE)) != 0;
+            if (!want) continue;
+            ClassRun cr{cls, cls == 0, cls == 1 && (blocks & QDT_GAUNT), cls == 1 && (blocks & QDT_GAUGE)};
+            PairClass &pc = c->cls[cls];
+            ClassPlan P;
+            Timer tm(c, false);
+            class_issue(c, cr, k_begin, k_end - k_begin, tau, QDT_SPLIT, P, tm);
+            class_finish(c, P, nullptr);
+            RowBatch B;
+            batch_prepare(c, P, 0, B);
+            arg_check(P.one_batch && B.b1 == pc.nsp, "qdt_f32_error_ratio: the class must fit one row batch");
+            const EriParams *d_prm = dcopy(c->prms, std::vector<EriParams>{B.prm}, s);
+            const EriShape shape{pc.maxnfp, pc.maxLab, pc.maxnpp};
+            EriLaunch how;
+            how.threads = eri_default_threads(shape, B.prm.gauge != 0);
+            const size_t n = (size_t)B.rows * P.mult * B.ldw;
+            struct Bufs {         // released on every exit path
+                DBuf ref, rp, cp, out;
+                ~Bufs() { ref.release(); rp.release(); cp.release(); out.release(); }
+            } tmp;
+            double *W2 = (double *)tmp.ref.get(std::max<size_t>(1, n) * sizeof(double));
+            std::vector<int> none(pc.nsp, 0);
+            for (int pass = 0; pass < 2; ++pass) {      // compensated FP32, then plain FP32
+                std::vector<EriTask> tk;
+                build_tiles(B.bras, P.h_prefix, how.kets, 0, tk, pass ? &none : nullptr);
+                EriTask *d_tk = dcopy(c->tasks, tk, s);
+                launch_zero(B.W, (long long)n, s);
+                launch_eri(d_prm, d_tk, (int)tk.size(), (int *)c->next.get(sizeof(int)), shape, B.prm.gauge != 0, true,
+                           how, s);
+                if (pass == 0) QDT_CUDA_TRY(cudaMemcpyAsync(W2, B.W, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            }
+            std::vector<int> rp(P.M), cp(P.M);
+            for (int k = 0; k < pc.nsp; ++k) {
+                const PairDev &pr = pc.h_pairs[pc.bra_order[k]];
+                for (int f = 0; f < pr.nfp; ++f) rp[pr.rowoff + f] = pc.bra_order[k];
+            }
+            for (int q = 0; q < pc.nsp; ++q)
+                for (long long j = P.h_col[q]; j < P.h_col[q + 1]; ++j) cp[j] = P.h_ketsp[q];
+            const int *d_rp = dcopy(tmp.rp, rp, s), *d_cp = dcopy(tmp.cp, cp, s);
+            double *d_out = (double *)tmp.out.get(sizeof(double));
+            QDT_CUDA_TRY(cudaMemsetAsync(d_out, 0, sizeof(double), s));
+            launch_ratio(B.W, W2, B.rows * P.mult, B.ldw, P.mult, d_rp, d_cp, P.M, pc.d_Q, d_out, s);
+            QDT_CUDA_TRY(cudaMemcpyAsync(&ratio[cls], d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+            QDT_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+    } catch (const Error &e) {
+        return fail(c, e);
+    }
+    c->err.clear();
+    return QDT_OK;
 }
 
 int qdt_check_bounded_wait(qdt_ctx *c, double limit_s) {

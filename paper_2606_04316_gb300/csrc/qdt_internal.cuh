@@ -108,6 +108,7 @@ struct PairClass {
     PrimPairDev *d_pp = nullptr;
     double *d_E = nullptr;
     float2 *d_E2 = nullptr;     // E split into FP32 pairs (hi, lo) for the split form's integrals
+    float *d_E1 = nullptr;      // the high parts alone, for the quartets run in plain FP32
     double *d_Q = nullptr;
     int *d_bra_order = nullptr;
     long long npp_total = 0, e_total = 0;
@@ -121,6 +122,7 @@ struct EriParams {
     const PrimPairDev *pp;
     const double *E;
     const float2 *E2;           // E as FP32 pairs: non-null selects the compensated FP32 contraction
+    const float *E1;            // fl32(E), read by the tiles run in plain FP32
     const double *boys;         // [kBoysGrid][kBoysCols]
     const int *ket_sp;          // shell pair id at each sorted ket position
     const long long *ket_col;   // first column of each sorted ket position
@@ -142,6 +144,7 @@ struct EriTask {                // one tile: bra shell pair x range of sorted ke
     int bra_sp;
     int k0, k1;
     int req;                    // index into the EriParams array of the launch
+    int f32 = 0;                // compensated-FP32 kernels: 1 = these quartets in plain FP32
 };
 
 // Class maxima that fix the integral kernel's shared-memory plan.
@@ -173,7 +176,10 @@ void launch_shell_norms(const ShellDev *shells, int nL_shells, const double *exp
 void launch_eri(const EriParams *prms, const EriTask *tasks, int ntasks, int *next, const EriShape &shape,
                 bool gauge, bool df, const EriLaunch &how, cudaStream_t s);
 // E2[i] = (hi, lo) with hi = fl32(E[i]), lo = fl32(E[i] - hi).
-void launch_split_pairs(const double *E, long long n, float2 *E2, cudaStream_t s);
+// max |A - B| / (Q_row Q_col) over integral rows (FP32 error model check).
+void launch_ratio(const double *A, const double *B, long long rows, long long ldw, int mult, const int *row_pair,
+                  const int *col_pair, long long ncols, const double *Q, double *out, cudaStream_t s);
+void launch_split_pairs(const double *E, long long n, float2 *E2, float *E1, cudaStream_t s);
 int eri_default_threads(const EriShape &shape, bool gauge);
 void launch_schwarz(const ShellDev *shells, const PairDev *pairs, const PrimPairDev *pp,
                     const double *E, const double *boys, int npairs, int maxnfp, int maxLab,

@@ -24,7 +24,7 @@ EXPORTS = ["qdt_create", "qdt_destroy", "qdt_set_basis", "qdt_num_functions", "q
            "qdt_footprint", "qdt_server_create", "qdt_server_destroy", "qdt_submit", "qdt_poll", "qdt_wait",
            "qdt_second_half_noalloc", "qdt_transform_batch", "qdt_graph_counts",
            "qdt_set_spinor_coefficients", "qdt_set_rkb_coefficients", "qdt_set_route",
-           "qdt_check_bounded_wait"]
+           "qdt_check_bounded_wait", "qdt_f32_error_ratio"]
 BATCH_GRAPH = 1
 
 
@@ -42,7 +42,9 @@ class Stats(ctypes.Structure):
                 ("flops_half2", ctypes.c_double), ("quartets_total", ctypes.c_longlong * 3),
                 ("quartets_kept", ctypes.c_longlong * 3), ("eri_values", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_int), ("precision", ctypes.c_int),
-                ("slices", ctypes.c_int), ("flops_eri", ctypes.c_double)]
+                ("slices", ctypes.c_int), ("flops_eri", ctypes.c_double),
+                ("quartets_f32", ctypes.c_longlong * 3), ("f32_bound", ctypes.c_double),
+                ("flops_eri_f32", ctypes.c_double)]
 
     def as_dict(self):
         d = {}
@@ -97,6 +99,7 @@ def load(build_if_missing=True):
     L.qdt_set_rkb_coefficients.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_int]
     L.qdt_set_route.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.qdt_check_bounded_wait.argtypes = [vp, ctypes.c_double]
+    L.qdt_f32_error_ratio.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp]
     L.qdt_packed_size.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int]
     L.qdt_packed_size.restype = ctypes.c_size_t
     L.qdt_transform.argtypes = [vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -211,6 +214,13 @@ class Context:
         'mo' (MO-driven, integrals recomputed per block of mo_block outer MOs)."""
         code = {"density": 0, "quarter": 1, "mo": 2}[route]
         self._check(self.L.qdt_set_route(self.h, code, int(mo_block)))
+
+    def f32_error_ratio(self, blocks, k_begin, k_end, tau):
+        """[Coulomb, L-S class] max |FP32 - compensated FP32| / (Q_A Q_C) of the kept integrals."""
+        r = (ctypes.c_double * 2)()
+        self._check(self.L.qdt_f32_error_ratio(self.h, blocks_mask(blocks), int(k_begin), int(k_end), float(tau),
+                                               ctypes.cast(r, ctypes.c_void_p)))
+        return [r[0], r[1]]
 
     def check_bounded_wait(self, limit_s=0.05):
         """Status code of the bounded-wait self-check (QDT_ERR_TIMEOUT = -6 expected)."""

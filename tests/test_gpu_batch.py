@@ -81,10 +81,13 @@ def test_batch_host_output(torch_cuda):
         assert np.abs(o - ref).max() <= TOL_FP64
 
 
-def test_batch_graph_capture_and_replay(torch_cuda):
+def test_batch_graph_capture_and_replay(torch_cuda, monkeypatch):
     """tau = 0 keeps the screening outcome fixed when the coefficients change,
-    so the same batch signature recurs: the graph is captured, replayed, and
-    a replay after new coefficients gives the new results."""
+    and a zero FP32 budget keeps every integral in compensated pairs (the
+    FP32 set follows the densities), so the same batch signature recurs: the
+    graph is captured, replayed, and a replay after new coefficients gives the
+    new results."""
+    monkeypatch.setenv("QDT_F32_BUDGET", "0")
     torch = torch_cuda
     from paper_2606_04316_gb300 import qdt
     probs = problems(tau=0.0)
