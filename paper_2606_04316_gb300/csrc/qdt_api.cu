@@ -195,9 +195,9 @@ void build_tiles(const std::vector<int> &bras, const std::vector<int> &prefix, i
 // class maxima), chosen by timing on a sample of the class: every 8th bra
 // pair of the bra order (an eighth of the work, so that every candidate runs
 // many tiles per CTA slot).  The search is coordinate-wise from (plan threads,
-// 8 kets, bra order), the start point timed twice (warm): ket
-// positions per tile {4, 8, 16}, then CTA threads {128, 256}, then the tile
-// order.  The candidates differ only in how the work is cut and scheduled,
+// 8 kets, bra order), after one warm-up run: ket positions per tile
+// {2, 4, 8, 16}, then CTA threads {128, 256}, then the tile order; each
+// candidate keeps the faster of two timings.  The candidates differ only in how the work is cut and scheduled,
 // never in the arithmetic of an integral, so the choice changes no result bit.
 // Process-wide cache; QDT_AUTOTUNE=0 keeps the start point, QDT_AUTOTUNE_VERBOSE=1
 // prints every timing to stderr, QDT_ERI_LAUNCH="threads,kets,order" pins the
