@@ -366,6 +366,41 @@ __device__ __forceinline__ void ket_orders_f32(int n0, int Ly, int tx, int ux, i
     }
 }
 
+// The same for two T rows (Hermite indices a, b) of one inner function pair:
+// each E value is loaded once for both rows (the FP32 tiles wait on these loads).
+template <bool NEG>
+__device__ __forceinline__ void ket_orders_f32x2(int n0, int Ly, int txa, int uxa, int vxa, int txb, int uxb,
+                                                 int vxb, const int *trip, const float2 *Rq, int nr,
+                                                 const float *ey, int nfpY, long long sE, int nk, float &acca,
+                                                 float &accb) {
+    for (int n = n0; n <= Ly; n += 2) {
+        const int hb = n ? nherm(n - 1) : 0, he = nherm(n);
+        for (int hp = hb; hp < he; ++hp) {
+            const int tq = trip[hp];
+            const int tp = tq & 255, up = (tq >> 8) & 255, vp = tq >> 16;
+            const int Ta = txa + tp, Ua = uxa + up, Va = vxa + vp, sa = Ta + Ua + Va, wa = Ua + Va;
+            const int Tb = txb + tp, Ub = uxb + up, Vb = vxb + vp, sb = Tb + Ub + Vb, wb = Ub + Vb;
+            const int ia = sa * (sa + 1) * (sa + 2) / 6 + wa * (wa + 1) / 2 + Va;
+            const int ib = sb * (sb + 1) * (sb + 2) / 6 + wb * (wb + 1) / 2 + Vb;
+            const float *e = ey + (size_t)hp * nfpY;
+            const float *ra = reinterpret_cast<const float *>(Rq + ia);
+            const float *rb = reinterpret_cast<const float *>(Rq + ib);
+            float a = acca, b2 = accb;
+#pragma unroll 4
+            for (int kl = 0; kl < nk; ++kl) {
+                const float ev = __ldg(e);
+                a = NEG ? fmaf(-*ra, ev, a) : fmaf(*ra, ev, a);
+                b2 = NEG ? fmaf(-*rb, ev, b2) : fmaf(*rb, ev, b2);
+                ra += 2 * nr;
+                rb += 2 * nr;
+                e += sE;
+            }
+            acca = a;
+            accb = b2;
+        }
+    }
+}
+
 // The same for two adjacent inner function pairs y, y + 1 at once (the second
 // when has1): R and the primitive-pair offsets are loaded once for both, and
 // the two accumulator chains are independent (gauge kernel, whose larger
@@ -518,7 +553,28 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
             }
             // T[ij][h][y] += sum_kl sum_h' (-1)^{|h'|} R[h+h'] E^{kl}[h'][y]: rows h < nhx
             // with the Coulomb tensor, then (gauge) rows g = 4.. with the r12 tensor
-            if constexpr (DF && F32) {
+            if constexpr (DF && F32 && !GAUGE) {
+                // two T rows per thread sharing the E loads
+                const int nT2 = (nT + 1) / 2;
+                for (int it = tid; it < nij * nT2 * ych; it += nt) {
+                    const int ijl = it / (nT2 * ych);
+                    const int rem = it - ijl * nT2 * ych;
+                    const int h0 = 2 * (rem / ych), yy = rem - (rem / ych) * ych;
+                    const bool has1 = h0 + 1 < nT;
+                    const int h1 = has1 ? h0 + 1 : h0;
+                    const int tra = b.trip[h0], trb = b.trip[h1];
+                    float2 *T2 = reinterpret_cast<float2 *>(T + (size_t)ijl * tsz + (size_t)h0 * ych + yy);
+                    float acca = T2[0].x, accb = has1 ? T2[ych].x : 0.f;
+                    const float2 *R2 = reinterpret_cast<const float2 *>(RC + (size_t)ijl * nk * nrC);
+                    const float *ey = E1 + b.eY[k0] + (y0 + yy);
+                    ket_orders_f32x2<false>(0, Ly, tra & 255, (tra >> 8) & 255, tra >> 16, trb & 255, (trb >> 8) & 255,
+                                            trb >> 16, b.trip, R2, nrC, ey, Y.nfp, sE, nk, acca, accb);
+                    ket_orders_f32x2<true>(1, Ly, tra & 255, (tra >> 8) & 255, tra >> 16, trb & 255, (trb >> 8) & 255,
+                                           trb >> 16, b.trip, R2, nrC, ey, Y.nfp, sE, nk, acca, accb);
+                    T2[0] = make_float2(acca, 0.f);
+                    if (has1) T2[ych] = make_float2(accb, 0.f);
+                }
+            } else if constexpr (DF && F32) {
                 for (int it = tid; it < nij * nT * ych; it += nt) {
                     const int ijl = it / (nT * ych);
                     const int rem = it - ijl * nT * ych;
