@@ -571,10 +571,13 @@ void f32_split(qdt_ctx *ctx, ClassPlan &P, double &bound_out) {
         lo = hi;
     } else {
         if (total(lo) > budget) return;                  // zero products alone exceed the budget
-        for (int it = 0; it < 60; ++it) {                // bisection on the exponent scale
-            const double mid = lo > 0.0 ? std::sqrt(lo * hi) : hi * 1e-30;
+        // bisection on the exponent scale, to 1 % in t (each step costs a pass over the rows,
+        // host time inside the transform)
+        for (int it = 0; it < 60; ++it) {
+            const double mid = lo > 0.0 ? std::sqrt(lo) * std::sqrt(hi) : hi * 1e-30;
             if (mid <= lo || mid >= hi) break;
             if (total(mid) <= budget) lo = mid; else hi = mid;
+            if (lo > 0.0 && hi <= lo * 1.01) break;
         }
     }
     for (int a = 0; a < n; ++a) P.h_split[a] = start(a, lo);
