@@ -20,7 +20,8 @@ def sources():
 
 
 def _headers_mtime():
-    hs = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(HERE, "..", "include", "*.h"))
+    hs = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+          glob.glob(os.path.join(HERE, "..", "include", "*.h")))
     return max([os.path.getmtime(h) for h in hs] + [0])
 
 

@@ -22,6 +22,7 @@
 #include <tuple>
 #include <vector>
 
+#include "plan.h"
 #include "qdt_internal.cuh"
 #include "split.cuh"
 
@@ -535,53 +536,15 @@ double f32_budget() {
 void f32_split(qdt_ctx *ctx, ClassPlan &P, double &bound_out) {
     PairClass &pc = ctx->cls[P.cr.c];
     const int n = pc.nsp;
-    P.h_split = P.h_prefix;
-    bound_out = 0.0;
     const double budget = P.precision == QDT_SPLIT ? f32_budget() : 0.0;
-    if (budget <= 0.0 || n == 0) return;
     const double g = !P.ls ? 1.0 : (P.cr.gauge ? 18.0 : 3.0);
-    std::vector<double> w(n), ws(n), S(n + 1, 0.0);      // w per pair; sorted w and prefix sums of w nfp
-    for (int i = 0; i < n; ++i) w[i] = pc.h_Q[i] * P.h_Dmax[i];
-    for (int q = 0; q < n; ++q) {
-        const int id = P.h_ketsp[q];
-        ws[q] = w[id];
-        S[q + 1] = S[q] + ws[q] * (double)pc.h_pairs[id].nfp;
+    std::vector<double> w(n);
+    std::vector<int> nfp(n);
+    for (int i = 0; i < n; ++i) {
+        w[i] = pc.h_Q[i] * P.h_Dmax[i];
+        nfp[i] = pc.h_pairs[i].nfp;
     }
-    // first kept position of row a whose product with w_a is <= t
-    auto start = [&](int a, double t) {
-        int lo = 0, hi = P.h_prefix[a];
-        while (lo < hi) {
-            const int mid = (lo + hi) / 2;
-            if (w[a] * ws[mid] <= t) hi = mid; else lo = mid + 1;
-        }
-        return lo;
-    };
-    auto total = [&](double t) {
-        double b = 0.0;
-        for (int a = 0; a < n; ++a) {
-            const int s0 = start(a, t), e = P.h_prefix[a];
-            if (s0 < e) b += w[a] * (double)pc.h_pairs[a].nfp * (S[e] - S[s0]);
-        }
-        return g * kF32Rel * b;
-    };
-    double lo = 0.0, hi = 0.0;                           // total(lo) within budget, search up to w_max^2
-    for (int i = 0; i < n; ++i) hi = std::max(hi, w[i]);
-    hi = hi * hi;
-    if (total(hi) <= budget) {
-        lo = hi;
-    } else {
-        if (total(lo) > budget) return;                  // zero products alone exceed the budget
-        // bisection on the exponent scale, to 1 % in t (each step costs a pass over the rows,
-        // host time inside the transform)
-        for (int it = 0; it < 60; ++it) {
-            const double mid = lo > 0.0 ? std::sqrt(lo) * std::sqrt(hi) : hi * 1e-30;
-            if (mid <= lo || mid >= hi) break;
-            if (total(mid) <= budget) lo = mid; else hi = mid;
-            if (lo > 0.0 && hi <= lo * 1.01) break;
-        }
-    }
-    for (int a = 0; a < n; ++a) P.h_split[a] = start(a, lo);
-    bound_out = total(lo);
+    f32_tail_split(w, nfp, P.h_ketsp, P.h_prefix, g * kF32Rel, budget, P.h_split, &bound_out);
 }
 
 // Waits for class_issue; kept-quartet statistics, V buffers and the row-batch
