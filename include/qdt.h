@@ -222,6 +222,12 @@ size_t qdt_packed_size(const qdt_ctx *ctx, unsigned blocks, int k_begin, int k_e
  * Transform: packed (pq|rs) for the Kramers pairs [k_begin, k_end) of the
  * current coefficients, for every block bit set in `blocks`, with Schwarz
  * threshold `schwarz_tau` >= 0 and `precision` QDT_FP64 or QDT_SPLIT.
+ * QDT_FP64: integrals and contractions in FP64.  QDT_SPLIT: contractions as
+ * Ozaki BF16 slices on the tensor cores with FP64 recombination; integrals in
+ * compensated FP32 pairs, except the quartets whose error bound fits a 1e-11
+ * budget on every output element, which run in plain FP32 (the environment
+ * variable QDT_F32_BUDGET sets the budget, 0 turns it off; stats report the
+ * quartets and the bound).  Held to 1e-10 Eh of the FP64 form.
  * `out` (host or device, caller-owned) receives qdt_packed_size() bytes;
  * `out_bytes` must be at least that.  Device scratch is allocated and kept by
  * the context between calls.  `stats` may be NULL.
