@@ -58,3 +58,33 @@ def test_packed_size_formula(lib):
     nP = n * (n + 1) // 2
     assert lib.qdt_packed_size(None, 1, 0, n) == nP * (nP + 1) // 2 * 16 * 8
     assert lib.qdt_packed_size(None, 7, 0, n) == 3 * nP * (nP + 1) // 2 * 16 * 8
+
+
+def test_null_context_arguments_are_refused(lib):
+    """Every entry point that takes a context refuses a null one with
+    QDT_ERR_ARG (-1) instead of crashing (no GPU touched)."""
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    calls = [
+        ("qdt_set_route", [vp, i, i], (None, 0, 0)),
+        ("qdt_check_bounded_wait", [vp, d], (None, 0.05)),
+        ("qdt_f32_error_ratio", [vp, ctypes.c_uint, i, i, d, vp], (None, 1, 0, 1, 0.0, None)),
+        ("qdt_set_coefficients", [vp, i, vp, vp], (None, 1, None, None)),
+        ("qdt_set_spinor_coefficients", [vp, i, vp, vp], (None, 1, None, None)),
+        ("qdt_set_rkb_coefficients", [vp, i, vp, vp, d, i], (None, 1, None, None, 137.0, 0)),
+    ]
+    for name, argtypes, args in calls:
+        f = getattr(lib, name)
+        f.argtypes = argtypes
+        f.restype = ctypes.c_int
+        assert f(*args) == -1, name
+    lib.qdt_num_functions.argtypes = [vp]
+    assert lib.qdt_num_functions(None) == 0
+
+
+def test_unrestricted_packed_size_of_null_context_is_restricted_formula(lib):
+    """Without a context the size is that of quaternion input (16 reals per
+    canonical pair of Kramers pairs)."""
+    lib.qdt_packed_size.restype = ctypes.c_size_t
+    lib.qdt_packed_size.argtypes = [ctypes.c_void_p, ctypes.c_uint, ctypes.c_int, ctypes.c_int]
+    assert lib.qdt_packed_size(None, 1, 3, 3) == 0
+    assert lib.qdt_packed_size(None, 1, 2, 5) == 6 * 7 // 2 * 16 * 8
