@@ -96,9 +96,19 @@ def lib():
             L.or_pair_rows.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_long, lp, dp]
             L.or_pair_matrix.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, dp]
             L.or_pair_diag.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
+            L.or_shell_pair_rows.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_void_p, lp, dp]
+            L.or_shell_pair_rows.restype = ctypes.c_long
+            L.or_set_threads.argtypes = [ctypes.c_int]
+            L.or_set_threads.restype = None
             L.or_overlap_block.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, dp]
             _LIB = L
     return _LIB
+
+
+def set_threads(n):
+    """Host threads of the C integral loops (OpenMP)."""
+    lib().or_set_threads(int(n))
 
 
 def _dp(a):
@@ -244,6 +254,43 @@ class OracleBasis:
         lib().or_pair_rows(self.h, cls, kernel, int(rows.shape[0]),
                            rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out))
         return out
+
+    def shell_pair_rows(self, cls, kernel, p, keep):
+        """Rows of the pair matrix for the function pairs of shell pair ``p``
+        (the ``pairs(cls)`` shell-pair id), computed only against the ket shell
+        pairs with keep[q] true (the others stay zero).  Returns (row pair
+        indices [n], values [n, M] or [n, 6, M] for kernel 2)."""
+        M = self.npairs(cls)
+        keep = np.ascontiguousarray(keep, dtype=np.uint8)
+        n = self.n_shell_pairs(cls)
+        if keep.shape != (n,):
+            raise ValueError("keep must have one entry per shell pair")
+        sa, sb = self._shell_pair_shells(cls, int(p))
+        nmax = self._nfunc(sa) * self._nfunc(sb)
+        ncomp = 6 if kernel == 2 else 1
+        rows = np.zeros(nmax, np.int64)
+        out = np.zeros((nmax, ncomp, M))
+        nr = lib().or_shell_pair_rows(self.h, int(cls), int(kernel), int(p), keep.ctypes.data_as(ctypes.c_void_p),
+                                      rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out))
+        rows, out = rows[:nr], out[:nr]
+        return rows, (out if kernel == 2 else out[:, 0, :])
+
+    def _shell_pair_shells(self, cls, p):
+        """Oracle shells (index >= nsh: derivative shell) of shell pair p:
+        class 0 = LL pairs A <= B (row-major) then SS pairs A <= B; class 1 =
+        (A, derivative shell of B), p = A nsh + B."""
+        n = self.nsh
+        if cls == 1:
+            return p // n, n + p % n
+        off = 0
+        if p >= n * (n + 1) // 2:
+            p -= n * (n + 1) // 2
+            off = n
+        a = 0
+        while p >= n - a:
+            p -= n - a
+            a += 1
+        return a + off, a + p + off
 
     def pair_diag(self, cls):
         out = np.zeros(self.npairs(cls))
@@ -576,6 +623,82 @@ class Transform:
 
     def packed(self, block, screened=True):
         return pack_canonical(self.packed_full(block, screened), self.nKa)
+
+    # the same, streamed by bra shell pairs (large systems) ----------------
+    def V_rows_streamed(self, block, bra_pairs=None):
+        """First half V = G_screened D (Eq. firsthalf) one bra shell pair at a
+        time, without the whole pair matrix: yields (rows, V[rows]) for every
+        bra shell pair AB of ``bra_pairs`` (all if None), from the integral
+        rows of AB's function pairs against the ket shell pairs the screening
+        keeps for AB (Eq. SchwarzDen).  For a fixed AB the rule
+        Q_AB (Q_CD Dmax_CD) >= tau keeps exactly the kets whose weight
+        w_CD = Q_CD Dmax_CD is at least tau / Q_AB, a leading run of the kets
+        in w order, so the contraction runs over the density rows of that run
+        (asserted below).  V[rows] is [n, ncol] (Coulomb), [n, 3, ncol]
+        (Gaunt, one slice per J) or [n, 3, ncol] (gauge: V^I = sum_J K_IJ D^J)."""
+        cls = 0 if block == "coulomb" else 1
+        mask = self.mask(block)
+        key = "order%d" % cls
+        if key not in self._cache:
+            Q, Dm = self._cache["Q%d" % cls], self._cache["Dmax%d" % cls]
+            _, _, sp = self.ob.pairs(cls)
+            order = np.argsort(-(Q * Dm)[sp], kind="stable")     # function-pair columns, w descending
+            self._cache[key] = (order, self.density(block)[order])
+        order, Dw = self._cache[key]
+        _, _, sp = self.ob.pairs(cls)
+        kernel = 2 if block == "gauge" else 0
+        todo = range(self.ob.n_shell_pairs(cls)) if bra_pairs is None else bra_pairs
+        for p in todo:
+            keep = mask[p]
+            kept = keep[sp[order]]
+            n = int(kept.sum())
+            assert kept[:n].all(), "screening kept set is not a leading run in w order"
+            if n == 0:
+                continue
+            rows, G = self.ob.shell_pair_rows(cls, kernel, p, keep)
+            if block == "coulomb":
+                yield rows, G[:, order[:n]] @ Dw[:n]
+            elif block == "gaunt":
+                Gk = G[:, order[:n]]
+                yield rows, np.stack([Gk @ Dw[:n, J] for J in range(3)], axis=1)
+            else:
+                Vr = np.zeros((rows.shape[0], 3, Dw.shape[-1]))
+                for ij, (I, J) in enumerate(IJ6):
+                    Kk = G[:, ij][:, order[:n]]
+                    Vr[:, I] += Kk @ Dw[:n, J]
+                    if I != J:
+                        Vr[:, J] += Kk @ Dw[:n, I]
+                yield rows, Vr
+
+    def V_streamed(self, block, progress=None):
+        """The whole V of V_rows_streamed, [M, ncol] or [M, 3, ncol]."""
+        V = np.zeros(self.density(block).shape)
+        n = self.ob.n_shell_pairs(0 if block == "coulomb" else 1)
+        for i, (rows, Vr) in enumerate(self.V_rows_streamed(block)):
+            V[rows] = Vr
+            if progress and i % 200 == 0:
+                progress(i, n)
+        return V
+
+    def second_half_rows(self, block, rows, Vr):
+        """The contribution D[rows]^T V[rows] of some bra rows to O = D^T V
+        (Eq. secondhalf; O is the sum over all bra rows)."""
+        D = self.density(block)
+        if block == "coulomb":
+            return D[rows].T @ Vr
+        return sum(D[rows, J, :].T @ Vr[:, J, :] for J in range(3))
+
+    def packed_full_streamed(self, block, progress=None):
+        """O = D^T V with V from V_streamed: the same matrix as packed_full
+        (to rounding), within memory O(M ncol)."""
+        V = self.V_streamed(block, progress=progress)
+        D = self.density(block)
+        if block == "coulomb":
+            return D.T @ V
+        return sum(D[:, J, :].T @ V[:, J, :] for J in range(3))
+
+    def packed_streamed(self, block, progress=None):
+        return pack_canonical(self.packed_full_streamed(block, progress), self.nKa)
 
     # MO-driven route (Sec. 3.3) ----------------------------------------------
     def _n_parts(self):

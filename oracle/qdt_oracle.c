@@ -30,6 +30,9 @@
  */
 #include <math.h>
 #include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <string.h>
 
 #define OR_MAXLT 18          /* max total order of a triple table            */
@@ -632,6 +635,61 @@ void or_pair_rows(void *h, int cls, int kernel, long nrows, const long *rows, do
     free(need); free(sp);
 }
 
+/*
+ * Row-streamed form of the pair matrix for one bra shell pair p of a class:
+ * the rows of its stored function pairs (fa major, fb minor), computed only
+ * against the ket shell pairs q with keep[q] != 0 -- the shell quartets that
+ * the screening of Eq. SchwarzDen keeps; the columns of the other ket shell
+ * pairs stay zero.  rows_out[r] receives the global pair index of row r,
+ * out[r][k][col] the value (k < 6 components for kernel 2, else 1); out holds
+ * nfunc_A * nfunc_B * ncomp * M doubles.  Returns the number of rows.
+ */
+long or_shell_pair_rows(void *h, int cls, int kernel, int p, const unsigned char *keep, long *rows_out,
+                        double *out)
+{
+    OrBasis *B = (OrBasis *)h;
+    SPair *sp;
+    int nsp = shell_pairs(B, cls, &sp);
+    long M = or_npairs(h, cls);
+    int ncomp = kernel == 2 ? 6 : 1;
+    const OrShell *A = &B->sh[sp[p].sa], *Bb = &B->sh[sp[p].sb];
+    int na = A->nfunc, nb = Bb->nfunc;
+    int *rl = (int *)malloc(sizeof(int) * na * nb);
+    long nrows = 0;
+    for (int fa = 0; fa < na; ++fa)
+        for (int fb = 0; fb < nb; ++fb) {
+            long g = pair_index(B, cls, sp[p].sa, sp[p].sb, fa, fb);
+            rl[fa * nb + fb] = g < 0 ? -1 : (int)nrows;
+            if (g >= 0) rows_out[nrows++] = g;
+        }
+    memset(out, 0, sizeof(double) * (size_t)nrows * ncomp * M);
+#pragma omp parallel for schedule(dynamic)
+    for (int q = 0; q < nsp; ++q) {
+        if (!keep[q]) continue;
+        const OrShell *Cc = &B->sh[sp[q].sa], *Dd = &B->sh[sp[q].sb];
+        int nc = Cc->nfunc, nd = Dd->nfunc;
+        size_t blk = (size_t)na * nb * nc * nd;
+        double *buf = (double *)malloc(sizeof(double) * blk * ncomp);
+        or_shell_block(h, kernel == 2 ? 2 : 0, sp[p].sa, sp[p].sb, sp[q].sa, sp[q].sb, buf);
+        for (int fa = 0; fa < na; ++fa)
+            for (int fb = 0; fb < nb; ++fb) {
+                int r = rl[fa * nb + fb];
+                if (r < 0) continue;
+                for (int fc = 0; fc < nc; ++fc)
+                    for (int fd = 0; fd < nd; ++fd) {
+                        long col = pair_index(B, cls, sp[q].sa, sp[q].sb, fc, fd);
+                        if (col < 0) continue;
+                        for (int k = 0; k < ncomp; ++k)
+                            out[((size_t)r * ncomp + k) * M + col] =
+                                buf[k * blk + ((size_t)(fa * nb + fb) * nc + fc) * nd + fd];
+                    }
+            }
+        free(buf);
+    }
+    free(rl); free(sp);
+    return nrows;
+}
+
 /* Full pair matrix: cls 0 -> [M][M]; cls 1 kernel 0 -> [M][M];
    cls 1 kernel 2 -> [6][M][M] (note the component-major layout). */
 void or_pair_matrix(void *h, int cls, int kernel, double *out)
@@ -744,4 +802,14 @@ void or_overlap_block(void *h, int sa, int sb, double *out)
                     out[X->ent_f[ea] * nb + Y->ent_f[eb]] += v;
                 }
         }
+}
+
+/* Threads of the OpenMP loops above (timing on a given number of host cores). */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
