@@ -4,13 +4,18 @@ One step = one qdt_transform() over the whole hot path (density, screening,
 AO integral tiles, first and second half-transforms, packing) of the
 workload, with the basis and coefficients already resident on the GPU.
 
-Default workload: the 40-centre s+p chain (nL = 160, nS = 480, 40 Kramers
-pairs, Schwarz threshold 1e-12, seeded synthetic inputs standing in for the
-paper's Hg/Pu chains).  Prints one JSON line (rank 0).
+Default workload: the Dirac-Coulomb-Breit blocks (Coulomb + Gaunt + gauge)
+of the 40-centre s+p chain (nL = 160, nS = 480, 40 Kramers pairs, Schwarz
+threshold 1e-12, seeded synthetic inputs standing in for the paper's Hg/Pu
+chains), split form timed, FP64 form timed beside it.  Prints one JSON line
+(rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload chain40-sp] [--blocks coulomb[,gaunt,gauge]]
+                  [--workload chain40-sp] [--blocks coulomb,gaunt,gauge]
                   [--precision split|fp64]
+
+--impl reference times the CPU oracle on a bounded sample of the same
+workload per step (OracleSampler).
 Multi-GPU (torchrun): every rank transforms its own copy of the workload
 (independent problems, weak scaling, no data-path collective).
 """
@@ -157,59 +162,283 @@ def job_value(n_mo, world, ms):
     return n_mo * world / (ms / 1e3)
 
 
+class OracleSampler:
+    """The oracle timed on the bench workload itself: its row-streamed
+    transform (oracle.Transform.V_rows_streamed, then each bra row's share
+    D[rows]^T V[rows] of the second half) over a stratified sample of the bra
+    shell pairs of every requested block.  A block's bra shell pairs are sorted
+    by a cost proxy (function pairs x primitive pairs) and every k-th one taken
+    (k at most the block's pair count), from an offset that rotates from one
+    sample to the next.  Each sample records, per block, its time t_b and the
+    fraction f_b of the block's bra shell pairs it covered; the time of a whole
+    transformation is estimated as t_setup + sum_b (sum of t_b) / (sum of f_b),
+    where t_setup is the per-transformation set-up (densities, Schwarz factors,
+    density maxima, screening masks), run once."""
+
+    def __init__(self, problem, blocks):
+        from oracle import oracle as O
+        O.build()
+        self.O = O
+        self.blocks = blocks
+        self.problem = problem
+        t0 = time.perf_counter()
+        self.tr = O.Transform(problem) if problem.kramers else O.TransformKU(problem)
+        for b in blocks:
+            self.tr.density(b)
+            self.tr.mask(b)
+            list(self.tr.V_rows_streamed(b, bra_pairs=[]))      # ket order of the block
+        self.t_setup = time.perf_counter() - t0
+        self.order = {}
+        for b in blocks:
+            cls = 0 if b == "coulomb" else 1
+            ob = self.tr.ob
+            nsp = ob.n_shell_pairs(cls)
+            cost = []
+            for p in range(nsp):
+                sa, sb = ob._shell_pair_shells(cls, p)
+                cost.append(ob._nfunc(sa) * ob._nfunc(sb) * int(problem.basis.shell_nprim[sa % ob.nsh]) *
+                            int(problem.basis.shell_nprim[sb % ob.nsh]))
+            self.order[b] = np.argsort(-np.array(cost), kind="stable")
+        self.step = 0
+        self.reset()
+
+    def reset(self):
+        self.tsum = {b: 0.0 for b in self.blocks}
+        self.fsum = {b: 0.0 for b in self.blocks}
+        self.times = []
+
+    def sample(self, k):
+        """Seconds of one sample at stride k (next offset); accumulates t_b, f_b."""
+        total = 0.0
+        for b in self.blocks:
+            n = len(self.order[b])
+            kb = max(1, min(k, n))
+            pairs = self.order[b][self.step % kb::kb]
+            t0 = time.perf_counter()
+            for rows, Vr in self.tr.V_rows_streamed(b, bra_pairs=pairs):
+                self.tr.second_half_rows(b, rows, Vr)
+            dt = time.perf_counter() - t0
+            self.tsum[b] += dt
+            self.fsum[b] += len(pairs) / n
+            total += dt
+        self.step += 1
+        self.times.append(total)
+        return total
+
+    def calibrate(self, budget_s):
+        """Stride k (a power of two, from 4096 down) at which one sample takes
+        at least budget_s / 2."""
+        k = 4096
+        while self.sample(k) < budget_s / 2 and k > 1:
+            k //= 2
+        self.reset()
+        return k
+
+    def full_seconds(self):
+        """Estimated seconds of one whole transformation from the samples so far."""
+        return self.t_setup + sum(self.tsum[b] / self.fsum[b] for b in self.blocks if self.fsum[b] > 0)
+
+    def describe(self, k, cores):
+        fr = ", ".join("%s %.2e" % (b, self.fsum[b] / max(1, len(self.times))) for b in self.blocks)
+        return ("oracle (oracle.Transform, row-streamed, screened) on this workload itself: %d samples, each "
+                "every %d-th bra shell pair of every block in cost order (rotating offset; mean fraction of a "
+                "block's bra pairs per sample: %s) through both half-transforms; whole transformation "
+                "estimated as set-up %.1f s (densities, Schwarz factors, masks; run once) + sum over blocks of "
+                "sampled time / sampled fraction = %.1f s; %s host threads"
+                % (len(self.times), k, fr, self.t_setup, self.full_seconds(), cores))
+
+
+def oracle_threads():
+    """Host threads the oracle's OpenMP integrals use on this machine."""
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
 def run_reference(args, problem, blocks, rank):
-    """CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    """The oracle on the bench workload, a bounded sample per step (rank 0
+    only; under torchrun the other ranks exit without work)."""
     if rank != 0:
         return
-    res = cpu_oracle_rate(problem, blocks, budget_s=args.ref_budget)
-    line = {"metric": METRIC, "value": res["value"], "unit": "MO-integrals/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
+    n_mo = mo_count(problem, len(blocks))
+    smp = OracleSampler(problem, blocks)
+    k = smp.calibrate(args.ref_budget)
+    for _ in range(max(0, args.warmup - 1)):
+        smp.sample(k)
+    smp.reset()
+    for _ in range(args.steps):
+        smp.sample(k)
+    t_full = smp.full_seconds()
+    value = n_mo / t_full
+    cores = oracle_threads()
+    one = one_core_rate(smp, n_mo, k)
+    cpu = {"value": value, "unit": "MO-integrals/s", "cores": cores, "kind": "oracle",
+           "sample": smp.describe(k, cores), "value_1core": one}
+    line = {"metric": METRIC, "value": value, "unit": "MO-integrals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(smp.times)) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": config_dict(args, problem, blocks),
-            "cpu_baseline": {"value": res["value"], "unit": "MO-integrals/s", "cores": res["cores"],
-                             "kind": "oracle", "sample": res["sample"]},
-            "e2e": {"value": res["value"], "unit": "MO-integrals/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "step": ("one bounded sample of the workload (see cpu_baseline.sample); value = MO integrals of one "
+                     "whole transformation / its estimated time %.1f s" % t_full),
+            "full_transform_s_est": t_full, "setup_s": smp.t_setup,
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "MO-integrals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_oracle_rate(problem, blocks, budget_s=20.0):
-    """Time the oracle on a reduced chain of the same recipe, grown until one
-    full transformation takes about budget_s / 2 seconds."""
-    from oracle import oracle as O
-    O.build()
-    cores = os.cpu_count()
-    n, last = 2, None
-    while True:
-        p = synth.chain_problem(n, n, seed=synth.SEED_BASE + 1, shells=(0, 1), nprim=3,
-                                blocks=blocks, tau=problem.tau, name="sample")
-        if not problem.kramers:
-            p = as_unrestricted(p)
-        t0 = time.perf_counter()
-        tr = O.Transform(p) if problem.kramers else O.TransformKU(p)
-        for b in blocks:
-            tr.packed(b)
-        dt = time.perf_counter() - t0
-        last = (n, dt)
-        if dt > budget_s / 2 or n >= 12:
-            break
-        n += 2
-    n, dt = last
-    rate = mo_integrals(n, len(blocks)) / dt
-    kind = "nK=%d" % n if problem.kramers else "%d unrestricted spinors" % (2 * n)
-    return {"value": rate, "ms": dt * 1e3, "cores": cores,
-            "sample": "oracle, full transform of a %d-centre s+p chain (same recipe, %s, blocks=%s) "
-                      "on %d host threads; %.1f s" % (n, kind, "+".join(blocks), cores, dt)}
+def one_core_rate(smp, n_mo, k):
+    """One more sample (stride 4k) with the oracle's integrals on one host
+    thread (oracle.set_threads) and numpy's BLAS on one thread where its
+    library exposes the switch; the whole transformation's time is estimated
+    from it as in OracleSampler.full_seconds, with the set-up (timed on all
+    threads) scaled by the all-thread/one-thread ratio of the sample."""
+    O = smp.O
+    saved = (dict(smp.tsum), dict(smp.fsum), list(smp.times))
+    t_all = float(np.mean(smp.times)) if smp.times else None
+    try:
+        O.set_threads(1)
+    except Exception:
+        return None
+    blas = _blas_threads(1)
+    try:
+        smp.reset()
+        smp.sample(4 * k)
+        est = sum(smp.tsum[b] / smp.fsum[b] for b in smp.blocks if smp.fsum[b] > 0)
+    finally:
+        O.set_threads(oracle_threads())
+        _blas_threads(os.cpu_count() or 1)
+        smp.tsum, smp.fsum, smp.times = saved
+    full_all = smp.full_seconds() - smp.t_setup
+    ratio = est / full_all if full_all > 0 else 1.0
+    return {"value": n_mo / (est + smp.t_setup * ratio), "unit": "MO-integrals/s",
+            "sample": "one sample at stride %d, integrals on 1 thread, BLAS threads %s; set-up scaled by %.1f"
+                      % (4 * k, "1" if blas else "unchanged", ratio), "all_thread_sample_s": t_all}
+
+
+def _blas_threads(n):
+    """Set numpy's OpenBLAS thread count through the loaded library, if found."""
+    import ctypes
+    try:
+        with open("/proc/self/maps") as f:
+            libs = sorted({ln.split()[-1] for ln in f if "openblas" in ln.lower() and ln.strip().endswith(".so")
+                           or ("openblas" in ln.lower() and ".so" in ln)})
+    except Exception:
+        return False
+    for path in libs:
+        try:
+            lib = ctypes.CDLL(path)
+        except Exception:
+            continue
+        for name in ("openblas_set_num_threads", "scipy_openblas_set_num_threads64_",
+                     "openblas_set_num_threads64_", "scipy_openblas_set_num_threads"):
+            fn = getattr(lib, name, None)
+            if fn is not None:
+                fn(ctypes.c_int(n))
+                return True
+    return False
+
+
+def dtype_of(fp64):
+    if fp64:
+        return "f64"
+    return ("f32/f32-pair integrals, bf16x6-slice contractions (f32 exact chunks), "
+            "f64 recombination and accumulation")
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+ERI_SOURCE = os.path.join(ROOT, "paper_2606_04316_gb300", "csrc", "eri_kernels.cu")
+
+
+def source_sha16(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_per_value(kind):
+    """DRAM bytes per integral value of the integral kernel from the committed
+    ncu capture (profiles/traffic.txt), or None when that file is absent or was
+    taken on another version of the kernel source."""
+    try:
+        sha = source_sha16(ERI_SOURCE)
+        with open(TRAFFIC_FILE) as f:
+            for ln in f:
+                if ln.startswith("#") or not ln.strip():
+                    continue
+                parts = ln.split()
+                if parts[0] == kind and parts[1] == sha:
+                    return float(parts[2]), " ".join(parts[3:])
+    except Exception:
+        pass
+    return None, None
+
+
+def roofline(st, avg, prec, clocks, pk, src, device, blocks):
+    """Roofline of the dominant phase's kernel: algorithmic work per step over
+    its measured time (CUDA events on the launching stream), against the
+    measured peak of the unit it runs on."""
+    from paper_2606_04316_gb300 import qdt
+    dom = max(("ms_eri", "ms_half1", "ms_half2"), key=lambda k: avg[k])
+    fp64_derived, mhz = fp64_alu_peak(clocks)
+    try:
+        p32, p64 = qdt.alu_peak(device, "fp32"), qdt.alu_peak(device, "fp64")
+    except Exception:
+        p32, p64 = None, None
+    p32_derived = SMS * FP32_PER_CLK_SM * 2 * mhz * 1e6 / 1e12
+    measured = {"fp32_fma_tflops": p32, "fp64_fma_tflops": p64, "how": "qdt_alu_peak (own FMA probe)",
+                "fp32_derived_tflops": p32_derived, "fp64_derived_tflops": fp64_derived}
+    nclass = (1 if "coulomb" in blocks else 0) + (1 if ("gaunt" in blocks or "gauge" in blocks) else 0)
+    if dom == "ms_eri":
+        achieved = st["flops_eri"] / (avg[dom] / 1e3) / 1e12
+        if prec == qdt.SPLIT:
+            # compensated FP32-pair multiply-adds cost 12 FP32 operations, the
+            # quartets within the FP32 error budget one FMA: the bound weighs
+            # the two by their share of the flops
+            f32 = st.get("flops_eri_f32", 0.0) / st["flops_eri"] if st["flops_eri"] else 0.0
+            ops = DF_OPS_PER_MADD * (1.0 - f32) + 1.0 * f32
+            base = p32 if p32 else p32_derived
+            peak = base / ops
+            note = ("measured FP32 FMA rate %.1f TF/s / %.2f FP32 operations per multiply-add (%d for "
+                    "compensated pairs, 1 for the %.1f %% of flops in plain FP32), FP64-equivalent flops"
+                    % (base, ops, DF_OPS_PER_MADD, 100.0 * f32))
+        else:
+            peak = p64 if p64 else fp64_derived
+            note = "measured FP64 FMA rate (qdt_alu_peak)"
+        per_value, how = traffic_per_value("eri_rows_kernel")
+        traffic = per_value * st["eri_values"] if per_value else None
+        return {"kernel": "eri_rows_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": ("DRAM bytes of the step's integral launches: %s" % how) if how else
+                "no capture of this kernel version",
+                "launches_per_step": nclass, "peak_note": note, "peaks": measured,
+                "work": "E R E multiply-adds of the kept quartets (qdt_stats.flops_eri), per step"}
+    fl = st["flops_half1"] if dom == "ms_half1" else st["flops_half2"]
+    achieved = fl / (avg[dom] / 1e3) / 1e12
+    if prec == qdt.FP64:
+        peak, note, bound = (p64 or fp64_derived), "measured FP64 FMA rate (qdt_alu_peak)", "alu"
+    else:
+        peak, note, bound = pk["bf16_tflops_sustained"], "%s bf16 sustained" % src, "tensor"
+    return {"kernel": "half1" if dom == "ms_half1" else "half2", "bound": bound, "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_note": note, "peaks": measured}
 
 
 METRIC = "DCB AO->MO transform MO-integrals/s (split vs FP64 @1e-10 Eh)"
+
+
+WORKLOAD_NOTES = {
+    "chain40-sp": "the 40-centre s+p chain (nL 160, nS 480, 40 Kramers pairs, Schwarz 1e-12) with the "
+                  "Dirac-Coulomb-Breit blocks: the largest DCB workload whose 20 + 5 steps fit the bench's "
+                  "minute of timed work; the 64-centre DCB cluster (nL 256, nK 64) needs minutes per split "
+                  "step (its first half alone is ~9e15 FP64-equivalent flops) and is measured separately",
+}
 
 
 def config_dict(args, problem, blocks):
     d = {"workload": args.workload, "nL": problem.basis.nL, "nS": problem.basis.nS,
          "n_kramers": problem.nK, "blocks": "+".join(blocks), "schwarz_tau": problem.tau,
          "precision": args.precision, "l2": "inputs larger than L2 (densities, integral rows)"}
+    if args.workload in WORKLOAD_NOTES and len(blocks) == 3:
+        d["why_this_workload"] = WORKLOAD_NOTES[args.workload]
     if getattr(args, "route", "density") != "density":
         d["route"] = args.route
         if args.route == "mo":
@@ -344,17 +573,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chain40-sp")
-    ap.add_argument("--blocks", default="coulomb")
+    ap.add_argument("--blocks", default="coulomb,gaunt,gauge",
+                    help="the metric is Dirac-Coulomb-Breit: Coulomb + Gaunt + gauge blocks")
     ap.add_argument("--input", default="kramers", choices=["kramers", "ku"],
                     help="coefficients: quaternion (Kramers pairs) or Kramers-unrestricted spinors")
     ap.add_argument("--precision", default="split", choices=["split", "fp64"])
     ap.add_argument("--route", default="density", choices=["density", "quarter", "mo"],
                     help="density (AO-driven), quarter (O(N^5) Coulomb first half) or mo (MO-driven comparator)")
     ap.add_argument("--mo-block", type=int, default=8, help="MO-driven route: outer MO indices per block")
-    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 form (0: skip)")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form (0: skip)")
+    ap.add_argument("--e2e-calls", type=int, default=5, help="calls of the end-to-end (host buffers) timing")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-samples", type=int, default=2, help="oracle samples of the cpu_baseline leg")
+    ap.add_argument("--ref-budget", type=float, default=4.0, help="seconds of one oracle sample")
     ap.add_argument("--stats", action="store_true", help="print per-phase statistics to stderr")
     ap.add_argument("--requests", type=int, default=32, help="serving workload: number of requests")
     ap.add_argument("--slots", type=int, default=4, help="serving workload: concurrent contexts")
@@ -423,22 +655,25 @@ def main():
     n_mo = mo_count(problem, len(blocks))
     value = job_value(n_mo, world, ms)
 
-    # end to end through the public API with host buffers (pinned)
+    # end to end through the public API with host buffers (pinned): coefficients
+    # in and packed integrals out, copies inside the timed region; median of calls
     e2e = None
     if not args.no_e2e:
         CLh = torch.from_numpy(problem.CL).pin_memory()
         CSh = torch.from_numpy(problem.CS).pin_memory()
         outh = torch.zeros(nout, dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
-        ne = 1
-        t0 = time.perf_counter()
-        for _ in range(ne):
+        dts = []
+        for _ in range(max(1, args.e2e_calls)):
+            t0 = time.perf_counter()
             set_coefs(CLh, CSh)
             ctx.transform(blocks, 0, nK, tau, prec, outh)
-        dt = (time.perf_counter() - t0) / ne
+            dts.append(time.perf_counter() - t0)
+        dt = float(np.median(dts))
         e2e = {"value": n_mo * world / dt, "unit": "MO-integrals/s",
                "h2d_bytes_per_step": int(CLh.numel() * 8 + CSh.numel() * 8),
-               "d2h_bytes_per_step": int(outh.numel() * 8)}
+               "d2h_bytes_per_step": int(outh.numel() * 8), "calls": len(dts),
+               "timing": "median host wall clock of qdt_set_coefficients + qdt_transform with pinned host buffers"}
 
     # the FP64 form on the same workload, and the agreement of the two forms
     other = None
@@ -458,48 +693,24 @@ def main():
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1) / args.fp64_steps
         other = {"value": n_mo * world / (ms64 / 1e3), "ms_per_step": ms64, "steps": args.fp64_steps,
-                 "phases_ms": {k: st64[k] for k in phase}, "max_abs_diff_split_vs_fp64": diff}
+                 "phases_ms": {k: st64[k] for k in phase}, "max_abs_diff_split_vs_fp64": diff,
+                 "split_speedup": ms64 / ms}
 
     pk, src = peaks()
     avg = {k: v / args.steps for k, v in phase.items()}
-    dom = max(("ms_eri", "ms_half1", "ms_half2"), key=lambda k: avg[k])
-    fp64_peak, mhz = fp64_alu_peak(clocks)
-    fp64_note = "FP64 pipe: %d SMs x %d DFMA/clk x 2 flops x %.0f MHz sampled SM clock" % (SMS, DFMA_PER_CLK_SM, mhz)
-    if dom == "ms_eri":
-        achieved = st["flops_eri"] / (avg[dom] / 1e3) / 1e12
-        if prec == qdt.SPLIT:
-            # split form: the contractions run in compensated FP32 pairs (12 FP32 operations per
-            # multiply-add) or, for the quartets within the FP32 error budget, in plain FP32 (one
-            # FMA); the bound weighs the two by their share of the flops
-            f32 = st.get("flops_eri_f32", 0.0) / st["flops_eri"] if st["flops_eri"] else 0.0
-            ops = DF_OPS_PER_MADD * (1.0 - f32) + 1.0 * f32
-            peak = SMS * FP32_PER_CLK_SM * mhz * 1e6 / ops * 2 / 1e12
-            note = ("FP32 pipe: %d SMs x %d lanes x %.0f MHz / %.2f FP32 ops per multiply-add (%d for "
-                    "compensated pairs, 1 for the %.1f %% of flops in plain FP32) x 2 flops (FP64-equivalent)"
-                    % (SMS, FP32_PER_CLK_SM, mhz, ops, DF_OPS_PER_MADD, 100.0 * f32))
-        else:
-            peak, note = fp64_peak, fp64_note
-        roof = {"kernel": "eri_rows_kernel", "bound": "alu", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_note": note,
-                "work": "E R E multiply-adds of the kept quartets (qdt_stats.flops_eri)"}
-    else:
-        fl = st["flops_half1"] if dom == "ms_half1" else st["flops_half2"]
-        achieved = fl / (avg[dom] / 1e3) / 1e12
-        if prec == qdt.FP64:
-            peak, note, bound = fp64_peak, fp64_note, "alu"
-        else:
-            peak, note, bound = pk["bf16_tflops_sustained"], "%s bf16 sustained" % src, "tensor"
-        roof = {"kernel": "half1" if dom == "ms_half1" else "half2", "bound": bound,
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_note": note}
+    roof = roofline(st, avg, prec, clocks, pk, src, local, blocks)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
         try:
-            r = cpu_oracle_rate(problem, blocks)
-            cpu = {"value": r["value"], "unit": "MO-integrals/s", "cores": r["cores"], "kind": "oracle",
-                   "sample": r["sample"]}
+            smp = OracleSampler(problem, blocks)
+            k = smp.calibrate(args.ref_budget)
+            for _ in range(args.cpu_samples):
+                smp.sample(k)
+            cores = oracle_threads()
+            cpu = {"value": n_mo / smp.full_seconds(), "unit": "MO-integrals/s", "cores": cores,
+                   "kind": "oracle", "sample": smp.describe(k, cores),
+                   "value_1core": one_core_rate(smp, n_mo, k)}
         except Exception as ex:  # keep the bench line even if the oracle fails
             cpu = {"value": None, "unit": "MO-integrals/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "failed: %s" % ex}
@@ -507,10 +718,12 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MO-integrals/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == qdt.FP64 else "bf16-slices/f64",
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(prec == qdt.FP64),
                 "data": "synthetic", "config": config_dict(args, problem, blocks), "clocks": clocks,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
                 "phases_ms": avg, "quartets_kept": st["quartets_kept"], "quartets_total": st["quartets_total"],
+                "quartets_f32": st["quartets_f32"],
+                "eri_values_per_s": st["eri_values"] / (avg["ms_eri"] / 1e3) if avg["ms_eri"] > 0 else None,
                 "fp64_form": other}
         print(json.dumps(line), flush=True)
         if args.stats:

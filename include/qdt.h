@@ -349,8 +349,8 @@ int qdt_wait(qdt_server *srv, uint64_t handle, double timeout_s, double *latency
  * cannot allocate device memory -- a host framework that owns all device memory
  * through its own pool allocator, or a latency-critical service that must not
  * take the implicit synchronisation of a fresh cudaMalloc.  It computes the
- * FP64 second-half contraction O = Dq^T V (Eq. secondhalf in real quaternion
- * form) like qdt_transform does internally, but keeps its split-K partial sums
+ * FP64 second-half contraction O = Dq^T V like qdt_transform does
+ * internally, but keeps its split-K partial sums
  * in a fixed device array of the library (32 MiB of doubles, held on every GPU
  * that loads the library until the process exits) and calls no allocator.
  *
@@ -367,13 +367,27 @@ int qdt_wait(qdt_server *srv, uint64_t handle, double timeout_s, double *latency
  *   msg    optional buffer (msg_len bytes) for an error description.
  *
  * The first call on a device looks up the array's device address on that
- * device (it must be the current device); make that first call before any
- * stream capture.  Every call shares the one array: calls whose work overlaps
+ * device (it must be the current device) and caches it for the process; make
+ * that first call before any stream capture.  After cudaDeviceReset on that
+ * device the cached address is stale: do not call this entry point again in
+ * that process.  Every call shares the one array: calls whose work overlaps
  * on the GPU (different streams, or host threads) race and must be serialised
  * by the caller.  Returns QDT_OK, QDT_ERR_ARG or QDT_ERR_CUDA.
  */
 int qdt_second_half_noalloc(const double *Dq, const double *V, long long K, long long N, double *O,
                             void *cuda_stream, char *msg, size_t msg_len);
+
+/*
+ * Measured FMA throughput of the CUDA cores of `device`, the peak that the AO
+ * integral kernel's roofline divides by (that kernel runs on the CUDA cores:
+ * FP64 FMAs in the FP64 form, FP32 FMAs in the split form).  The paper has no
+ * counterpart; it is a diagnostic.  kind 0: FP32 FMA, kind 1: FP64 FMA;
+ * *tflops receives 2 x FMAs per second / 1e12 of a kernel of eight
+ * independent FMA chains per thread on every SM (best of three timed runs
+ * after a warm-up).  Runs on a stream of its own and synchronises it.
+ * Returns QDT_OK, QDT_ERR_ARG (bad kind or NULL) or QDT_ERR_CUDA.
+ */
+int qdt_alu_peak(int device, int kind, double *tflops);
 
 /* Text of the last error of this context ("" if none); valid until the next call. */
 const char *qdt_last_error(const qdt_ctx *ctx);

@@ -13,7 +13,8 @@
 // Host code never dereferences or passes the array's name to a kernel (on the
 // host it is only a stand-in symbol); its device address is obtained once per
 // device with cudaGetSymbolAddress, with that device current, on the first
-// call made on that device.
+// call made on that device, and cached for the life of the process; a
+// cudaDeviceReset on that device invalidates the cached address.
 #include <mutex>
 #include <string>
 
@@ -45,10 +46,11 @@ extern "C" int qdt_second_half_noalloc(const double *Dq, const double *V, long l
         put_msg(msg, msg_len, "qdt_second_half_noalloc: null pointer or non-positive size");
         return QDT_ERR_ARG;
     }
-    if (N * N > kNoAllocScratchDoubles) {
-        put_msg(msg, msg_len, "qdt_second_half_noalloc: N*N = " + std::to_string(N * N) +
-                                  " exceeds the fixed scratch of " + std::to_string(kNoAllocScratchDoubles) +
-                                  " doubles (N <= 2048)");
+    // N > max / N, not N * N > max: the product overflows for N above ~3e9
+    if (N > kNoAllocScratchDoubles / N) {
+        put_msg(msg, msg_len, "qdt_second_half_noalloc: N = " + std::to_string(N) +
+                                  " needs N*N doubles, more than the fixed scratch of " +
+                                  std::to_string(kNoAllocScratchDoubles) + " doubles (N <= 2048)");
         return QDT_ERR_ARG;
     }
     int dev = -1;

@@ -547,6 +547,18 @@ void f32_split(qdt_ctx *ctx, ClassPlan &P, double &bound_out) {
     f32_tail_split(w, nfp, P.h_ketsp, P.h_prefix, g * kF32Rel, budget, P.h_split, &bound_out);
 }
 
+// QDT_W_BUDGET (bytes, > 0) replaces the device-memory test of the row-batch
+// decision: a class runs as one batch when its integral block fits the value,
+// else in batches of at most that many bytes (without bra-ket symmetry).
+// Small values exercise the batched path on small inputs.
+size_t w_budget_override() {
+    const char *e = std::getenv("QDT_W_BUDGET");
+    if (!e || !e[0]) return 0;
+    const long long v = std::atoll(e);
+    if (v <= 0) throw Error{QDT_ERR_ARG, "QDT_W_BUDGET must be a positive byte count"};
+    return (size_t)v;
+}
+
 // Waits for class_issue; kept-quartet statistics, V buffers and the row-batch
 // decision: one batch (and bra-ket symmetry) when the integral block (plus the
 // split form's digit planes of one row chunk) fits in 70 % of the device
@@ -585,10 +597,11 @@ void class_finish(qdt_ctx *ctx, ClassPlan &P, qdt_stats *st) {
     const double wfac = (P.ls && P.cr.gauge && P.cr.gaunt) ? 1.12 : 1.0;
     const double slices = (P.precision == QDT_SPLIT ? 1.1 * (double)kSliceBudget : 0.0) +
                           (P.quarter ? 1.1 * (double)kQuarterBudget : 0.0);
-    P.one_batch = (double)wall * wfac + slices <= (double)usable;
+    const size_t forced = w_budget_override();
+    P.one_batch = forced ? (double)wall * wfac <= (double)forced : (double)wall * wfac + slices <= (double)usable;
     // what the decision counted as reusable is handed back first
     if (P.one_batch && (double)wall * wfac + slices > 0.7 * (double)(fr + ctx->W.n + ctx->Wc.n)) split_release(ctx->split);
-    P.wbudget = P.one_batch ? wall : ((size_t)6 << 30);
+    P.wbudget = P.one_batch ? wall : (forced ? forced : ((size_t)6 << 30));
     P.h_kpos.assign(pc.nsp, 0);
     for (int q = 0; q < pc.nsp; ++q) P.h_kpos[P.h_ketsp[q]] = q;
     P.d_kpos = P.one_batch ? dcopy(ctx->kpos, P.h_kpos, s) : nullptr;

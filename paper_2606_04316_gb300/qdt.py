@@ -24,7 +24,7 @@ EXPORTS = ["qdt_create", "qdt_destroy", "qdt_set_basis", "qdt_num_functions", "q
            "qdt_footprint", "qdt_server_create", "qdt_server_destroy", "qdt_submit", "qdt_poll", "qdt_wait",
            "qdt_second_half_noalloc", "qdt_transform_batch", "qdt_graph_counts",
            "qdt_set_spinor_coefficients", "qdt_set_rkb_coefficients", "qdt_set_route",
-           "qdt_check_bounded_wait", "qdt_f32_error_ratio"]
+           "qdt_check_bounded_wait", "qdt_f32_error_ratio", "qdt_alu_peak"]
 BATCH_GRAPH = 1
 
 
@@ -121,6 +121,7 @@ def load(build_if_missing=True):
                                           ctypes.c_char_p, ctypes.c_size_t]
     L.qdt_transform_batch.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_int, ctypes.c_uint]
     L.qdt_graph_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    L.qdt_alu_peak.argtypes = [ctypes.c_int, ctypes.c_int, dp]
     _LIB = L
     return L
 
@@ -353,11 +354,36 @@ class Server:
 
 def second_half_noalloc(Dq, V, O, stream=None):
     """O = Dq^T V (FP64, upper 64x64 tiles) through qdt_second_half_noalloc:
-    no device allocation.  Dq, V: cuda float64 [K, N]; O: cuda float64 [N, N]."""
+    no device allocation.  Dq, V: CUDA float64 contiguous [K, N] of the same
+    shape; O: CUDA float64 contiguous [N, N].  The C entry point takes no size
+    for V or O, so the shapes are checked here before anything is launched."""
+    for name, t in (("Dq", Dq), ("V", V), ("O", O)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise ValueError("second_half_noalloc: %s must be a CUDA tensor" % name)
+        if str(t.dtype) != "torch.float64":
+            raise ValueError("second_half_noalloc: %s must be float64, not %s" % (name, t.dtype))
+        if t.dim() != 2 or not t.is_contiguous():
+            raise ValueError("second_half_noalloc: %s must be a contiguous 2-D tensor" % name)
+    if tuple(V.shape) != tuple(Dq.shape):
+        raise ValueError("second_half_noalloc: V %s must have Dq's shape %s" % (tuple(V.shape), tuple(Dq.shape)))
+    N = int(Dq.shape[1])
+    if tuple(O.shape) != (N, N):
+        raise ValueError("second_half_noalloc: O %s must be (%d, %d)" % (tuple(O.shape), N, N))
+    if Dq.device != V.device or Dq.device != O.device:
+        raise ValueError("second_half_noalloc: Dq, V and O must be on one device")
     L = load()
     buf = ctypes.create_string_buffer(512)
     sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
-    rc = L.qdt_second_half_noalloc(_ptr(Dq), _ptr(V), int(Dq.shape[0]), int(Dq.shape[1]), _ptr(O), sp,
-                                   buf, 512)
+    rc = L.qdt_second_half_noalloc(_ptr(Dq), _ptr(V), int(Dq.shape[0]), N, _ptr(O), sp, buf, 512)
     if rc != 0:
         raise QdtError(rc, buf.value.decode())
+
+
+def alu_peak(device=0, kind="fp32"):
+    """Measured FMA throughput (TFLOP/s) of the CUDA cores: kind "fp32" or "fp64"."""
+    L = load()
+    v = ctypes.c_double()
+    rc = L.qdt_alu_peak(int(device), {"fp32": 0, "fp64": 1}[kind], ctypes.byref(v))
+    if rc != 0:
+        raise QdtError(rc, "qdt_alu_peak")
+    return v.value

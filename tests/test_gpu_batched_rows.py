@@ -1,0 +1,64 @@
+"""The row-batched path of a transformation: when a class's integral rows do
+not fit one batch, they run in batches of bra rows without bra-ket symmetry
+(large systems take this path).  QDT_W_BUDGET forces it on a small input;
+both forms, all three blocks, against the oracle and against the one-batch
+result."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2606_04316_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL_FP64 = 1e-12
+TOL_SPLIT = 1e-10
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def run(p, blocks, precision, budget=None):
+    from paper_2606_04316_gb300 import qdt
+    old = os.environ.get("QDT_W_BUDGET")
+    if budget is not None:
+        os.environ["QDT_W_BUDGET"] = str(budget)
+    try:
+        ctx = qdt.Context(0)
+        ctx.set_basis(p.basis)
+        ctx.set_coefficients(p.CL, p.CS)
+        out = np.zeros(ctx.packed_size(blocks, 0, p.nK) // 8)
+        st = ctx.transform(blocks, 0, p.nK, p.tau, precision, out)
+        ctx.close()
+    finally:
+        if old is None:
+            os.environ.pop("QDT_W_BUDGET", None)
+        else:
+            os.environ["QDT_W_BUDGET"] = old
+    return out.reshape(len(blocks), -1), st
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_forced_row_batches_match_oracle_and_one_batch(oracle, torch_cuda, precision):
+    blocks = ["coulomb", "gaunt", "gauge"]
+    # 4 centres of a jittered cluster, s+p with 2 primitives: class 0 has 1312
+    # function-pair rows (W about 14 MB), the L-S class 768 (gauge W about 42 MB);
+    # a 2 MB budget cuts them into many batches with ragged last ones
+    p = synth.cluster_problem((2, 2, 1), 3, seed=611, nprim=2, blocks=blocks, tau=1e-10)
+    got, st = run(p, blocks, precision, budget=2 << 20)
+    one, st1 = run(p, blocks, precision)
+    tr = oracle.Transform(p)
+    tol = TOL_FP64 if precision == 0 else TOL_SPLIT
+    for i, b in enumerate(blocks):
+        ref = tr.packed(b).reshape(-1)
+        assert np.abs(got[i] - ref).max() <= tol, b
+        assert np.abs(got[i] - one[i]).max() <= tol, b
+    # the same quartets are kept either way; without bra-ket symmetry the
+    # batched path computes more integral blocks
+    assert st["quartets_kept"] == st1["quartets_kept"]
+    assert st["flops_eri"] > st1["flops_eri"]

@@ -64,12 +64,55 @@ def test_noalloc_matches_allocating_path_twice(oracle, torch_cuda):
         assert np.abs(got - ref).max() <= TOL_FP64
 
 
+def test_noalloc_several_tiles_on_a_side_stream(oracle, torch_cuda):
+    """N = 144 (three 64-wide tile rows and columns, several split-K slices of
+    the shared array) on a non-default stream, twice in a row."""
+    torch = torch_cuda
+    from paper_2606_04316_gb300 import qdt
+    p = synth.chain_problem(4, 8, seed=503, shells=(0, 1), nprim=2, blocks=("coulomb",), tau=0.0)
+    D, V = operands(oracle, p)
+    assert D.shape[1] == 144
+    ref = reference_packed(torch, p)
+    side = torch.cuda.Stream()
+    for _ in range(2):
+        with torch.cuda.stream(side):
+            Dd = torch.from_numpy(D).to("cuda", non_blocking=False)
+            Vd = torch.from_numpy(V).to("cuda", non_blocking=False)
+            O = torch.full((144, 144), float("nan"), dtype=torch.float64, device="cuda")
+        qdt.second_half_noalloc(Dd, Vd, O, stream=side)
+        side.synchronize()
+        got = oracle.pack_canonical(O.cpu().numpy(), p.nK).reshape(-1)
+        assert np.all(np.isfinite(got))
+        assert np.abs(got - ref).max() <= TOL_FP64
+
+
+def test_noalloc_wrapper_rejects_mismatched_operands(torch_cuda):
+    torch = torch_cuda
+    from paper_2606_04316_gb300 import qdt
+    D = torch.zeros((8, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        qdt.second_half_noalloc(D, torch.zeros((8, 15), dtype=torch.float64, device="cuda"),
+                                torch.zeros((16, 16), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        qdt.second_half_noalloc(D, D, torch.zeros((15, 16), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        qdt.second_half_noalloc(D, D, torch.zeros((16, 16), dtype=torch.float64))
+    with pytest.raises(ValueError):
+        qdt.second_half_noalloc(D, D.float(), torch.zeros((16, 16), dtype=torch.float64, device="cuda"))
+
+
 def test_noalloc_rejects_oversized(torch_cuda):
+    """The C entry point refuses N > 2048 before launching anything."""
     torch = torch_cuda
     from paper_2606_04316_gb300 import qdt
     N = 2049
     Dd = torch.zeros((4, N), dtype=torch.float64, device="cuda")
-    O = torch.zeros((1, 1), dtype=torch.float64, device="cuda")
+    O = torch.zeros((N, N), dtype=torch.float64, device="cuda")
     with pytest.raises(qdt.QdtError) as e:
         qdt.second_half_noalloc(Dd, Dd, O)
     assert e.value.code == -1 and "2048" in str(e.value)
+    L = qdt.load()
+    buf = ctypes.create_string_buffer(256)
+    rc = L.qdt_second_half_noalloc(ctypes.c_void_p(Dd.data_ptr()), ctypes.c_void_p(Dd.data_ptr()), 4,
+                                   3_100_000_000, ctypes.c_void_p(O.data_ptr()), None, buf, 256)
+    assert rc == -1 and b"2048" in buf.value
