@@ -439,6 +439,8 @@ def config_dict(args, problem, blocks):
          "precision": args.precision, "l2": "inputs larger than L2 (densities, integral rows)"}
     if args.workload in WORKLOAD_NOTES and len(blocks) == 3:
         d["why_this_workload"] = WORKLOAD_NOTES[args.workload]
+    if getattr(args, "nk_active", 0) > 0 and args.nk_active < problem.nK:
+        d["active_range"] = [0, args.nk_active]
     if getattr(args, "route", "density") != "density":
         d["route"] = args.route
         if args.route == "mo":
@@ -450,16 +452,13 @@ def config_dict(args, problem, blocks):
     return d
 
 
-def run_serving(args):
-    """Request stream through the continuous-batching server (qdt_server_*):
-    seeded chain/cluster requests of different sizes, half Dirac-Coulomb and half
-    Dirac-Coulomb-Breit, Poisson arrivals at 0.8 x the capacity measured by a
-    sequential calibration pass; p50/p99 latency and MO-integrals/s."""
-    import torch
+def serve_stream(reqs, prec, slots, seed_offset=3):
+    """One request stream through the continuous-batching server: a sequential
+    calibration pass (one qdt_transform after another on one context), then the
+    same requests submitted on a seeded Poisson process at 0.8 x the calibrated
+    capacity.  Latency = completion - submission (= arrival).  Returns the
+    metrics and whether every result equals its sequential result."""
     from paper_2606_04316_gb300 import qdt
-    torch.cuda.set_device(0)
-    prec = qdt.SPLIT if args.precision == "split" else qdt.FP64
-    reqs = synth.serving_requests(args.requests, nl_range=(24, args.max_nl), nk_range=(8, args.max_nk))
     outs = []
     ctx = qdt.Context(0)
     t0 = time.perf_counter()
@@ -472,9 +471,9 @@ def run_serving(args):
     t_seq = time.perf_counter() - t0
     ctx.close()
     rate = 0.8 * len(reqs) / t_seq
-    rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 3))
+    rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + seed_offset))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
-    srv = qdt.Server(0, n_slots=args.slots)
+    srv = qdt.Server(0, n_slots=slots)
     handles, res = [], []
     start = time.perf_counter()
     for p, ta in zip(reqs, arrivals):
@@ -490,15 +489,42 @@ def run_serving(args):
     srv.close()
     same = all(np.array_equal(a, b) for a, b in zip(outs, res))
     n_mo = sum(mo_integrals(p.nK, len(p.blocks)) for p in reqs)
-    line = {"metric": "serving: p50/p99 request latency and MO-integrals/s (continuous batching)",
-            "value": n_mo / makespan, "unit": "MO-integrals/s", "n_gpus": 1, "higher_is_better": True,
+    return {"value": n_mo / makespan, "unit": "MO-integrals/s",
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "mean": float(np.mean(lat))},
-            "arrival_rate_per_s": rate, "calibration_sequential_s": t_seq, "makespan_s": makespan,
-            "requests": len(reqs), "slots": args.slots, "precision": args.precision,
-            "results_same_alone_and_in_mix": same, "data": "synthetic",
-            "config": {"workload": "serving", "nL": [24, args.max_nl], "nK": [8, args.max_nk],
-                       "blocks": "half coulomb, half coulomb+gaunt+gauge", "schwarz_tau": 1e-11}}
+                          "mean": float(np.mean(lat)), "max": float(np.max(lat))},
+            "arrival_rate_per_s": rate, "calibration_sequential_s": t_seq,
+            "sequential_value": n_mo / t_seq, "makespan_s": makespan, "requests": len(reqs),
+            "results_same_alone_and_in_mix": same}
+
+
+def run_serving(args):
+    """Request stream through the continuous-batching server (qdt_server_*):
+    seeded chain/cluster requests (nL 24..200, nK 8..48, half Dirac-Coulomb
+    and half Dirac-Coulomb-Breit, tau 1e-11), Poisson arrivals at 0.8 x the
+    capacity of a sequential calibration pass; p50/p99 latency and
+    MO-integrals/s in the split form over the whole stream, and both forms
+    side by side over its first --compare-prefix requests."""
+    import torch
+    from paper_2606_04316_gb300 import qdt
+    torch.cuda.set_device(0)
+    prec = qdt.SPLIT if args.precision == "split" else qdt.FP64
+    reqs = synth.serving_requests(args.requests, nl_range=(24, args.max_nl), nk_range=(8, args.max_nk))
+    main = serve_stream(reqs, prec, args.slots)
+    both = None
+    if args.compare_prefix > 0:
+        pre = reqs[:args.compare_prefix]
+        both = {"requests": len(pre),
+                "split": serve_stream(pre, qdt.SPLIT, args.slots, seed_offset=4),
+                "fp64": serve_stream(pre, qdt.FP64, args.slots, seed_offset=4)}
+        both["p99_fp64_over_split"] = both["fp64"]["latency_s"]["p99"] / both["split"]["latency_s"]["p99"]
+        both["throughput_split_over_fp64"] = both["split"]["value"] / both["fp64"]["value"]
+    line = {"metric": "serving: p50/p99 request latency and MO-integrals/s (continuous batching)",
+            "value": main["value"], "unit": "MO-integrals/s", "n_gpus": 1, "higher_is_better": True,
+            "latency_s": main["latency_s"], "precision": args.precision, "slots": args.slots,
+            "stream": main, "both_forms_on_prefix": both, "data": "synthetic",
+            "config": {"workload": "serving", "requests": len(reqs), "nL": [24, args.max_nl], "nK": [8, args.max_nk],
+                       "blocks": "half coulomb, half coulomb+gaunt+gauge", "schwarz_tau": 1e-11,
+                       "arrivals": "Poisson at 0.8 x the sequential capacity of each form"}}
     print(json.dumps(line), flush=True)
 
 
@@ -513,7 +539,8 @@ def run_batch(args):
     from paper_2606_04316_gb300 import qdt
     torch.cuda.set_device(0)
     prec = qdt.SPLIT if args.precision == "split" else qdt.FP64
-    reqs = synth.serving_requests(args.requests, nl_range=(24, args.max_nl), nk_range=(8, args.max_nk))
+    reqs = synth.serving_requests(args.batch_requests, nl_range=(24, args.batch_max_nl),
+                                  nk_range=(8, args.batch_max_nk))
     # graph replay needs a fixed screening outcome across passes: same inputs every pass
     ctxs, outs, jobs = [], [], []
     for p in reqs:
@@ -561,7 +588,7 @@ def run_batch(args):
             "max_abs_diff_vs_sequential": {"batch": diff_batch, "batch_graph": diff_graph},
             "graph_captures": caps, "graph_replays": reps, "requests": len(reqs), "precision": args.precision,
             "data": "synthetic", "timing": "host wall clock around synchronised passes",
-            "config": {"workload": "batch", "nL": [24, args.max_nl], "nK": [8, args.max_nk],
+            "config": {"workload": "batch", "nL": [24, args.batch_max_nl], "nK": [8, args.batch_max_nk],
                        "blocks": "half coulomb, half coulomb+gaunt+gauge", "schwarz_tau": 1e-11}}
     print(json.dumps(line), flush=True)
 
@@ -583,15 +610,22 @@ def main():
     ap.add_argument("--mo-block", type=int, default=8, help="MO-driven route: outer MO indices per block")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form (0: skip)")
     ap.add_argument("--e2e-calls", type=int, default=5, help="calls of the end-to-end (host buffers) timing")
+    ap.add_argument("--nk-active", type=int, default=0,
+                    help="transform only the first N units of the active range (0: all); AO work unchanged")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=2, help="oracle samples of the cpu_baseline leg")
     ap.add_argument("--ref-budget", type=float, default=4.0, help="seconds of one oracle sample")
     ap.add_argument("--stats", action="store_true", help="print per-phase statistics to stderr")
-    ap.add_argument("--requests", type=int, default=32, help="serving workload: number of requests")
+    ap.add_argument("--requests", type=int, default=256, help="serving workload: number of requests")
     ap.add_argument("--slots", type=int, default=4, help="serving workload: concurrent contexts")
-    ap.add_argument("--max-nl", type=int, default=64, help="serving workload: largest nL")
-    ap.add_argument("--max-nk", type=int, default=16, help="serving workload: largest nK")
+    ap.add_argument("--max-nl", type=int, default=200, help="serving workload: largest nL")
+    ap.add_argument("--max-nk", type=int, default=48, help="serving workload: largest nK")
+    ap.add_argument("--batch-requests", type=int, default=32, help="batch workload: number of requests")
+    ap.add_argument("--batch-max-nl", type=int, default=64, help="batch workload: largest nL")
+    ap.add_argument("--batch-max-nk", type=int, default=16, help="batch workload: largest nK")
+    ap.add_argument("--compare-prefix", type=int, default=32,
+                    help="serving workload: requests of the stream's start run in both forms side by side")
     args = ap.parse_args()
     if args.workload == "serving":
         return run_serving(args)
@@ -621,7 +655,7 @@ def main():
     set_coefs = ctx.set_coefficients if problem.kramers else ctx.set_spinor_coefficients
     set_coefs(CLd, CSd)
     ctx.set_route(args.route, args.mo_block if args.route == "mo" else 0)
-    nK = problem.nK
+    nK = problem.nK if args.nk_active <= 0 else min(args.nk_active, problem.nK)
     prec = qdt.SPLIT if args.precision == "split" else qdt.FP64
     nout = ctx.packed_size(blocks, 0, nK) // 8
     out = torch.zeros(nout, dtype=torch.float64, device="cuda")
@@ -652,7 +686,7 @@ def main():
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, world, "cuda")
-    n_mo = mo_count(problem, len(blocks))
+    n_mo = mo_count(problem, len(blocks)) * (float(nK) / problem.nK) ** 4
     value = job_value(n_mo, world, ms)
 
     # end to end through the public API with host buffers (pinned): coefficients

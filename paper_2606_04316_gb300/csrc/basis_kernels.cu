@@ -27,6 +27,16 @@ __global__ void boys_table_kernel(double *tab) {
     double *row = tab + (size_t)i * kBoysCols;
     row[M] = e * sum;
     for (int n = M - 1; n >= 0; --n) row[n] = (2.0 * T * row[n + 1] + e) / (2.0 * n + 1.0);
+    // after the FP64 table: its FP32 copy (header of the plain-FP32 integrals), its
+    // split into FP32 pairs hi + lo, and per grid point exp(-T_i) and T_i as pairs
+    // (header of the compensated-FP32 integrals); layout in boys_tables()
+    BoysTables t = boys_tables(tab);
+    for (int n = 0; n <= M; ++n) {
+        t.f32[(size_t)i * kBoysCols + n] = (float)row[n];
+        t.pair[(size_t)i * kBoysCols + n] = split_pair(row[n]);
+    }
+    t.exp_pair[i] = split_pair(e);
+    t.t_pair[i] = split_pair(T);
 }
 
 void launch_boys_table(double *d_tab, cudaStream_t s) {

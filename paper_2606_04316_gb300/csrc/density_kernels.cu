@@ -15,6 +15,51 @@ __device__ inline cplx cconj(cplx a) { return {a.re, -a.im}; }
 __device__ inline cplx cneg(cplx a) { return {-a.re, -a.im}; }
 __device__ inline cplx ctimes_i(cplx a) { return {-a.im, a.re}; }
 
+// Compensated FP32 pair x = h + l (~48-bit significand): products by the
+// exact-product FMA plus the cross terms, sums by the error-free two-sum,
+// both renormalised.  The intrinsics keep the compiler from contracting the
+// rounded operations into FMAs.  FP32 issues 64 times faster than FP64 on this
+// part, so the split form's density (whose digits keep 42 bits) runs in these.
+struct dfl { float h, l; };
+__device__ inline dfl dfl_of(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+__device__ inline double dfl_val(dfl a) { return (double)a.h + (double)a.l; }
+__device__ inline dfl operator*(dfl a, dfl b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    const float s = __fadd_rn(p, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+__device__ inline dfl operator+(dfl a, dfl b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bv = __fsub_rn(s, a.h);
+    float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bv)), __fsub_rn(b.h, bv));
+    err = __fadd_rn(err, __fadd_rn(a.l, b.l));
+    const float t = __fadd_rn(s, err);
+    return {t, __fsub_rn(err, __fsub_rn(t, s))};
+}
+__device__ inline dfl operator-(dfl a) { return {-a.h, -a.l}; }
+__device__ inline dfl operator-(dfl a, dfl b) { return a + (-b); }
+
+// Complex numbers over the real type R (double, or dfl in the split form).
+template <class R> struct Cx { R re, im; };
+template <class R> __device__ inline Cx<R> operator*(Cx<R> a, Cx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R> __device__ inline Cx<R> operator+(Cx<R> a, Cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R> __device__ inline Cx<R> operator-(Cx<R> a, Cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R> __device__ inline Cx<R> conj_(Cx<R> a) { return {a.re, -a.im}; }
+template <class R> __device__ inline Cx<R> neg_(Cx<R> a) { return {-a.re, -a.im}; }
+template <class R> __device__ inline Cx<R> times_i(Cx<R> a) { return {-a.im, a.re}; }
+__device__ inline double val_(double x) { return x; }
+__device__ inline double val_(dfl x) { return dfl_val(x); }
+__device__ inline double real_of(double x, double) { return x; }
+__device__ inline dfl real_of(double x, dfl) { return dfl_of(x); }
+
 // Two-spinor coefficients of row f, Kramers pair k: alpha = q0 + i q1, beta = q2 + i q3.
 __device__ inline void spinor(const double *Cq, int nK, int f, int k, cplx &al, cplx &be) {
     const double *q = Cq + ((size_t)f * nK + k) * 4;
@@ -60,38 +105,76 @@ __device__ inline double block_max(double v) {
 //   conj(C[a,alpha,R']) = -C[a,beta,R],  conj(C[a,beta,R']) = C[a,alpha,R].
 // KU (Kramers-unrestricted input): R, S are spinors with their own
 // coefficients; only A is formed, 2 parts (Re A, Im A) per spinor pair.
-template <bool KU>
-__global__ void density_coulomb_kernel(const PairDev *pairs, const int *bra_order,
-                                       const ShellDev *shells, const double *Cq, int nK, int k0,
-                                       const int *rsR, const int *rsS, int nRS, double *D,
-                                       double *Dmax) {
+//
+// One CTA per shell pair; its function pairs run one after another (uniform
+// across the CTA), the two coefficient rows of a function pair are staged in
+// shared memory, and the threads run over the column pairs RS, each writing
+// its parts as 16-byte stores next to its neighbours' (a warp writes one
+// contiguous run of the row).
+constexpr int kDensityThreads = 256;
+
+// Coefficient rows a and b (active range k0 .. k0 + nKa) into shared memory,
+// as the real type R.
+template <class R>
+__device__ inline void stage_rows(const double *Cq, int nK, int k0, int nKa, int ia, int ib, R *ca, R *cb) {
+    const double *ra = Cq + ((size_t)ia * nK + k0) * 4, *rb = Cq + ((size_t)ib * nK + k0) * 4;
+    for (int i = threadIdx.x; i < 4 * nKa; i += blockDim.x) {
+        ca[i] = real_of(ra[i], R{});
+        cb[i] = real_of(rb[i], R{});
+    }
+}
+
+template <class R>
+__device__ inline void spinor_s(const R *c, int k, Cx<R> &al, Cx<R> &be) {
+    al = {c[4 * k], c[4 * k + 1]};
+    be = {c[4 * k + 2], c[4 * k + 3]};
+}
+
+template <bool KU, class R>
+__global__ void __launch_bounds__(kDensityThreads) density_coulomb_kernel(
+    const PairDev *pairs, const int *bra_order, const ShellDev *shells, const double *Cq, int nK, int k0, int nKa,
+    const int *rsR, const int *rsS, int nRS, double *D, double *Dmax) {
+    extern __shared__ double crow_raw[];
+    R *ca = reinterpret_cast<R *>(crow_raw), *cb = ca + 4 * nKa;
     const int sp = bra_order[blockIdx.x];
     const PairDev pr = pairs[sp];
     const ShellDev A = shells[pr.sa], B = shells[pr.sb];
     constexpr int parts = KU ? 2 : 4;
     const long long ld = (long long)parts * nRS;
+    const bool diag = pr.sa == pr.sb;
     double vmax = 0.0;
-    for (long long idx = threadIdx.x; idx < (long long)pr.nfp * nRS; idx += blockDim.x) {
-        int fp = (int)(idx / nRS), rs = (int)(idx - (long long)fp * nRS);
-        int fa, fb;
-        decode_fp(pr, B.nfunc, fp, fa, fb);
-        int ia = A.foff + fa, ib = B.foff + fb;
-        int R = k0 + rsR[rs], S = k0 + rsS[rs];
-        cplx aaR, abR, aaS, abS, baR, bbR, baS, bbS;
-        spinor(Cq, nK, ia, R, aaR, abR);
-        spinor(Cq, nK, ia, S, aaS, abS);
-        spinor(Cq, nK, ib, R, baR, bbR);
-        spinor(Cq, nK, ib, S, baS, bbS);
-        cplx Av = cadd(cmul(cconj(aaR), baS), cmul(cconj(abR), bbS));
-        if (ia != ib) Av = cadd(Av, cadd(cmul(cconj(baR), aaS), cmul(cconj(bbR), abS)));
-        double *o = D + (pr.rowoff + fp) * ld + (long long)parts * rs;
-        o[0] = Av.re; o[1] = Av.im;
-        vmax = fmax(vmax, fmax(fabs(Av.re), fabs(Av.im)));
-        if (!KU) {
-            cplx Bv = csub(cmul(aaR, bbS), cmul(abR, baS));
-            if (ia != ib) Bv = cadd(Bv, csub(cmul(baR, abS), cmul(bbR, aaS)));
-            o[2] = Bv.re; o[3] = Bv.im;
-            vmax = fmax(vmax, fmax(fabs(Bv.re), fabs(Bv.im)));
+    int fa = 0, fb = 0;
+    for (int fp = 0; fp < pr.nfp; ++fp) {
+        const int ia = A.foff + fa, ib = B.foff + fb;
+        __syncthreads();                       // the previous function pair's readers are done
+        stage_rows(Cq, nK, k0, nKa, ia, ib, ca, cb);
+        __syncthreads();
+        double *row = D + (pr.rowoff + fp) * ld;
+        for (int rs = threadIdx.x; rs < nRS; rs += blockDim.x) {
+            const int Rr = rsR[rs], Ss = rsS[rs];
+            Cx<R> aaR, abR, aaS, abS, baR, bbR, baS, bbS;
+            spinor_s(ca, Rr, aaR, abR);
+            spinor_s(ca, Ss, aaS, abS);
+            spinor_s(cb, Rr, baR, bbR);
+            spinor_s(cb, Ss, baS, bbS);
+            Cx<R> Av = conj_(aaR) * baS + conj_(abR) * bbS;
+            if (ia != ib) Av = Av + (conj_(baR) * aaS + conj_(bbR) * abS);
+            const double are = val_(Av.re), aim = val_(Av.im);
+            double2 *o = reinterpret_cast<double2 *>(row + (long long)parts * rs);
+            o[0] = make_double2(are, aim);
+            vmax = fmax(vmax, fmax(fabs(are), fabs(aim)));
+            if (!KU) {
+                Cx<R> Bv = aaR * bbS - abR * baS;
+                if (ia != ib) Bv = Bv + (baR * abS - bbR * aaS);
+                const double bre = val_(Bv.re), bim = val_(Bv.im);
+                o[1] = make_double2(bre, bim);
+                vmax = fmax(vmax, fmax(fabs(bre), fabs(bim)));
+            }
+        }
+        // next function pair: b runs fastest; a diagonal pair keeps b >= a
+        if (++fb == B.nfunc) {
+            ++fa;
+            fb = diag ? fa : 0;
         }
     }
     // block max -> Dmax[sp]
@@ -101,69 +184,107 @@ __global__ void density_coulomb_kernel(const PairDev *pairs, const int *bra_orde
 
 // sigma_J between the spin components: c = (conj(C[u,alpha,x]), conj(C[u,beta,x])),
 // d = (C[v,alpha,y], C[v,beta,y]).
-__device__ inline cplx sigma_form(int J, cplx c1, cplx c2, cplx d1, cplx d2) {
-    if (J == 0) return cadd(cmul(c1, d2), cmul(c2, d1));                          // sigma_x
-    if (J == 1) return ctimes_i(csub(cmul(c2, d1), cmul(c1, d2)));                // sigma_y
-    return csub(cmul(c1, d1), cmul(c2, d2));                                      // sigma_z
+template <class R>
+__device__ inline Cx<R> sigma_form(int J, Cx<R> c1, Cx<R> c2, Cx<R> d1, Cx<R> d2) {
+    if (J == 0) return c1 * d2 + c2 * d1;                          // sigma_x
+    if (J == 1) return times_i(c2 * d1 - c1 * d2);                 // sigma_y
+    return c1 * d1 - c2 * d2;                                      // sigma_z
 }
 
 // Gaunt / gauge: rows (a in L, b in S), columns (J, RS, part) of the folded
-// L-S alpha densities D^J_{ab} + D^J_{ba} (Eqs. GauntInt, gaugeInt).
-template <bool KU>
-__global__ void density_gaunt_kernel(const PairDev *pairs, const int *bra_order,
-                                     const ShellDev *shells, const double *Cq, int nK, int k0,
-                                     const int *rsR, const int *rsS, int nRS, double *D,
-                                     double *Dmax) {
+// L-S alpha densities D^J_{ab} + D^J_{ba} (Eqs. GauntInt, gaugeInt).  Same
+// work layout as the Coulomb kernel.
+template <bool KU, class R>
+__global__ void __launch_bounds__(kDensityThreads) density_gaunt_kernel(
+    const PairDev *pairs, const int *bra_order, const ShellDev *shells, const double *Cq, int nK, int k0, int nKa,
+    const int *rsR, const int *rsS, int nRS, double *D, double *Dmax) {
+    extern __shared__ double crow_raw[];
+    R *ca = reinterpret_cast<R *>(crow_raw), *cb = ca + 4 * nKa;
     const int sp = bra_order[blockIdx.x];
     const PairDev pr = pairs[sp];
     const ShellDev A = shells[pr.sa], B = shells[pr.sb];
     constexpr int parts = KU ? 2 : 4;
     const long long ld = 3LL * parts * nRS;
     double vmax = 0.0;
-    for (long long idx = threadIdx.x; idx < (long long)pr.nfp * nRS; idx += blockDim.x) {
-        int fp = (int)(idx / nRS), rs = (int)(idx - (long long)fp * nRS);
-        int fa = fp / B.nfunc, fb = fp % B.nfunc;
-        int ia = A.foff + fa, ib = B.foff + fb;
-        int R = k0 + rsR[rs], S = k0 + rsS[rs];
-        cplx aaR, abR, aaS, abS, baR, bbR, baS, bbS;
-        spinor(Cq, nK, ia, R, aaR, abR);
-        spinor(Cq, nK, ia, S, aaS, abS);
-        spinor(Cq, nK, ib, R, baR, bbR);
-        spinor(Cq, nK, ib, S, baS, bbS);
-        for (int J = 0; J < 3; ++J) {
-            // x = R: (conj alpha, conj beta); x = R': (-beta, alpha)
-            cplx A1 = sigma_form(J, cconj(aaR), cconj(abR), baS, bbS);
-            cplx A2 = sigma_form(J, cconj(baR), cconj(bbR), aaS, abS);
-            cplx Av = cadd(A1, A2);
-            double *o = D + (pr.rowoff + fp) * ld + (long long)J * parts * nRS + (long long)parts * rs;
-            o[0] = Av.re; o[1] = Av.im;
-            vmax = fmax(vmax, fmax(fabs(Av.re), fabs(Av.im)));
-            if (!KU) {
-                cplx B1 = sigma_form(J, cneg(abR), aaR, baS, bbS);
-                cplx B2 = sigma_form(J, cneg(bbR), baR, aaS, abS);
-                cplx Bv = cadd(B1, B2);
-                o[2] = Bv.re; o[3] = Bv.im;
-                vmax = fmax(vmax, fmax(fabs(Bv.re), fabs(Bv.im)));
+    int fa = 0, fb = 0;
+    for (int fp = 0; fp < pr.nfp; ++fp) {
+        const int ia = A.foff + fa, ib = B.foff + fb;
+        __syncthreads();
+        stage_rows(Cq, nK, k0, nKa, ia, ib, ca, cb);
+        __syncthreads();
+        double *row = D + (pr.rowoff + fp) * ld;
+        for (int rs = threadIdx.x; rs < nRS; rs += blockDim.x) {
+            const int Rr = rsR[rs], Ss = rsS[rs];
+            Cx<R> aaR, abR, aaS, abS, baR, bbR, baS, bbS;
+            spinor_s(ca, Rr, aaR, abR);
+            spinor_s(ca, Ss, aaS, abS);
+            spinor_s(cb, Rr, baR, bbR);
+            spinor_s(cb, Ss, baS, bbS);
+#pragma unroll
+            for (int J = 0; J < 3; ++J) {
+                // x = R: (conj alpha, conj beta); x = R': (-beta, alpha)
+                const Cx<R> Av = sigma_form(J, conj_(aaR), conj_(abR), baS, bbS) +
+                                 sigma_form(J, conj_(baR), conj_(bbR), aaS, abS);
+                const double are = val_(Av.re), aim = val_(Av.im);
+                double2 *o = reinterpret_cast<double2 *>(row + (long long)J * parts * nRS + (long long)parts * rs);
+                o[0] = make_double2(are, aim);
+                vmax = fmax(vmax, fmax(fabs(are), fabs(aim)));
+                if (!KU) {
+                    const Cx<R> Bv = sigma_form(J, neg_(abR), aaR, baS, bbS) + sigma_form(J, neg_(bbR), baR, aaS, abS);
+                    const double bre = val_(Bv.re), bim = val_(Bv.im);
+                    o[1] = make_double2(bre, bim);
+                    vmax = fmax(vmax, fmax(fabs(bre), fabs(bim)));
+                }
             }
+        }
+        if (++fb == B.nfunc) {
+            ++fa;
+            fb = 0;
         }
     }
     vmax = block_max(vmax);
     if (threadIdx.x == 0) atomic_max_nonneg(Dmax + sp, vmax);
 }
 
-void launch_density(bool gaunt, bool ku, const PairDev *pairs, const int *bra_order, int nsp,
+template <bool KU, class R>
+void launch_density_t(bool gaunt, const PairDev *pairs, const int *bra_order, int nsp, const ShellDev *shells,
+                      const double *Cq, int nK, int k0, int nKa, const int *rsR, const int *rsS, int nRS, double *D,
+                      double *Dmax, cudaStream_t s) {
+    const size_t smem = 2 * 4 * (size_t)(nKa > 0 ? nKa : 1) * sizeof(R);
+    if (smem > (size_t)200 * 1024) throw Error{QDT_ERR_ARG, "density: too many active columns"};
+    if (gaunt) {
+        if (smem > (size_t)48 * 1024)
+            QDT_CUDA_TRY(cudaFuncSetAttribute(density_gaunt_kernel<KU, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        density_gaunt_kernel<KU, R><<<nsp, kDensityThreads, smem, s>>>(pairs, bra_order, shells, Cq, nK, k0, nKa, rsR,
+                                                                       rsS, nRS, D, Dmax);
+    } else {
+        if (smem > (size_t)48 * 1024)
+            QDT_CUDA_TRY(cudaFuncSetAttribute(density_coulomb_kernel<KU, R>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        density_coulomb_kernel<KU, R><<<nsp, kDensityThreads, smem, s>>>(pairs, bra_order, shells, Cq, nK, k0, nKa,
+                                                                         rsR, rsS, nRS, D, Dmax);
+    }
+    QDT_CHECK_LAUNCH();
+}
+
+// The split form (pairs = true) computes the density in compensated FP32
+// pairs, the FP64 form in FP64.
+void launch_density(bool gaunt, bool ku, bool pairs_arith, const PairDev *pairs, const int *bra_order, int nsp,
                     const ShellDev *shells, const double *Cq, int nK, int k0, const int *rsR,
                     const int *rsS, int nRS, double *D, double *Dmax, cudaStream_t s) {
     if (nsp <= 0) return;
-    if (gaunt && ku)
-        density_gaunt_kernel<true><<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
-    else if (gaunt)
-        density_gaunt_kernel<false><<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
-    else if (ku)
-        density_coulomb_kernel<true><<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
-    else
-        density_coulomb_kernel<false><<<nsp, 256, 0, s>>>(pairs, bra_order, shells, Cq, nK, k0, rsR, rsS, nRS, D, Dmax);
-    QDT_CHECK_LAUNCH();
+    // active units: every R and S index of the column list lies in [0, nKa)
+    // (Kramers pairs, or spinors of unrestricted input: the same triangular list)
+    int nKa = 0;
+    while ((long long)nKa * (nKa + 1) / 2 < nRS) ++nKa;
+    if (ku) {
+        if (pairs_arith) launch_density_t<true, dfl>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, rsR, rsS, nRS, D, Dmax, s);
+        else launch_density_t<true, double>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, rsR, rsS, nRS, D, Dmax, s);
+    } else {
+        if (pairs_arith) launch_density_t<false, dfl>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, rsR, rsS, nRS, D, Dmax, s);
+        else launch_density_t<false, double>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, rsR, rsS, nRS, D, Dmax, s);
+    }
 }
 
 // Dmax of one MO block (MO-driven route): the largest |entry| of the density

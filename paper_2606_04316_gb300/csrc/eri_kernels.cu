@@ -33,6 +33,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "qdt_internal.cuh"
 
@@ -211,6 +212,221 @@ __device__ __forceinline__ void quartet_header(const double *boys, const PrimPai
         float2 *h2 = reinterpret_cast<float2 *>(hd);
         const int len = header_len(L, GAUGE);
         for (int i = 0; i < len; ++i) h2[i] = df_split_bits(hd[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32-pair arithmetic (x = hi + lo, ~2^-47 relative per operation) for the
+// header of the compensated-FP32 integrals: error-free product and two-sum,
+// renormalised.  The intrinsics keep the compiler from contracting the
+// rounded operations.
+__device__ __forceinline__ float2 pr_add(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float bv = __fsub_rn(s, a.x);
+    float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bv)), __fsub_rn(b.x, bv));
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    const float t = __fadd_rn(s, e);
+    return make_float2(t, __fsub_rn(e, __fsub_rn(t, s)));
+}
+__device__ __forceinline__ float2 pr_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 pr_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float t = __fadd_rn(p, e);
+    return make_float2(t, __fsub_rn(e, __fsub_rn(t, p)));
+}
+// times a power of two (exact)
+__device__ __forceinline__ float2 pr_pow2(float2 a, float f) { return make_float2(a.x * f, a.y * f); }
+// 1/a: the FP32 reciprocal y and one Newton step y + y (1 - a y), the residual in pairs
+__device__ __forceinline__ float2 pr_rcp(float2 a) {
+    const float y = __frcp_rn(a.x);
+    const float2 r = pr_add(make_float2(1.f, 0.f), pr_neg(pr_mul(a, make_float2(y, 0.f))));
+    return pr_add(make_float2(y, 0.f), make_float2(__fmul_rn(y, r.x), 0.f));
+}
+// sqrt(a): the FP32 root y and one Newton step y + (a - y^2) / (2 y)
+__device__ __forceinline__ float2 pr_sqrt(float2 a) {
+    const float y = __fsqrt_rn(a.x);
+    const float2 r = pr_add(a, pr_neg(pr_mul(make_float2(y, 0.f), make_float2(y, 0.f))));
+    return pr_add(make_float2(y, 0.f), make_float2(__fdiv_rn(r.x, y + y), 0.f));
+}
+__host__ __device__ constexpr float2 pair_const(double x) { return float2{(float)x, (float)(x - (double)(float)x)}; }
+__constant__ float2 c_inv_int_p[8] = {pair_const(0.0),       pair_const(1.0),       pair_const(1.0 / 2),
+                                      pair_const(1.0 / 3),   pair_const(1.0 / 4),   pair_const(1.0 / 5),
+                                      pair_const(1.0 / 6),   pair_const(1.0 / 7)};
+__constant__ float2 c_inv_odd_p[16] = {
+    pair_const(1.0),      pair_const(1.0 / 3),  pair_const(1.0 / 5),  pair_const(1.0 / 7),
+    pair_const(1.0 / 9),  pair_const(1.0 / 11), pair_const(1.0 / 13), pair_const(1.0 / 15),
+    pair_const(1.0 / 17), pair_const(1.0 / 19), pair_const(1.0 / 21), pair_const(1.0 / 23),
+    pair_const(1.0 / 25), pair_const(1.0 / 27), pair_const(1.0 / 29), pair_const(1.0 / 31)};
+
+// F_0..F_nmax at T (a pair) into F[0..nmax] as pairs; returns exp(-T).  Inside
+// the table: Taylor expansion of the top order about the nearest grid point
+// T_i, exp(-T) = exp(-T_i) exp(T_i - T) (|T_i - T| <= 0.025, eight terms), then
+// the downward recursion; beyond it F_0 = sqrt(pi / T) / 2 and the upward
+// recursion (exp(-T) < 3e-16 F_0 there, so its FP32 value suffices).
+__device__ __forceinline__ float2 boys_eval_pairs(const BoysTables &bt, float2 T, int nmax, float2 *F) {
+    if (T.x < (float)kBoysTMax) {
+        const int i = min((int)rintf(T.x * (float)kBoysInvDelta), kBoysGrid - 1);
+        const float2 md = pr_add(bt.t_pair[i], pr_neg(T));        // T_i - T
+        const float2 *row = bt.pair + (size_t)i * kBoysCols + nmax;
+        float2 f = row[kBoysTaylor - 1];
+#pragma unroll
+        for (int k = kBoysTaylor - 1; k > 0; --k) f = pr_add(pr_mul(f, pr_mul(md, c_inv_int_p[k])), row[k - 1]);
+        F[nmax] = f;
+        float2 em = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int k = 7; k > 0; --k) em = pr_add(make_float2(1.f, 0.f), pr_mul(em, pr_mul(md, c_inv_int_p[k])));
+        const float2 e = pr_mul(bt.exp_pair[i], em);
+        const float2 t2 = pr_pow2(T, 2.f);
+        for (int n = nmax - 1; n >= 0; --n) {
+            f = pr_mul(pr_add(pr_mul(t2, f), e), c_inv_odd_p[n]);
+            F[n] = f;
+        }
+        return e;
+    }
+    const float2 e = make_float2(expf(-T.x), 0.f);
+    float2 f = pr_mul(pair_const(kHalfSqrtPi), pr_rcp(pr_sqrt(T)));
+    const float2 inv2t = pr_pow2(pr_rcp(T), 0.5f);
+    F[0] = f;
+    for (int n = 0; n < nmax; ++n) {
+        f = pr_mul(pr_add(pr_mul(f, make_float2((float)(2 * n + 1), 0.f)), pr_neg(e)), inv2t);
+        F[n + 1] = f;
+    }
+    return e;
+}
+
+// Header of a primitive quartet whose integrals run in compensated FP32 pairs:
+// the same quantities as quartet_header<GAUGE, true> computed in FP32 pairs
+// (X_PQ and p + q from FP64 sums, the rest in pairs), so the FP64 pipe does four
+// additions per quartet instead of the whole header.  Layout as quartet_header.
+template <bool GAUGE>
+__device__ __forceinline__ void quartet_header_pairs(const double *boys, const PrimPairDev *pa, const PrimPairDev *pc,
+                                                     int L, double *hd) {
+    float2 *h2 = reinterpret_cast<float2 *>(hd);
+    const BoysTables bt = boys_tables(boys);
+    const float2 p = df_split_bits(pa->p), q = df_split_bits(pc->p);
+    const float2 s = df_split_bits(pa->p + pc->p);
+    const float2 X = df_split_bits(pa->P[0] - pc->P[0]), Y = df_split_bits(pa->P[1] - pc->P[1]),
+                 Z = df_split_bits(pa->P[2] - pc->P[2]);
+    const float2 inv_s = pr_rcp(s);
+    const float2 rho = pr_mul(pr_mul(p, q), inv_s);
+    const float2 T = pr_mul(rho, pr_add(pr_add(pr_mul(X, X), pr_mul(Y, Y)), pr_mul(Z, Z)));
+    h2[0] = X;
+    h2[1] = Y;
+    h2[2] = Z;
+    const float2 sq = pr_sqrt(s);
+    const float2 d = pr_mul(pr_mul(pr_mul(df_split_bits(pa->inv_p), df_split_bits(pc->inv_p)), inv_s), sq);
+    const float2 m2r = pr_pow2(rho, -2.f);
+    float2 fC = pr_mul(pair_const(kTwoPi52), d);
+    if (!GAUGE) {
+        float2 *F = h2 + 3;
+        boys_eval_pairs(bt, T, L, F);
+        for (int n = 0; n <= L; ++n) {
+            F[n] = pr_mul(F[n], fC);
+            fC = pr_mul(fC, m2r);
+        }
+    } else {
+        float2 *RC = h2 + 3, *RR = h2 + 4 + L;
+        const float2 e = boys_eval_pairs(bt, T, L + 2, RR);
+        float2 fR = pr_mul(pr_mul(pr_mul(pair_const(kPi52), s), sq), pr_mul(d, d));
+        float2 prev = pr_neg(pr_add(pr_mul(pr_pow2(T, 2.f), RR[0]), e));     // F_{-1}
+        for (int n = 0; n <= L + 2; ++n) {
+            const float2 cur = RR[n];
+            if (n <= L) {
+                RC[n] = pr_mul(cur, fC);
+                fC = pr_mul(fC, m2r);
+            }
+            RR[n] = pr_mul(pr_add(cur, pr_neg(prev)), fR);
+            fR = pr_mul(fR, m2r);
+            prev = cur;
+        }
+    }
+}
+
+// Header of a primitive quartet whose integrals run in plain FP32 (only the
+// high parts are read): the geometry -- X_PQ, 1/(p+q), rho and T = rho |PQ|^2
+// -- in FP64, so that T keeps its absolute accuracy (the Boys values are
+// sensitive to it), and the Boys values, exp(-T) and the prefactors in FP32
+// from the table's FP32 copy (the FP64 Boys evaluation would hold the FP64
+// pipe for most of the header).  Layout as quartet_header, as (value, 0) pairs.
+__constant__ float c_inv_int_f[8] = {0.f, 1.f, 1.f / 2, 1.f / 3, 1.f / 4, 1.f / 5, 1.f / 6, 1.f / 7};
+__constant__ float c_odd_f[16] = {1, 3, 5, 7, 9, 11, 13, 15, 17, 19, 21, 23, 25, 27, 29, 31};
+__constant__ float c_inv_odd_f[16] = {1.f,      1.f / 3,  1.f / 5,  1.f / 7,  1.f / 9,  1.f / 11,
+                                      1.f / 13, 1.f / 15, 1.f / 17, 1.f / 19, 1.f / 21, 1.f / 23,
+                                      1.f / 25, 1.f / 27, 1.f / 29, 1.f / 31};
+
+// F_0..F_nmax at T into F[0..nmax].x (FP32; Taylor offset from the FP64 T);
+// returns exp(-T).
+__device__ __forceinline__ float boys_eval_f32(const float *tab, double T, int nmax, float2 *F) {
+    const float Tf = (float)T;
+    const float e = expf(-Tf);
+    if (T < kBoysTMax) {
+        const double ti = rint(T * kBoysInvDelta);
+        const float md = (float)fma(ti, kBoysDelta, -T);       // -(T - T_i), exact to FP32 rounding
+        const float *row = tab + (size_t)(int)ti * kBoysCols + nmax;
+        float f = __ldg(row + kBoysTaylor - 1);
+#pragma unroll
+        for (int k = kBoysTaylor - 1; k > 0; --k) f = fmaf(f, md * c_inv_int_f[k], __ldg(row + k - 1));
+        F[nmax] = make_float2(f, 0.f);
+        const float t2 = Tf + Tf;
+        for (int n = nmax - 1; n >= 0; --n) {
+            f = fmaf(t2, f, e) * c_inv_odd_f[n];
+            F[n] = make_float2(f, 0.f);
+        }
+    } else {
+        float f = (float)kHalfSqrtPi * rsqrtf(Tf);
+        const float inv2t = 0.5f / Tf;
+        F[0] = make_float2(f, 0.f);
+        for (int n = 0; n < nmax; ++n) {
+            f = fmaf(c_odd_f[n], f, -e) * inv2t;
+            F[n + 1] = make_float2(f, 0.f);
+        }
+    }
+    return e;
+}
+
+template <bool GAUGE>
+__device__ __forceinline__ void quartet_header_f32(const double *boys, const PrimPairDev *pa, const PrimPairDev *pc,
+                                                   int L, double *hd) {
+    float2 *h2 = reinterpret_cast<float2 *>(hd);
+    const float *boysf = boys_tables(boys).f32;
+    const double p = pa->p, q = pc->p, s = p + q;
+    const double X = pa->P[0] - pc->P[0], Y = pa->P[1] - pc->P[1], Z = pa->P[2] - pc->P[2];
+    const double inv_s = 1.0 / s;
+    const double rho = p * q * inv_s;
+    const double T = rho * fma(X, X, fma(Y, Y, Z * Z));
+    h2[0] = make_float2((float)X, 0.f);
+    h2[1] = make_float2((float)Y, 0.f);
+    h2[2] = make_float2((float)Z, 0.f);
+    const float sf = (float)s;
+    const float d = (float)pa->inv_p * (float)pc->inv_p * (float)inv_s * sqrtf(sf);    // 1 / (p q sqrt(p + q))
+    const float m2r = (float)(-2.0 * rho);
+    float fC = (float)kTwoPi52 * d;
+    if (!GAUGE) {
+        float2 *F = h2 + 3;
+        boys_eval_f32(boysf, T, L, F);
+        for (int n = 0; n <= L; ++n) {
+            F[n].x *= fC;
+            fC *= m2r;
+        }
+    } else {
+        float2 *RC = h2 + 3, *RR = h2 + 4 + L;
+        const float e = boys_eval_f32(boysf, T, L + 2, RR);
+        const float Tf = (float)T;
+        float fR = (float)kPi52 * sf * sqrtf(sf) * d * d;
+        float prev = -fmaf(Tf + Tf, RR[0].x, e);                 // F_{-1}
+        for (int n = 0; n <= L + 2; ++n) {
+            const float cur = RR[n].x;
+            if (n <= L) {
+                RC[n] = make_float2(cur * fC, 0.f);
+                fC *= m2r;
+            }
+            RR[n] = make_float2((cur - prev) * fR, 0.f);
+            fR *= m2r;
+            prev = cur;
+        }
     }
 }
 
@@ -440,6 +656,128 @@ __device__ __forceinline__ void ket_orders_df2(int n0, int Ly, int tx, int ux, i
     }
 }
 
+// Register tile of the ket pass: TH rows of T (Hermite rows of the outer pair,
+// each with its own R tensor base and stride: the Coulomb tensor, or for the
+// gauge kernel the r12 tensor) times TY adjacent inner function pairs, for one
+// outer primitive pair:
+//   acc[r][c] += sum_{kl} sum_{h'} (-1)^{|h'|} R_kl[h_r + h'] E^kl[h'][y_c].
+// Each E value is loaded once for the TH rows and each R value once for the TY
+// columns, and the TH x TY accumulators are independent chains.  DF: compensated
+// FP32 pairs (R, E and the accumulators as hi + lo); else plain FP32 (the high
+// parts).  Rows and columns past the chunk are clamped by the caller (their sums
+// are discarded).
+template <int TH, int TY, bool DF>
+struct KetTile {
+    float ah[TH][TY], al[TH][TY];
+};
+
+template <int TH, int TY, bool DF, bool NEG>
+__device__ __forceinline__ void ket_tile_orders(int n0, int Ly, const int (&rs)[TH], const int (&rw)[TH],
+                                                const int (&rv)[TH], const float2 *const (&Rb)[TH],
+                                                const int (&nr)[TH], const int *trip, const void *eyv, int nfpY,
+                                                long long sE, int nk, const int (&yo)[TY], KetTile<TH, TY, DF> &t) {
+    for (int n = n0; n <= Ly; n += 2) {
+        const int hb = n ? nherm(n - 1) : 0, he = nherm(n);
+        for (int hp = hb; hp < he; ++hp) {
+            const int tq = trip[hp];
+            const int up = (tq >> 8) & 255, vp = tq >> 16, wp = up + vp, sp = (tq & 255) + wp;
+            const float2 *rp[TH];
+#pragma unroll
+            for (int r = 0; r < TH; ++r) {
+                const int s = rs[r] + sp, w = rw[r] + wp;
+                rp[r] = Rb[r] + (s * (s + 1) * (s + 2) / 6 + w * (w + 1) / 2 + rv[r] + vp);
+            }
+            if constexpr (DF) {
+                const float2 *e = reinterpret_cast<const float2 *>(eyv) + (size_t)hp * nfpY;
+#pragma unroll 2
+                for (int kl = 0; kl < nk; ++kl) {
+                    float2 ev[TY];
+#pragma unroll
+                    for (int c = 0; c < TY; ++c) ev[c] = __ldg(e + yo[c]);
+#pragma unroll
+                    for (int r = 0; r < TH; ++r) {
+                        const float2 rvv = *rp[r];
+                        rp[r] += nr[r];
+#pragma unroll
+                        for (int c = 0; c < TY; ++c) df_madd<NEG>(rvv, ev[c], t.ah[r][c], t.al[r][c]);
+                    }
+                    e += sE;
+                }
+            } else {
+                const float *e = reinterpret_cast<const float *>(eyv) + (size_t)hp * nfpY;
+#pragma unroll 3
+                for (int kl = 0; kl < nk; ++kl) {
+                    float ev[TY];
+#pragma unroll
+                    for (int c = 0; c < TY; ++c) ev[c] = __ldg(e + yo[c]);
+#pragma unroll
+                    for (int r = 0; r < TH; ++r) {
+                        const float rvv = rp[r]->x;
+                        rp[r] += nr[r];
+#pragma unroll
+                        for (int c = 0; c < TY; ++c)
+                            t.ah[r][c] = NEG ? fmaf(-rvv, ev[c], t.ah[r][c]) : fmaf(rvv, ev[c], t.ah[r][c]);
+                    }
+                    e += sE;
+                }
+            }
+        }
+    }
+}
+
+// The tiled ket pass over every (outer primitive pair, row block, column
+// block) of a chunk: T[ij][hh][y] (float2 slots) += the sums above.  Rows hh <
+// nhx use the Coulomb tensor RC (Hermite index hh); for the gauge kernel rows
+// hh >= nhx use the r12 tensor RR (Hermite index hh - nhx + 4).
+template <int TH, int TY, bool DF, bool GAUGE>
+__device__ __forceinline__ void ket_pass_tiled(int nij, int nT, int nhx, int ych, int Ly, const int *trip,
+                                               float2 *T, int tsz, const float2 *RC, int nrC, const float2 *RR,
+                                               int nrR, int nk, const void *ey0, int nfpY, long long sE) {
+    const int nHB = (nT + TH - 1) / TH, nYB = (ych + TY - 1) / TY;
+    for (int it = threadIdx.x; it < nij * nHB * nYB; it += blockDim.x) {
+        const int ijl = it / (nHB * nYB);
+        const int rem = it - ijl * nHB * nYB;
+        const int hb = rem / nYB, yb = rem - hb * nYB;
+        const int h0 = hb * TH, y0 = yb * TY;
+        int rs[TH], rw[TH], rv[TH], nr[TH], hh[TH];
+        const float2 *Rb[TH];
+#pragma unroll
+        for (int r = 0; r < TH; ++r) {
+            hh[r] = min(h0 + r, nT - 1);
+            const bool r12 = GAUGE && hh[r] >= nhx;
+            const int tr = trip[r12 ? hh[r] - nhx + 4 : hh[r]];
+            const int u = (tr >> 8) & 255, v = tr >> 16;
+            rv[r] = v;
+            rw[r] = u + v;
+            rs[r] = (tr & 255) + u + v;
+            nr[r] = r12 ? nrR : nrC;
+            Rb[r] = r12 ? RR + (size_t)ijl * nk * nrR : RC + (size_t)ijl * nk * nrC;
+        }
+        int yo[TY];
+#pragma unroll
+        for (int c = 0; c < TY; ++c) yo[c] = min(y0 + c, ych - 1) - y0;
+        KetTile<TH, TY, DF> t;
+        float2 *Tq = T + (size_t)ijl * tsz + y0;
+#pragma unroll
+        for (int r = 0; r < TH; ++r)
+#pragma unroll
+            for (int c = 0; c < TY; ++c) {
+                const float2 v = Tq[(size_t)hh[r] * ych + yo[c]];
+                t.ah[r][c] = v.x;
+                t.al[r][c] = DF ? v.y : 0.f;
+            }
+        const void *ey = DF ? (const void *)(reinterpret_cast<const float2 *>(ey0) + y0)
+                            : (const void *)(reinterpret_cast<const float *>(ey0) + y0);
+        ket_tile_orders<TH, TY, DF, false>(0, Ly, rs, rw, rv, Rb, nr, trip, ey, nfpY, sE, nk, yo, t);
+        ket_tile_orders<TH, TY, DF, true>(1, Ly, rs, rw, rv, Rb, nr, trip, ey, nfpY, sE, nk, yo, t);
+#pragma unroll
+        for (int r = 0; r < TH; ++r)
+#pragma unroll
+            for (int c = 0; c < TY; ++c)
+                if (h0 + r < nT && y0 + c < ych) Tq[(size_t)(h0 + r) * ych + c] = make_float2(t.ah[r][c], DF ? t.al[r][c] : 0.f);
+    }
+}
+
 // One chunk (x in [x0,x1) of X, y in [y0,y1) of Y) of the block (X|Y);
 // results in b.G[comp][x][y].  NC = 1 (Coulomb) or 7 (gauge: [0] Coulomb,
 // [1..6] (xy|d_I d_J r|zw) for IJ = xx,xy,xz,yy,yz,zz).
@@ -494,32 +832,49 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
             // Boys values, prefactors and X_PQ of every primitive quartet of the group
             for (int q = tid; q < nq; q += nt) {
                 const int ijl = q / nk, kl = q - ijl * nk;
-                quartet_header<GAUGE, DF>(boys, pp + X.ppoff + i0 + ijl, pp + Y.ppoff + k0 + kl, L, H + (size_t)q * hs);
+                // plain-FP32 quartets of the Coulomb kernel: FP32 header; those of
+                // the gauge kernel keep the FP64 header (its r12 tensor takes
+                // differences F_n - F_{n-1} that lose digits in FP32; measured
+                // 13x the Coulomb kernel's error ratio)
+                if constexpr (DF && F32 && !GAUGE)
+                    quartet_header_f32<GAUGE>(boys, pp + X.ppoff + i0 + ijl, pp + Y.ppoff + k0 + kl, L, H + (size_t)q * hs);
+                else if constexpr (DF && F32)
+                    quartet_header<GAUGE, true>(boys, pp + X.ppoff + i0 + ijl, pp + Y.ppoff + k0 + kl, L,
+                                                H + (size_t)q * hs);
+                else if constexpr (DF)
+                    quartet_header_pairs<GAUGE>(boys, pp + X.ppoff + i0 + ijl, pp + Y.ppoff + k0 + kl, L,
+                                                H + (size_t)q * hs);
+                else
+                    quartet_header<GAUGE, false>(boys, pp + X.ppoff + i0 + ijl, pp + Y.ppoff + k0 + kl, L,
+                                                 H + (size_t)q * hs);
             }
             __syncthreads();
-            // Hermite recursion, one auxiliary order per pass; order 0 ends in buffer 0
+            // Hermite recursion, one auxiliary order per pass; order 0 ends in buffer 0.
+            // Each warp runs all orders of its own primitive quartets (q = warp,
+            // warp + nwarps, ...), so consecutive orders need only a warp barrier;
+            // one CTA barrier after the last order.
+            const int nw = nt >> 5, wq = tid >> 5, lane = tid & 31;
+            const int nqw = wq < nq ? (nq - wq + nw - 1) / nw : 0;
             for (int m = Ltop; m >= 0; --m) {
                 const int cC = m <= L ? nherm(L - m) : 0;
                 const int cR = GAUGE ? nherm(Lr - m) : 0;
                 const int cnt = cC + cR;
                 const int cur = m & 1, prv = cur ^ 1;
-                for (int it = tid; it < nq * cnt; it += nt) {
-                    const int q = it / cnt;
-                    int h = it - q * cnt;
+                // items (quartet of this warp, Hermite entry) of the order; for cnt >= 2
+                // the quotient it / cnt by a multiply-high with ceil(2^32 / cnt) =
+                // floor((2^32 - 1) / cnt) + 1 (exact while it * cnt < 2^32; here
+                // it * cnt < 2^16 * 2^8); cnt == 1 (the top order) has quotient it
+                const unsigned magic = cnt > 1 ? 0xFFFFFFFFu / (unsigned)cnt + 1u : 0u;
+                for (int it = lane; it < nqw * cnt; it += 32) {
+                    const int qi = cnt > 1 ? (int)__umulhi((unsigned)it, magic) : it;
+                    const int q = wq + qi * nw;
+                    const int hh = it - qi * cnt;
                     const double *hd = H + (size_t)q * hs;
-                    double *dst;
-                    const double *src;
-                    int i0h;
-                    if (!GAUGE || h < cC) {
-                        dst = RC + ((size_t)cur * nq + q) * nrC;
-                        src = RC + ((size_t)prv * nq + q) * nrC;
-                        i0h = 3 + m;
-                    } else {
-                        h -= cC;
-                        dst = RR + ((size_t)cur * nq + q) * nrR;
-                        src = RR + ((size_t)prv * nq + q) * nrR;
-                        i0h = 4 + L + m;
-                    }
+                    const bool cpart = !GAUGE || hh < cC;
+                    const int h = cpart ? hh : hh - cC;
+                    double *dst = cpart ? RC + ((size_t)cur * nq + q) * nrC : RR + ((size_t)cur * nq + q) * nrR;
+                    const double *src = cpart ? RC + ((size_t)prv * nq + q) * nrC : RR + ((size_t)prv * nq + q) * nrR;
+                    const int i0h = cpart ? 3 + m : 4 + L + m;
                     if constexpr (DF && F32) {
                         const float2 *hd2 = reinterpret_cast<const float2 *>(hd);
                         const float2 *src2 = reinterpret_cast<const float2 *>(src);
@@ -549,11 +904,21 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
                         dst[h] = r;
                     }
                 }
-                __syncthreads();
+                __syncwarp();
             }
+            __syncthreads();
             // T[ij][h][y] += sum_kl sum_h' (-1)^{|h'|} R[h+h'] E^{kl}[h'][y]: rows h < nhx
             // with the Coulomb tensor, then (gauge) rows g = 4.. with the r12 tensor
-            if constexpr (DF && F32 && !GAUGE) {
+            if (DF && nT >= 4 && ych >= 2) {
+                // register tiles: 4 T rows x 2 inner function pairs per thread
+                if constexpr (DF) {
+                    float2 *T2 = reinterpret_cast<float2 *>(T);
+                    const float2 *RC2 = reinterpret_cast<const float2 *>(RC), *RR2 = reinterpret_cast<const float2 *>(RR);
+                    const void *ey = F32 ? (const void *)(E1 + b.eY[k0] + y0) : (const void *)(E2 + b.eY[k0] + y0);
+                    ket_pass_tiled<4, 2, !F32, GAUGE>(nij, nT, nhx, ych, Ly, b.trip, T2, tsz, RC2, nrC, RR2, nrR, nk,
+                                                      ey, Y.nfp, sE);
+                }
+            } else if constexpr (DF && F32 && !GAUGE) {
                 // two T rows per thread sharing the E loads
                 const int nT2 = (nT + 1) / 2;
                 for (int it = tid; it < nij * nT2 * ych; it += nt) {

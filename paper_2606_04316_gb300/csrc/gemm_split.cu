@@ -4,14 +4,17 @@
 //  QDT_FP64:  plain FP64 GEMMs (gemm_fp64.cu).
 //  QDT_SPLIT: Ozaki-style split precision on the 5th-generation tensor cores.
 //    Every FP64 operand row (A) or column (B) gets a power-of-two scale 2^e
-//    with 2^e > max |x|; x = sign * 2^e * sum_{i=1..6} d_i 2^{-7 i} with 7-bit
-//    digits d_i (exact in BF16).  C = 2^{e_r + f_c} sum_{i+j<=7} 2^{-7(i+j)}
-//    sum_k a_i b_j.  Digit products are integers < 2^14; over a K chunk of 256
-//    the sums of diagonals i+j = 2, 3, 4 (at most 3 pairs) stay below 2^24 and
-//    are exact in the FP32 TMEM accumulators; after each chunk they are
-//    converted to integers and folded into a 64-bit integer accumulator.  The
-//    lighter diagonals 5, 6, 7 (weights <= 2^{-35}) accumulate in FP32 over the
-//    whole K.  The result is recombined in FP64.
+//    with 2^e > max |x|; x 2^{42-e} is rounded to an integer X and written as
+//    six balanced 7-bit digits, x = 2^e sum_{i=1..6} d_i 2^{-7 i} with d_1 in
+//    [-128, 128] and d_2..d_6 in [-64, 64] (all exact in BF16; rounding halves
+//    the representation error of truncated digits).  C = 2^{e_r + f_c}
+//    sum_{i+j<=7} 2^{-7(i+j)} sum_k a_i b_j.  Per K index the digit products
+//    of the diagonals i+j = 2, 3, 4 sum to at most 128^2, 2 * 128 * 64 and
+//    2 * 128 * 64 + 64^2 (20 480), so over a K chunk of 768 their sums stay
+//    within 2^24 and are exact in the FP32 TMEM accumulators; after each chunk
+//    they are converted to integers and folded into a 64-bit integer
+//    accumulator.  The lighter diagonals 5, 6, 7 (weights <= 2^{-35})
+//    accumulate in FP32 over the whole K.  The result is recombined in FP64.
 //
 //  Tensor-core kernel: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), M = 128,
 //  N = 64, operands K-major in shared memory with the 128-byte swizzle, staged
@@ -39,7 +42,7 @@ constexpr int kSlices = 6;
 constexpr int kBits = 7;
 constexpr int kFrac = kSlices * kBits;       // 42 fractional bits
 constexpr int SBM = 128, SBN = 64, SBK = 64;
-constexpr int kChunkSub = 4;                  // 4 x 64 = 256 K per exact chunk
+constexpr int kChunkSub = 12;                 // 12 x 64 = 768 K per exact chunk
 constexpr size_t kPlaneBudget = (size_t)16 << 30;   // digit planes of one second-half K chunk
 constexpr int kATile = SBM * SBK * 2;         // 16 KB: one A digit plane of a K subtile
 constexpr int kBTile = SBN * SBK * 2;         // 8 KB: one B digit plane
@@ -117,22 +120,30 @@ __device__ inline int exp_of_max(double m) {
     return ex - 1023 + 1;
 }
 
+// x 2^{42-e} rounded to the nearest integer X (|X| <= 2^42 when |x| < 2^e), by
+// integer operations on the bits, then its balanced digits: d_1 = round(X /
+// 2^35) in [-128, 128], X -= d_1 2^35, and so on down to d_6 = X in [-64, 63].
 __device__ inline void digits7(double x, int e, __nv_bfloat16 *d, size_t plane) {
-    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    int ex = (int)((bits >> 52) & 0x7FF);
-    unsigned long long X = 0;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    long long X = 0;
     if (ex != 0) {
-        unsigned long long mant = (bits & ((1ULL << 52) - 1)) | (1ULL << 52);
-        int sh = ex - 1075 + kFrac - e;          // |x| 2^{42-e} = mant 2^sh
-        if (sh >= 0) X = (1ULL << kFrac) - 1;    // cannot happen when 2^e > |x|
-        else if (sh > -64) X = mant >> (-sh);
-        if (X >= (1ULL << kFrac)) X = (1ULL << kFrac) - 1;
+        const unsigned long long mant = (bits & ((1ULL << 52) - 1)) | (1ULL << 52);
+        const int sh = ex - 1075 + kFrac - e;         // |x| 2^{42-e} = mant 2^sh
+        unsigned long long M;
+        if (sh >= 0) M = 1ULL << kFrac;               // cannot happen when 2^e > |x|
+        else if (sh > -63) M = (mant + (1ULL << (-sh - 1))) >> (-sh);
+        else M = 0;
+        if (M > (1ULL << kFrac)) M = 1ULL << kFrac;
+        X = (bits >> 63) ? -(long long)M : (long long)M;
     }
-    bool neg = (bits >> 63) != 0;
 #pragma unroll
     for (int i = 0; i < kSlices; ++i) {
-        int v = (int)((X >> (kBits * (kSlices - 1 - i))) & 127);
-        d[i * plane] = __float2bfloat16_rn((float)(neg ? -v : v));
+        const int shift = kBits * (kSlices - 1 - i);
+        // floor((X + 2^{shift-1}) / 2^shift): arithmetic shift of a signed value
+        const long long di = shift ? (X + (1LL << (shift - 1))) >> shift : X;
+        X -= di * (1LL << shift);
+        d[i * plane] = __float2bfloat16_rn((float)di);
     }
 }
 
@@ -429,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             // fold the exact diagonals (accumulators 0, 1, 2) into the integer accumulator;
-            // |sums| < 3 * 127^2 * 256 < 2^24: integers exact in FP32 and in 32-bit ints,
+            // |sums| <= 20 480 * 768 < 2^24: integers exact in FP32 and in 32-bit ints,
             // 32-bit conversions and 64-bit integer adds keep the FP64 pipe free
 #pragma unroll
             for (int q = 0; q < SBN / 16; ++q) {
@@ -439,8 +450,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld16(trow + 2 * SBN + q * 16, v2);
 #pragma unroll
                 for (int t = 0; t < 16; ++t)
-                    acc[q * 16 + t] += ((long long)__float2int_rn(v0[t]) << 14) +
-                                       ((long long)__float2int_rn(v1[t]) << 7) + (long long)__float2int_rn(v2[t]);
+                    acc[q * 16 + t] += (long long)__float2int_rn(v0[t]) * 16384 +
+                                       (long long)__float2int_rn(v1[t]) * 128 + (long long)__float2int_rn(v2[t]);
             }
             tc_fence_before();
             __syncwarp();

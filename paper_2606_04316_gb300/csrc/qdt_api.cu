@@ -30,7 +30,7 @@ namespace qdt {
 void launch_prim_pairs_map(const ShellDev *shells, const PairDev *pairs, const int *pp_pair,
                            long long npp, const double *exps, const double *coefs,
                            const double *norms, PrimPairDev *pp, double *E, cudaStream_t s);
-void launch_density(bool gaunt, bool ku, const PairDev *pairs, const int *bra_order, int nsp,
+void launch_density(bool gaunt, bool ku, bool pairs_arith, const PairDev *pairs, const int *bra_order, int nsp,
                     const ShellDev *shells, const double *Cq, int nK, int k0, const int *rsR,
                     const int *rsS, int nRS, double *D, double *Dmax, cudaStream_t s);
 }  // namespace qdt
@@ -495,7 +495,7 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
     P.Dbra = (double *)ctx->Dbra.get(std::max<long long>(1, P.M * P.ncolD) * sizeof(double));
     P.Dmax = (double *)ctx->Dmax.get(std::max(1, pc.nsp) * sizeof(double));
     QDT_CUDA_TRY(cudaMemsetAsync(P.Dmax, 0, pc.nsp * sizeof(double), s));
-    launch_density(P.ls, P.ku, pc.d_pairs, pc.d_bra_order, pc.nsp, (const ShellDev *)ctx->shells.p,
+    launch_density(P.ls, P.ku, precision == QDT_SPLIT, pc.d_pairs, pc.d_bra_order, pc.nsp, (const ShellDev *)ctx->shells.p,
                    (const double *)ctx->Cq.p, ctx->nK, k0, d_rsR, d_rsS, P.nRS, P.Dbra, P.Dmax, s);
     ctx->launches++;
     if (P.quarter) {   // the quarter route screens on coefficient bounds, not on the density
@@ -1299,7 +1299,8 @@ int qdt_create(qdt_ctx **out, int device, void *cuda_stream) {
         for (int i = 0; i < 16; ++i) QDT_CUDA_TRY(cudaEventCreate(&c->ev[i]));
         QDT_CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
         QDT_CUDA_TRY(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
-        double *tab = (double *)c->boys.get((size_t)kBoysGrid * kBoysCols * sizeof(double));
+        // FP64 table [kBoysGrid][kBoysCols], then its FP32 and FP32-pair forms (boys_tables)
+        double *tab = (double *)c->boys.get(kBoysBytes);
         launch_boys_table(tab, c->stream);
         QDT_CUDA_TRY(cudaStreamSynchronize(c->stream));
     } catch (const Error &e) {

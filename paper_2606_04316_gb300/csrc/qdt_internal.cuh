@@ -23,6 +23,38 @@ constexpr int kBoysGrid = 721;                     // 36 / 0.05 + 1
 constexpr int kBoysCols = kBoysNMax + kBoysTaylor + 1;
 
 __host__ __device__ constexpr int nherm(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+
+// The Boys tables in one device buffer: the FP64 table [kBoysGrid][kBoysCols],
+// then its FP32 copy, its split into FP32 pairs (hi, lo), and per grid point
+// exp(-T_i) and T_i = i kBoysDelta as pairs.
+// floats of the FP32 copy, rounded up to an even count so the pairs after it are 8-byte aligned
+constexpr size_t kBoysF32Slots = ((size_t)kBoysGrid * kBoysCols + 1) / 2 * 2;
+struct BoysTables {
+    const double *f64;
+    float *f32;
+    float2 *pair;
+    float2 *exp_pair;
+    float2 *t_pair;
+};
+__host__ __device__ inline BoysTables boys_tables(const double *tab) {
+    BoysTables t;
+    t.f64 = tab;
+    t.f32 = reinterpret_cast<float *>(const_cast<double *>(tab) + (size_t)kBoysGrid * kBoysCols);
+    t.pair = reinterpret_cast<float2 *>(t.f32 + kBoysF32Slots);         // 8-byte aligned
+    t.exp_pair = t.pair + (size_t)kBoysGrid * kBoysCols;
+    t.t_pair = t.exp_pair + kBoysGrid;
+    return t;
+}
+constexpr size_t kBoysBytes = (size_t)kBoysGrid * kBoysCols * (sizeof(double) + sizeof(float2)) +
+                              kBoysF32Slots * sizeof(float) + 2 * (size_t)kBoysGrid * sizeof(float2);
+
+#ifdef __CUDACC__
+// x = hi + lo with hi = fl32(x) and lo = fl32(x - hi) (an FP32 pair, ~48 bits)
+__device__ inline float2 split_pair(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+#endif
 __host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 
 // Hermite / Cartesian triple index: all triples of order <= L, ordered by
@@ -123,7 +155,7 @@ struct EriParams {
     const double *E;
     const float2 *E2;           // E as FP32 pairs: non-null selects the compensated FP32 contraction
     const float *E1;            // fl32(E), read by the tiles run in plain FP32
-    const double *boys;         // [kBoysGrid][kBoysCols]
+    const double *boys;         // [kBoysGrid][kBoysCols], followed by the same as floats
     const int *ket_sp;          // shell pair id at each sorted ket position
     const long long *ket_col;   // first column of each sorted ket position
     double *W;                  // output rows
