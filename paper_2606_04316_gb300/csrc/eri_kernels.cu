@@ -166,8 +166,13 @@ __global__ void split_pairs_kernel(const double *E, long long n, float2 *E2, flo
 // Doubles of one primitive quartet's header: X_PQ (3), R^n_000 of the Coulomb
 // tensor (n = 0..L) and, for the gauge kernel, of the r12 tensor (n = 0..L+2).
 __host__ __device__ inline int header_len(int L, bool gauge) { return gauge ? 2 * L + 7 : L + 4; }
+// Doubles per primitive quartet: header, then the recursion's two buffers per
+// tensor -- even auxiliary orders (order 0 ends there: nherm(L) entries) and
+// odd orders (the largest is order 1: nherm(L - 1) entries); the r12 tensor of
+// the gauge kernel has top order L + 2.
+__host__ __device__ inline int odd_len(int Ltop) { return Ltop >= 1 ? nherm(Ltop - 1) : 0; }
 __host__ __device__ inline int quartet_len(int L, bool gauge) {
-    return header_len(L, gauge) + 2 * (nherm(L) + (gauge ? nherm(L + 2) : 0));
+    return header_len(L, gauge) + nherm(L) + odd_len(L) + (gauge ? nherm(L + 2) + odd_len(L + 2) : 0);
 }
 
 template <bool GAUGE, bool DF>
@@ -815,8 +820,12 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
     double *T = b.P;
     double *H = T + (size_t)nijMax * tsz;
     const int nqMax = nijMax * nkl;
+    // order-0 (and even-order) buffers RC, RR [nqMax][nrC | nrR]; odd-order buffers RC1, RR1
+    const int nrC1 = odd_len(L), nrR1 = GAUGE ? odd_len(Lr) : 0;
     double *RC = H + (size_t)nqMax * hs;
-    double *RR = RC + 2 * (size_t)nqMax * nrC;
+    double *RC1 = RC + (size_t)nqMax * nrC;
+    double *RR = RC1 + (size_t)nqMax * nrC1;
+    double *RR1 = RR + (size_t)nqMax * nrR;
 
     for (int i = tid; i < X.npp; i += nt) b.eX[i] = pp[X.ppoff + i].eoff;
     for (int i = tid; i < Y.npp; i += nt) b.eY[i] = pp[Y.ppoff + i].eoff;
@@ -872,8 +881,10 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
                     const double *hd = H + (size_t)q * hs;
                     const bool cpart = !GAUGE || hh < cC;
                     const int h = cpart ? hh : hh - cC;
-                    double *dst = cpart ? RC + ((size_t)cur * nq + q) * nrC : RR + ((size_t)cur * nq + q) * nrR;
-                    const double *src = cpart ? RC + ((size_t)prv * nq + q) * nrC : RR + ((size_t)prv * nq + q) * nrR;
+                    double *dst = cpart ? (cur ? RC1 + (size_t)q * nrC1 : RC + (size_t)q * nrC)
+                                        : (cur ? RR1 + (size_t)q * nrR1 : RR + (size_t)q * nrR);
+                    const double *src = cpart ? (prv ? RC1 + (size_t)q * nrC1 : RC + (size_t)q * nrC)
+                                              : (prv ? RR1 + (size_t)q * nrR1 : RR + (size_t)q * nrR);
                     const int i0h = cpart ? 3 + m : 4 + L + m;
                     if constexpr (DF && F32) {
                         const float2 *hd2 = reinterpret_cast<const float2 *>(hd);
