@@ -17,15 +17,19 @@
 //    accumulate in FP32 over the whole K.  The result is recombined in FP64.
 //
 //  Tensor-core kernel: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), M = 128,
-//  N = 64, operands K-major in shared memory with the 128-byte swizzle, staged
+//  N = 80, operands K-major in shared memory with the 128-byte swizzle, staged
 //  by TMA (cp.async.bulk.tensor): per K subtile of 64 the six B planes are
 //  loaded once into one of two panels and the six A planes into one stage
-//  each, all tracked by mbarriers; six FP32 accumulators (384 TMEM columns)
-//  per CTA.  Roles: one thread issues the TMA loads, one the MMAs (its loops
+//  each, all tracked by mbarriers; six FP32 accumulators (480 of the 512 TMEM
+//  columns) per CTA.  N = 80 is the widest tile whose six accumulators fit the
+//  TMEM; each MMA then reads 6.5 KB of operands per 46 cycles instead of 6 KB
+//  per 37 (N = 64), which eases the shared-memory bandwidth the tensor pipe
+//  waits on.  Roles: one thread issues the TMA loads, one the MMAs (its loops
 //  unrolled over the digit pairs, so A stage, barrier phase, accumulator and
-//  descriptors are compile-time constants), four warps fold the exact
-//  diagonals and write the result.  Every wait is bounded
-//  and reports a timeout through a device status word instead of hanging.
+//  descriptors are compile-time constants), eight warps (two per TMEM lane
+//  quadrant, 40 columns each) fold the exact diagonals and write the result.
+//  Every wait is bounded and reports a timeout through a device status word
+//  instead of hanging.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -41,12 +45,12 @@ namespace qdt {
 constexpr int kSlices = 6;
 constexpr int kBits = 7;
 constexpr int kFrac = kSlices * kBits;       // 42 fractional bits
-constexpr int SBM = 128, SBN = 64, SBK = 64;
+constexpr int SBM = 128, SBN = 80, SBK = 64;
 constexpr int kChunkSub = 12;                 // 12 x 64 = 768 K per exact chunk
 constexpr size_t kPlaneBudget = (size_t)16 << 30;   // digit planes of one second-half K chunk
 constexpr int kATile = SBM * SBK * 2;         // 16 KB: one A digit plane of a K subtile
-constexpr int kBTile = SBN * SBK * 2;         // 8 KB: one B digit plane
-constexpr int kBPanel = kSlices * kBTile;     // 48 KB: the six B planes of a K subtile
+constexpr int kBTile = SBN * SBK * 2;         // 10 KB: one B digit plane
+constexpr int kBPanel = kSlices * kBTile;     // 60 KB: the six B planes of a K subtile
 // shared memory: one stage per A plane (6 x 16 KB) and two B panels (2 x 48 KB)
 constexpr int kSmemBytes = kSlices * kATile + 2 * kBPanel + 1024 + 256;
 constexpr long long kWaitNs = 2000000000LL;   // 2 s bound on every wait
@@ -313,12 +317,25 @@ __device__ inline void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ inline void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // ------------------------------------------------------------ GEMM kernel
 __device__ inline void mbar_arrive(uint64_t *b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
 
-constexpr int kThreads = 192;       // warps 0-3 fold and write, warp 4 loads, warp 5 issues MMAs
+// warps 0-7 fold and write (warp w: TMEM lanes 32 (w % 4) .. + 31, columns
+// 40 (w / 4) .. + 39), warp 8 loads, warp 9 issues MMAs
+constexpr int kFoldWarps = 8, kFoldCols = SBN / 2;
+constexpr int kThreads = 32 * (kFoldWarps + 2);
 
 // C[M x N] (FP64, ld ldc) = sum of digit products of A slices (tmA rows
 // i*Mpad + m) and B slices (tmB rows j*Npad + n), K extent per 128-row tile.
@@ -357,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < kSlices; ++i) { mbar_init(afull + i, 1); mbar_init(aempty + i, 1); }
         for (int p = 0; p < 2; ++p) { mbar_init(bfull + p, 1); mbar_init(bempty + p, 1); }
         mbar_init(chunk_bar, 1);
-        mbar_init(folded, 4);
+        mbar_init(folded, kFoldWarps);
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
@@ -367,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp == 4) {
+    if (warp == kFoldWarps) {
         if (lane == 0) {                               // TMA producer
             bool ok = true;
             for (int kt = 0; kt < nk && ok; ++kt) {
@@ -387,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) abort_flag = 1;
         }
-    } else if (warp == 5) {
+    } else if (warp == kFoldWarps + 1) {
         if (lane == 0) {                               // MMA issuer
             bool ok = true;
             const uint64_t da0 = sdesc(su32(base)), db0 = sdesc(su32(bpanel));
@@ -427,11 +444,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             umma_commit(done);                         // also on abort: lets issued MMAs be awaited
             if (!ok) abort_flag = 1;
         }
-    } else {                                           // warps 0-3: rows 32 warp .. + 31
-        long long acc[SBN];
+    } else {                                           // fold warps: 32 rows x 40 columns each
+        long long acc[kFoldCols];
 #pragma unroll
-        for (int j = 0; j < SBN; ++j) acc[j] = 0;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int j = 0; j < kFoldCols; ++j) acc[j] = 0;
+        const int quad = warp & 3, cbase = (warp >> 2) * kFoldCols;
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cbase;
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
             if (!mbar_wait(chunk_bar, (uint32_t)(c & 1)) || *(volatile int *)&abort_flag) {
@@ -443,21 +461,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             // |sums| <= 20 480 * 768 < 2^24: integers exact in FP32 and in 32-bit ints,
             // 32-bit conversions and 64-bit integer adds keep the FP64 pipe free
 #pragma unroll
-            for (int q = 0; q < SBN / 16; ++q) {
-                float v0[16], v1[16], v2[16];
-                tmem_ld16(trow + 0 * SBN + q * 16, v0);
-                tmem_ld16(trow + 1 * SBN + q * 16, v1);
-                tmem_ld16(trow + 2 * SBN + q * 16, v2);
+            for (int q = 0; q < kFoldCols / 8; ++q) {
+                float v0[8], v1[8], v2[8];
+                tmem_ld8(trow + 0 * SBN + q * 8, v0);
+                tmem_ld8(trow + 1 * SBN + q * 8, v1);
+                tmem_ld8(trow + 2 * SBN + q * 8, v2);
 #pragma unroll
-                for (int t = 0; t < 16; ++t)
-                    acc[q * 16 + t] += (long long)__float2int_rn(v0[t]) * 16384 +
-                                       (long long)__float2int_rn(v1[t]) * 128 + (long long)__float2int_rn(v2[t]);
+                for (int t = 0; t < 8; ++t)
+                    acc[q * 8 + t] += (long long)__float2int_rn(v0[t]) * 16384 +
+                                      (long long)__float2int_rn(v1[t]) * 128 + (long long)__float2int_rn(v2[t]);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(folded);
         }
-        const long long m = m0 + warp * 32 + lane;
+        const long long m = m0 + quad * 32 + lane;
         if (ok && nk > 0 && !mbar_wait(done, 0)) ok = false;
         if (!ok) {
             abort_flag = 1;
@@ -465,20 +483,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int er = (m < Mpad) ? rowexp[m] : 0;
 #pragma unroll
-            for (int q = 0; q < SBN / 16; ++q) {
-                float v3[16], v4[16], v5[16];
-                tmem_ld16(trow + 3 * SBN + q * 16, v3);
-                tmem_ld16(trow + 4 * SBN + q * 16, v4);
-                tmem_ld16(trow + 5 * SBN + q * 16, v5);
+            for (int q = 0; q < kFoldCols / 8; ++q) {
+                float v3[8], v4[8], v5[8];
+                tmem_ld8(trow + 3 * SBN + q * 8, v3);
+                tmem_ld8(trow + 4 * SBN + q * 8, v4);
+                tmem_ld8(trow + 5 * SBN + q * 8, v5);
                 if (m < Mvalid) {
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        const long long n = n0 + q * 16 + t;
+                    for (int t = 0; t < 8; ++t) {
+                        const long long n = n0 + cbase + q * 8 + t;
                         if (n < Nvalid) {
                             // diagonals 5, 6, 7 (weights 2^-35, -42, -49) folded in FP32, whose
                             // rounding is ~2^-59 of the result; then acc (weight 2^-28) in FP64
                             const float w = fmaf(v5[t], 0x1p-14f, fmaf(v4[t], 0x1p-7f, v3[t]));
-                            const double v = fma((double)w, 0x1p-7, (double)acc[q * 16 + t]);
+                            const double v = fma((double)w, 0x1p-7, (double)acc[q * 8 + t]);
                             const int k = er + colexp[n] - 28;
                             const double r = (k > -1022 && k < 1023)
                                                  ? v * __longlong_as_double((long long)(k + 1023) << 52)
@@ -489,8 +507,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         } else if (m < Mvalid && !accumulate) {
-            for (int t = 0; t < SBN; ++t)
-                if (n0 + t < Nvalid) C[m * ldc + n0 + t] = 0.0;
+            for (int t = 0; t < kFoldCols; ++t)
+                if (n0 + cbase + t < Nvalid) C[m * ldc + n0 + cbase + t] = 0.0;
         }
     }
     tc_fence_before();
@@ -552,7 +570,7 @@ static void slice_cols(SplitWorkspace &w, int slot, const double *X, long long l
     col_exp_kernel<<<(unsigned)((Cpad + 255) / 256), 256, 0, s>>>(cmax, cols, Cpad, colexp);
     QDT_CHECK_KERNEL("col_exp_kernel");
     __nv_bfloat16 *out = (__nv_bfloat16 *)ws_get(w, slot, (size_t)kSlices * Cpad * Rpad * 2 + (size_t)Cpad * sizeof(int));
-    dim3 g2((unsigned)(Rpad / 64), (unsigned)(Cpad / 32));
+    dim3 g2((unsigned)(Rpad / 64), (unsigned)((Cpad + 31) / 32));
     slice_cols_t_kernel<<<g2, 256, 0, s>>>(X, ld, rows, cols, Rpad, Cpad, colexp, out);
     QDT_CHECK_KERNEL("slice_cols_t_kernel");
 }
