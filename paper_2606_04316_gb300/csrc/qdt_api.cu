@@ -1278,6 +1278,30 @@ void batch_round(qdt_ctx *owner, std::vector<BatchReq> &R, int round, unsigned f
 
 }  // namespace
 
+namespace qdt {
+// Frees the per-transformation workspace of a context (densities, integral
+// rows, partial results, tile lists, split-form digit planes, comparator
+// buffers) and drops captured batch graphs that point into it; the basis
+// tables and coefficients stay.  The server calls it after every request, so
+// a slot does not keep the peak buffers of its largest request.
+void release_workspace(qdt_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    DBuf *bufs[] = {&c->Dbra, &c->Dket, &c->V, &c->Vg, &c->W, &c->Wc, &c->Dmax, &c->wsort, &c->ketsp, &c->ketcol,
+                    &c->prefix, &c->ktile, &c->tasks, &c->O, &c->partial, &c->stage, &c->kpos, &c->prms,
+                    &c->next, &c->ktile2, &c->qcols, &c->qWL, &c->qWS, &c->qT1, &c->qT, &c->qVf, &c->qkt[0],
+                    &c->qkt[1], &c->qkt[2]};
+    for (DBuf *b : bufs) b->release();
+    split_release(c->split);
+    for (GraphEntry &g : c->graph) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = GraphEntry();
+    }
+    cudaGetLastError();
+}
+}  // namespace qdt
+
 extern "C" {
 
 const char *qdt_version(void) { return "qdt 0.1 (sm_103a)"; }

@@ -265,4 +265,8 @@ void launch_quarter_gather(const double *Vf, int n, int P, const int *rsR, const
 void launch_merge_rows(const double *in, const int *m0, const int *m1, int nrows, int rowlen, double *out,
                        cudaStream_t s);
 
+// Frees a context's per-transformation workspace (basis tables and
+// coefficients stay); the request server calls it after every request.
+void release_workspace(qdt_ctx *c);
+
 }  // namespace qdt

@@ -61,6 +61,7 @@ struct Record {
     size_t foot = 0;
     double t_submit = 0, t_done = 0;
     bool done = false;
+    bool retried = false;       // ran out of memory beside other requests: runs again alone
     int status = QDT_OK;
     qdt_stats st{};
 };
@@ -70,6 +71,7 @@ struct Record {
 struct qdt_server {
     int device = 0;
     size_t pool = 0, used = 0;
+    int running = 0;            // requests admitted and not finished
     std::vector<qdt_ctx *> ctx;
     std::vector<BasisCopy> basis;
     std::vector<std::thread> workers;
@@ -90,12 +92,16 @@ void worker(qdt_server *S, int slot) {
         uint64_t id = 0;
         qdt_request r;
         size_t foot = 0;
+        bool others = false;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] {
                 if (S->stop && S->queue.empty()) return true;
                 if (S->queue.empty()) return false;
-                return S->used + S->recs[S->queue.front()].foot <= S->pool;
+                const Record &h = S->recs[S->queue.front()];
+                // a retried request waits until nothing else is admitted
+                if (h.retried) return S->running == 0;
+                return S->used + h.foot <= S->pool;
             });
             if (S->queue.empty()) return;
             id = S->queue.front();
@@ -104,6 +110,8 @@ void worker(qdt_server *S, int slot) {
             r = rec.r;
             foot = rec.foot;
             S->used += foot;
+            S->running++;
+            others = S->running > 1;
         }
         int rc = QDT_OK;
         if (!S->basis[slot].same(r)) {
@@ -116,14 +124,24 @@ void worker(qdt_server *S, int slot) {
         qdt_stats st{};
         if (rc == QDT_OK)
             rc = qdt_transform(c, r.blocks, r.k_begin, r.k_end, r.schwarz_tau, r.precision, r.out, r.out_bytes, &st);
+        // the footprint estimate counts one request per slot: drop this one's workspace
+        qdt::release_workspace(c);
         {
             std::lock_guard<std::mutex> lk(S->mu);
             Record &rec = S->recs[id];
-            rec.status = rc;
-            rec.st = st;
-            rec.t_done = now_s();
-            rec.done = true;
             S->used -= foot;
+            S->running--;
+            if (rc == QDT_ERR_OOM && others && !rec.retried) {
+                // device memory ran out beside other requests (the estimate is not a
+                // bound): queue it first, to run again when nothing else is admitted
+                rec.retried = true;
+                S->queue.push_front(id);
+            } else {
+                rec.status = rc;
+                rec.st = st;
+                rec.t_done = now_s();
+                rec.done = true;
+            }
         }
         S->cv_done.notify_all();
         S->cv_work.notify_all();
