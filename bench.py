@@ -620,6 +620,7 @@ def main():
                     help="density (AO-driven), quarter (O(N^5) Coulomb first half) or mo (MO-driven comparator)")
     ap.add_argument("--mo-block", type=int, default=8, help="MO-driven route: outer MO indices per block")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form (0: skip)")
+    ap.add_argument("--fp64-warmup", type=int, default=1, help="untimed steps of the FP64 form before them")
     ap.add_argument("--e2e-calls", type=int, default=5, help="calls of the end-to-end (host buffers) timing")
     ap.add_argument("--nk-active", type=int, default=0,
                     help="transform only the first N units of the active range (0: all); AO work unchanged")
@@ -721,14 +722,15 @@ def main():
                "timing": "median host wall clock of qdt_set_coefficients + qdt_transform with pinned host buffers"}
 
     # the FP64 form on the same workload, and the agreement of the two forms
+    # (after --fp64-warmup untimed FP64 steps; `out` still holds the last timed
+    # split result, compared with the last FP64 one)
     other = None
     if prec == qdt.SPLIT and args.fp64_steps > 0:
         out64 = torch.zeros_like(out)
         set_coefs(CLd, CSd)
-        ctx.transform(blocks, 0, nK, tau, qdt.FP64, out64)
-        ctx.transform(blocks, 0, nK, tau, prec, out)
+        for _ in range(args.fp64_warmup):
+            ctx.transform(blocks, 0, nK, tau, qdt.FP64, out64)
         torch.cuda.synchronize()
-        diff = float((out - out64).abs().max().item())
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -736,10 +738,12 @@ def main():
             st64 = ctx.transform(blocks, 0, nK, tau, qdt.FP64, out64)
         f1.record(stream)
         torch.cuda.synchronize()
+        diff = float((out - out64).abs().max().item())
         ms64 = f0.elapsed_time(f1) / args.fp64_steps
         other = {"value": n_mo * world / (ms64 / 1e3), "ms_per_step": ms64, "steps": args.fp64_steps,
-                 "phases_ms": {k: st64[k] for k in phase}, "max_abs_diff_split_vs_fp64": diff,
-                 "split_speedup": ms64 / ms}
+                 "warmup": args.fp64_warmup, "phases_ms": {k: st64[k] for k in phase},
+                 "max_abs_diff_split_vs_fp64": diff, "split_speedup": ms64 / ms,
+                 "quartets_kept": st64["quartets_kept"], "flops_eri": st64["flops_eri"]}
 
     pk, src = peaks()
     avg = {k: v / args.steps for k, v in phase.items()}

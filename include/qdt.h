@@ -199,7 +199,7 @@ int qdt_set_route(qdt_ctx *ctx, int route, int mo_block);
  * integral rows are computed twice, in compensated FP32 pairs and in plain
  * FP32, and ratio[c] = max |difference| / (Q_A Q_C) over all entries (Q the
  * Schwarz factors of the bra and ket shell pairs).  The split form lets a
- * quartet run in plain FP32 assuming this ratio stays below 1024 x 2^-24.
+ * quartet run in plain FP32 assuming this ratio stays below 256 x 2^-24.
  * Small inputs only: each class must fit one row batch (QDT_ERR_ARG).
  */
 int qdt_f32_error_ratio(qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end, double tau, double ratio[2]);
@@ -224,7 +224,7 @@ size_t qdt_packed_size(const qdt_ctx *ctx, unsigned blocks, int k_begin, int k_e
  * threshold `schwarz_tau` >= 0 and `precision` QDT_FP64 or QDT_SPLIT.
  * QDT_FP64: integrals and contractions in FP64.  QDT_SPLIT: contractions as
  * Ozaki BF16 slices on the tensor cores with FP64 recombination; integrals in
- * compensated FP32 pairs, except the quartets whose error bound fits a 1e-11
+ * compensated FP32 pairs, except the quartets whose error bound fits a 3e-11
  * budget on every output element, which run in plain FP32 (the environment
  * variable QDT_F32_BUDGET sets the budget, 0 turns it off; stats report the
  * quartets and the bound).  Held to 1e-10 Eh of the FP64 form.

@@ -1106,8 +1106,16 @@ __global__ void __launch_bounds__(256, 2) eri_rows_kernel(const EriParams *prms,
             const int cd_id = prm.ket_sp[kp];
             const PairDev CD = prm.pairs[cd_id];
             const long long col = prm.ket_col[kp];
-            // (CD|AB) also kept?  Then the lower pair id computes both blocks.
-            const bool rev = prm.sym && cd_id != tk.bra_sp && prm.ket_pos[tk.bra_sp] < prm.prefix[cd_id];
+            // (CD|AB) also kept?  Then one block serves both (EriParams::sym):
+            // rev writes it at (cd, ab) of W, mir into W2 for a later batch
+            const bool both = prm.sym && cd_id != tk.bra_sp && prm.ket_pos[tk.bra_sp] < prm.prefix[cd_id];
+            bool rev = both, mir = false;
+            if (both && prm.sym == 2) {
+                const int bp = prm.bra_pos[cd_id];
+                if (bp < prm.b0) continue;           // its transpose came from W2 of CD's batch
+                rev = bp < prm.b1;
+                mir = !rev;
+            }
             if (rev && cd_id < tk.bra_sp) continue;
             const long long col_rev = rev ? prm.ket_col[prm.ket_pos[tk.bra_sp]] : 0;
             // contract the orientation with the smaller cost; swapped -> G is (CD|AB)
@@ -1135,37 +1143,29 @@ __global__ void __launch_bounds__(256, 2) eri_rows_kernel(const EriParams *prms,
                         const int xx = idx / ych, yy = idx - xx * ych;
                         const int a = swap ? y0 + yy : x0 + xx;      // bra function pair
                         const int c = swap ? x0 + xx : y0 + yy;      // ket function pair
-                        const long long row = AB.rowoff + a - row0;
-                        const long long cc = col + c;
-                        if (!GAUGE) {
-                            W[row * ldw + cc] = b.G[idx];
-                        } else {
-                            const double C = b.G[idx];
-                            const double *Hh = b.G + (size_t)xch * ych;
-                            for (int I = 0; I < 3; ++I)
-                                for (int J = 0; J < 3; ++J) {
-                                    // K_IJ is symmetric, so the swapped block needs no index change
-                                    const double h = Hh[(size_t)ij_of[I][J] * xch * ych + idx];
-                                    W[(row * 3 + I) * ldw + cc * 3 + J] = (I == J ? C : 0.0) - h;
-                                }
-                            if (wc) Wc[row * ldwc + cc] = C;
-                        }
-                        if (rev) {    // the same integrals at (cd, ab): rows of CD, columns of AB
-                            const long long row2 = CD.rowoff + c - row0;
-                            const long long cc2 = col_rev + a;
+                        // the block's entry into row `r`, column `k` of an output
+                        // (gauge: rows (r, I), columns (k, J); K_IJ is symmetric, so the
+                        // transposed entry needs no index change)
+                        auto put = [&](double *Wo, long long ldo, double *Wco, long long ldco, long long r,
+                                       long long k) {
                             if (!GAUGE) {
-                                W[row2 * ldw + cc2] = b.G[idx];
+                                Wo[r * ldo + k] = b.G[idx];
                             } else {
                                 const double C = b.G[idx];
                                 const double *Hh = b.G + (size_t)xch * ych;
                                 for (int I = 0; I < 3; ++I)
                                     for (int J = 0; J < 3; ++J) {
                                         const double h = Hh[(size_t)ij_of[I][J] * xch * ych + idx];
-                                        W[(row2 * 3 + I) * ldw + cc2 * 3 + J] = (I == J ? C : 0.0) - h;
+                                        Wo[(r * 3 + I) * ldo + k * 3 + J] = (I == J ? C : 0.0) - h;
                                     }
-                                if (wc) Wc[row2 * ldwc + cc2] = C;
+                                if (wc) Wco[r * ldco + k] = C;
                             }
-                        }
+                        };
+                        put(W, ldw, Wc, ldwc, AB.rowoff + a - row0, col + c);
+                        // the same integrals at (cd, ab): rows of CD, columns of AB
+                        if (rev) put(W, ldw, Wc, ldwc, CD.rowoff + c - row0, col_rev + a);
+                        if (mir) put(prm.W2, prm.ldw2, prm.Wc2, prm.ldwc2, CD.rowoff + c - prm.row2,
+                                     prm.col2[tk.bra_sp] + a);
                     }
                     __syncthreads();
                 }

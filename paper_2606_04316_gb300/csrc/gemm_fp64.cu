@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(256) dgemm_nn_ragged(const double *__restrict_
                                                        const double *__restrict__ B, long long ldb,
                                                        double *__restrict__ C, long long ldc,
                                                        long long M, long long N,
-                                                       const long long *__restrict__ ktile) {
+                                                       const long long *__restrict__ ktile, int accumulate) {
     __shared__ double As[TK][TM + 1];
     __shared__ double Bs[TK][TN];
     const long long m0 = (long long)blockIdx.y * TM, n0 = (long long)blockIdx.x * TN;
@@ -56,17 +56,17 @@ __global__ void __launch_bounds__(256) dgemm_nn_ragged(const double *__restrict_
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             long long r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
-            if (r < M && c < N) C[r * ldc + c] = acc[i][j];
+            if (r < M && c < N) C[r * ldc + c] = accumulate ? C[r * ldc + c] + acc[i][j] : acc[i][j];
         }
 }
 
 void gemm_fp64_nn_ragged(const double *A, long long lda, const double *B, long long ldb, double *C,
                          long long ldc, long long M, long long N, const long long *ktile, int tileM,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool accumulate) {
     if (M <= 0 || N <= 0) return;
     if (tileM != TM) throw Error{QDT_ERR_ARG, "ragged GEMM tile mismatch"};
     dim3 grid((unsigned)((N + TN - 1) / TN), (unsigned)((M + TM - 1) / TM));
-    dgemm_nn_ragged<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, ktile);
+    dgemm_nn_ragged<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, ktile, accumulate ? 1 : 0);
     QDT_CHECK_LAUNCH();
 }
 

@@ -112,6 +112,11 @@ void split_invalidate(SplitWorkspace &w) {
     w.bnext = 0;      // every class fills the slots in the same order, call after call
 }
 
+void split_forget(SplitWorkspace &w, const void *lo, const void *hi) {
+    for (int q = 0; q < 2; ++q)
+        if (w.bkey[q].ptr >= lo && w.bkey[q].ptr < hi) w.bkey[q] = SplitKey();
+}
+
 static inline long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
 
 // ------------------------------------------------------------ digits
@@ -643,9 +648,9 @@ __global__ void tile_extent_kernel(const long long *kt64, long long n64, int rat
 
 void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B, long long ldb,
                 double *C, long long ldc, long long M, long long N, const long long *d_ktile,
-                const std::vector<long long> &h_ktile, cudaStream_t s) {
+                const std::vector<long long> &h_ktile, cudaStream_t s, bool accumulate) {
     if (precision != QDT_SPLIT) {
-        gemm_fp64_nn_ragged(A, lda, B, ldb, C, ldc, M, N, d_ktile, gemm_fp64_tile_m(), s);
+        gemm_fp64_nn_ragged(A, lda, B, ldb, C, ldc, M, N, d_ktile, gemm_fp64_tile_m(), s, accumulate);
         return;
     }
     if (M <= 0 || N <= 0) return;
@@ -691,7 +696,8 @@ void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda
         w.bkey[slot] = key;
     }
     char *bb = (char *)w.buf[WS_B0 + slot];
-    run_umma(w, Asl, Mpad, KpadA, bb, Npad, KpadB, d_kt, rowexp, (const int *)(bb + bslice), C, ldc, M, N, 0, s);
+    run_umma(w, Asl, Mpad, KpadA, bb, Npad, KpadB, d_kt, rowexp, (const int *)(bb + bslice), C, ldc, M, N,
+             accumulate ? 2 : 0, s);
 }
 
 void gemm_half2(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B, long long ldb,

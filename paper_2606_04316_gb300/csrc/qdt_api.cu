@@ -73,7 +73,7 @@ T *dcopy(DBuf &b, const std::vector<T> &v, cudaStream_t s) {
 }
 
 struct ClassBufs {
-    DBuf pairs, pp, E, E2, E1, Q, bra, pp_pair;
+    DBuf pairs, pp, E, E2, E1, Q, bra, brapos, pp_pair;
 };
 
 // Instantiated graph of a batch round and the signature it was captured for.
@@ -107,6 +107,9 @@ struct qdt_ctx {
     // per-transform workspace
     DBuf Dbra, Dket, V, Vg, W, Wc, Dmax, wsort, ketsp, ketcol, prefix, ktile, tasks, O, partial,
         stage, rsR, rsS, kpos, prms, next, ktile2;
+    // row batches with bra-ket symmetry: transposed blocks for later rows, their
+    // tile extents, the W2 column of each batch pair and the batch's density rows
+    DBuf W2, Wc2, ktile3, ktile4, col2, ketsp2, ketcol2, Dbra2;
     SplitWorkspace split;
     // first-half route of the Coulomb block: density (Eq. firsthalf) or the
     // two-quarter comparator, and the comparator's workspace
@@ -377,6 +380,9 @@ void build_class(qdt_ctx *ctx, int c) {
     QDT_CUDA_TRY(cudaMemcpyAsync(pc.d_pairs, pc.h_pairs.data(), pc.nsp * sizeof(PairDev),
                                  cudaMemcpyHostToDevice, s));
     pc.d_bra_order = dcopy(b.bra, pc.bra_order, s);
+    pc.bra_pos.assign(pc.nsp, 0);
+    for (int k = 0; k < pc.nsp; ++k) pc.bra_pos[pc.bra_order[k]] = k;
+    pc.d_bra_pos = dcopy(b.brapos, pc.bra_pos, s);
     QDT_CUDA_TRY(cudaStreamSynchronize(s));
 }
 
@@ -410,6 +416,8 @@ struct ClassPlan {
     int k0 = 0, nKa = 0, precision = 0, nRS = 0, mult = 1;
     double tau = 0;
     bool ls = false, one_batch = true;
+    bool mirror = false;      // row batches with bra-ket symmetry (EriParams::sym 2)
+    bool mo_blocks = false;   // MO-driven route in blocks: row batches without symmetry
     bool ku = false;          // columns are spinor pairs with 2 parts (Kramers-unrestricted input)
     bool quarter = false;     // Coulomb first half by two quarter steps (no ket density)
     int2 *qcols = nullptr;    // function indices of the ket-ordered integral columns
@@ -510,8 +518,9 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
 
 // Split form: which kept quartets may have their integrals in plain FP32.
 // An integral computed in FP32 from FP64 Boys values and prefactors is taken
-// to be within kF32Rel Q_A Q_C of its FP64 value (kF32Rel = 1024 x 2^-24;
-// `tests/test_gpu_dynprec.py` measures the actual ratio).  An error d in
+// to be within kF32Rel Q_A Q_C of its FP64 value (kF32Rel = 256 x 2^-24,
+// 23x the largest ratio measured on s/p/d quartets up to L = 12, 6.7e-7;
+// `tests/test_gpu_dynprec.py` requires the measured ratio to stay 8x below it).  An error d in
 // (ab|cd) moves a packed output element by at most |D_ab| d |D_cd| (times
 // g: 1 Coulomb, 3 Gaunt (three J), 18 gauge (nine IJ, two terms)), so the
 // FP32 quartets of a class add at most
@@ -521,8 +530,10 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
 // same decision for (C, A), so bra-ket symmetry is kept); t is the largest
 // threshold whose bound stays within kF32Budget.  QDT_F32_BUDGET overrides
 // the budget (0 turns the FP32 quartets off).
-constexpr double kF32Rel = 1024.0 / 16777216.0;
-constexpr double kF32Budget = 1e-11;
+constexpr double kF32Rel = 256.0 / 16777216.0;
+// A third of the split form's 1e-10 bar against the FP64 form; the slice
+// contractions add about 3e-13 on the 40-centre chain.
+constexpr double kF32Budget = 3e-11;
 
 double f32_budget() {
     if (const char *e = std::getenv("QDT_F32_BUDGET")) {
@@ -557,6 +568,13 @@ size_t w_budget_override() {
     const long long v = std::atoll(e);
     if (v <= 0) throw Error{QDT_ERR_ARG, "QDT_W_BUDGET must be a positive byte count"};
     return (size_t)v;
+}
+
+// QDT_BATCH_SYM=0 runs row batches without bra-ket symmetry (every kept block
+// computed in its own row's batch), for comparison.
+bool batch_sym_enabled() {
+    const char *e = std::getenv("QDT_BATCH_SYM");
+    return !(e && e[0] == '0');
 }
 
 // Waits for class_issue; kept-quartet statistics, V buffers and the row-batch
@@ -602,9 +620,17 @@ void class_finish(qdt_ctx *ctx, ClassPlan &P, qdt_stats *st) {
     // what the decision counted as reusable is handed back first
     if (P.one_batch && (double)wall * wfac + slices > 0.7 * (double)(fr + ctx->W.n + ctx->Wc.n)) split_release(ctx->split);
     P.wbudget = P.one_batch ? wall : (forced ? forced : ((size_t)6 << 30));
+    // row batches of the AO-driven density route keep bra-ket symmetry (each
+    // kept pair of blocks computed once, the transpose contracted into the later
+    // rows); their budget covers W and W2
+    P.mirror = !P.one_batch && !P.quarter && !P.mo_blocks && batch_sym_enabled();
+    if (P.mirror && !forced) {
+        const double room = (double)usable - slices;
+        P.wbudget = (size_t)std::max(2.0 * (1 << 30), std::min(24.0 * (1 << 30), room));
+    }
     P.h_kpos.assign(pc.nsp, 0);
     for (int q = 0; q < pc.nsp; ++q) P.h_kpos[P.h_ketsp[q]] = q;
-    P.d_kpos = P.one_batch ? dcopy(ctx->kpos, P.h_kpos, s) : nullptr;
+    P.d_kpos = (P.one_batch || P.mirror) ? dcopy(ctx->kpos, P.h_kpos, s) : nullptr;
 }
 
 // One batch of bra rows of a class.
@@ -616,7 +642,81 @@ struct RowBatch {
     std::vector<int> bras;                  // the batch's bra pairs, in bra order
     std::vector<long long> kt, kg;          // K extents of the 64-row tiles (gauge/Coulomb rows, Gaunt rows)
     long long *d_kt = nullptr, *d_kg = nullptr;
+    // bra-ket symmetry across batches (ClassPlan::mirror): W2 [(later rows)][(batch pairs in
+    // ket order)], its Gaunt companion Wc2, their tile extents, and the batch's density rows
+    // in the same order (Dbra2)
+    long long row2 = 0, rows2 = 0, ld2 = 1, ldw2 = 1;
+    double *W2 = nullptr, *Wc2 = nullptr, *Dbra2 = nullptr;
+    std::vector<long long> kt2, kg2;
+    long long *d_kt2 = nullptr, *d_kg2 = nullptr;
 };
+
+// Bra-ket symmetry across row batches (ClassPlan::mirror): a kept block
+// (AB|CD) with CD in a later batch whose (CD|AB) is kept too is computed once,
+// in AB's batch, and its transpose written into W2, whose rows are the later
+// rows and whose columns are this batch's pairs in ket (w-sorted) order; the
+// first half then adds W2 D(batch rows) into the later rows of V.  Row CD's
+// entries are those of the batch pairs AB with kpos(AB) < prefix(CD): a prefix
+// of the columns, so each 64-row tile of W2 has a K extent as W does.
+void batch_prepare_mirror(qdt_ctx *ctx, const ClassPlan &P, RowBatch &B) {
+    PairClass &pc = ctx->cls[P.cr.c];
+    cudaStream_t s = ctx->stream;
+    const int TMr = gemm_fp64_tile_m();
+    const int mult = P.mult;
+    B.row2 = B.row0 + B.rows;
+    B.rows2 = P.M - B.row2;
+    // this batch's pairs in ket order, their W2 columns
+    std::vector<int> k2(B.bras);
+    std::sort(k2.begin(), k2.end(), [&](int x, int y) { return P.h_kpos[x] < P.h_kpos[y]; });
+    std::vector<long long> col2(pc.nsp, 0), kcol(k2.size()), kend(k2.size());
+    std::vector<int> kk(k2.size());
+    long long off = 0;
+    for (size_t i = 0; i < k2.size(); ++i) {
+        col2[k2[i]] = off;
+        kcol[i] = off;
+        kk[i] = P.h_kpos[k2[i]];
+        off += pc.h_pairs[k2[i]].nfp;
+        kend[i] = off;
+    }
+    B.ld2 = std::max<long long>(off, 1);
+    B.ldw2 = B.ld2 * mult;
+    const bool gaunt_too = P.ls && P.cr.gauge && P.cr.gaunt;
+    B.W2 = (double *)ctx->W2.get((size_t)std::max<long long>(B.rows2, 1) * mult * B.ldw2 * sizeof(double));
+    if (gaunt_too) B.Wc2 = (double *)ctx->Wc2.get((size_t)std::max<long long>(B.rows2, 1) * B.ld2 * sizeof(double));
+    // tile extents of W2 (rows (cd, I) in units of mult) and of Wc2
+    const long long Wrows2 = B.rows2 * mult;
+    B.kt2.assign((size_t)((Wrows2 + TMr - 1) / TMr), 0);
+    if (gaunt_too) B.kg2.assign((size_t)((B.rows2 + TMr - 1) / TMr), 0);
+    for (int k = B.b1; k < pc.nsp; ++k) {
+        const int cd = pc.bra_order[k];
+        const PairDev &pr = pc.h_pairs[cd];
+        // batch pairs AB with kpos(AB) < prefix(CD)
+        const size_t n = (size_t)(std::lower_bound(kk.begin(), kk.end(), P.h_prefix[cd]) - kk.begin());
+        const long long ext = n ? kend[n - 1] : 0;
+        if (!ext) continue;
+        const long long r0 = pr.rowoff - B.row2;
+        for (long long t = r0 * mult / TMr; t <= ((r0 + pr.nfp) * mult - 1) / TMr; ++t)
+            B.kt2[t] = std::max(B.kt2[t], ext * mult);
+        if (gaunt_too)
+            for (long long t = r0 / TMr; t <= (r0 + pr.nfp - 1) / TMr; ++t) B.kg2[t] = std::max(B.kg2[t], ext);
+    }
+    B.d_kt2 = dcopy(ctx->ktile3, B.kt2, s);
+    if (gaunt_too) B.d_kg2 = dcopy(ctx->ktile4, B.kg2, s);
+    else { B.kg2 = B.kt2; B.d_kg2 = B.d_kt2; }
+    // the batch's density rows in W2 column order
+    int *d_k2 = dcopy(ctx->ketsp2, k2, s);
+    long long *d_kcol = dcopy(ctx->ketcol2, kcol, s);
+    B.Dbra2 = (double *)ctx->Dbra2.get((size_t)B.ld2 * P.ncolD * sizeof(double));
+    launch_gather_rows(P.Dbra, pc.d_pairs, d_k2, d_kcol, (int)k2.size(), P.ncolD, B.Dbra2, s);
+    ctx->launches++;
+    EriParams &prm = B.prm;
+    prm.W2 = B.W2;
+    prm.ldw2 = B.ldw2;
+    prm.row2 = B.row2;
+    prm.Wc2 = B.Wc2;
+    prm.ldwc2 = B.ld2;
+    prm.col2 = dcopy(ctx->col2, col2, s);
+}
 
 // Next batch from bra position b0: sizes, integral-row buffers, the integral
 // kernel's parameters and the tile extents (uploaded to the context).
@@ -629,12 +729,19 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
     B.b0 = b0;
     long long rows = 0, kmax = 0;
     int b1 = b0;
+    const long long row_b0 = pc.h_pairs[pc.bra_order[b0]].rowoff;
+    const bool gaunt_too = P.ls && P.cr.gauge && P.cr.gaunt;
     while (b1 < pc.nsp) {      // grow the batch while the W block fits the budget
         const PairDev &pr = pc.h_pairs[pc.bra_order[b1]];
         long long k = std::max(kmax, P.Krow[pc.bra_order[b1]]);
-        size_t need = (size_t)(rows + pr.nfp) * mult * (size_t)std::max<long long>(k, 1) * mult * sizeof(double);
-        if (b1 > b0 && need > P.wbudget) break;
-        rows += pr.nfp;
+        const long long r = rows + pr.nfp;
+        double need = (double)r * mult * (double)std::max<long long>(k, 1) * mult * sizeof(double);
+        if (P.mirror) {      // plus W2 over the later rows, and the Gaunt companions
+            need += (double)(P.M - row_b0 - r) * mult * (double)r * mult * sizeof(double);
+            if (gaunt_too) need *= 10.0 / 9.0;
+        }
+        if (b1 > b0 && need > (double)P.wbudget) break;
+        rows = r;
         kmax = k;
         ++b1;
     }
@@ -663,9 +770,12 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
     prm.with_coulomb = B.Wc ? 1 : 0;
     prm.Wc = B.Wc;
     prm.ldwc = B.ldwc;
-    prm.sym = P.one_batch ? 1 : 0;
+    prm.sym = P.one_batch ? 1 : (P.mirror ? 2 : 0);
     prm.ket_pos = P.d_kpos;
     prm.prefix = P.prefix;
+    prm.bra_pos = pc.d_bra_pos;
+    prm.b0 = b0;
+    prm.b1 = b1;
     B.bras.assign(pc.bra_order.begin() + b0, pc.bra_order.begin() + b1);
     // per-tile K extents (rows in units of W rows)
     const long long Wrows = rows * mult;
@@ -689,6 +799,7 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
         B.kg = B.kt;
         B.d_kg = B.d_kt;
     }
+    if (P.mirror) batch_prepare_mirror(ctx, P, B);
 }
 
 // Integral values, E R E flops and first-half flops of a batch.
@@ -707,7 +818,12 @@ void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, long long 
         for (int q = 0; q < P.h_prefix[sp]; ++q) {
             const int cid = P.h_ketsp[q];
             const PairDev &cd = pc.h_pairs[cid];
-            if (P.one_batch && cid < sp && P.h_kpos[sp] < P.h_prefix[cid]) continue;
+            const bool both = cid != sp && P.h_kpos[sp] < P.h_prefix[cid];      // (CD|AB) kept too
+            if (P.one_batch && both && cid < sp) continue;
+            if (P.mirror && both) {
+                const int bp = pc.bra_pos[cid];
+                if (bp < B.b0 || (bp < B.b1 && cid < sp)) continue;
+            }
             const double f = 2.0 * std::min(orient_cost_h(ab, cd, gauge), orient_cost_h(cd, ab, gauge));
             fl += f;
             if (B.prm.E2 && q >= P.h_split[sp]) fl32 += f;
@@ -726,6 +842,18 @@ void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, long long 
         double fg = 0;
         for (int k = B.b0; k < B.b1; ++k) fg += (double)pc.h_pairs[pc.bra_order[k]].nfp * P.Krow[pc.bra_order[k]];
         st->flops_half1 += 2.0 * fg * 3 * width;
+    }
+    if (P.mirror) {         // the transposed blocks into the later rows
+        double f2 = 0;
+        for (long long t = 0; t < (long long)B.kt2.size(); ++t)
+            f2 += (double)std::min<long long>(TMr, B.rows2 * P.mult - t * TMr) * B.kt2[t];
+        st->flops_half1 += 2.0 * f2 * ncols;
+        if (P.ls && P.cr.gaunt) {
+            double fg2 = 0;
+            for (long long t = 0; t < (long long)B.kg2.size(); ++t)
+                fg2 += (double)std::min<long long>(TMr, B.rows2 - t * TMr) * B.kg2[t];
+            st->flops_half1 += 2.0 * fg2 * 3 * width;
+        }
     }
 }
 
@@ -748,7 +876,7 @@ long long split_chunk_rows(long long ldw) {
 // chunks outside them, so each column chunk of the density is sliced once.
 void half1_rows(qdt_ctx *ctx, int precision, const double *W, long long ldw, const double *B, long long ldb,
                 double *C, long long ldc, long long rows, long long N, const long long *d_kt,
-                const std::vector<long long> &kt, cudaStream_t s) {
+                const std::vector<long long> &kt, cudaStream_t s, bool accumulate = false) {
     const int TMr = gemm_fp64_tile_m();
     const bool split = precision == QDT_SPLIT;
     const long long chunk = split ? split_chunk_rows(ldw) : std::max<long long>(rows, 1);
@@ -769,7 +897,7 @@ void half1_rows(qdt_ctx *ctx, int precision, const double *W, long long ldw, con
             const size_t t0 = (size_t)(r0 / TMr), t1 = std::min(kt.size(), (size_t)((r0 + m + TMr - 1) / TMr));
             const std::vector<long long> sub(kt.begin() + t0, kt.begin() + t1);
             gemm_half1(ctx->split, precision, W + r0 * ldw, ldw, B + n0, ldb, C + r0 * ldc + n0, ldc, m, nw,
-                       d_kt + t0, sub, s);
+                       d_kt + t0, sub, s, accumulate);
             ctx->launches++;
         }
     }
@@ -781,15 +909,16 @@ void half1_rows(qdt_ctx *ctx, int precision, const double *W, long long ldw, con
 void batch_half1(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, long long c0, long long c1,
                  cudaStream_t s) {
     const long long N4 = P.N4, w = c1 - c0;
+    const bool acc = P.mirror;      // earlier batches' transposed blocks are already in V
     if (!P.ls) {
         half1_rows(ctx, P.precision, B.W, B.ldw, P.Dket + c0, N4, P.Vc + B.row0 * N4 + c0, N4, B.rows, w, B.d_kt,
-                   B.kt, s);
+                   B.kt, s, acc);
         return;
     }
     if (P.cr.gauge) {
         // gauge: rows (ab, I), K (cd, J): D_ket viewed as [(cd, J)][4 nRS]
         half1_rows(ctx, P.precision, B.W, B.ldw, P.Dket + c0, N4, P.Vg + B.row0 * 3 * N4 + c0, N4, B.rows * 3, w,
-                   B.d_kt, B.kt, s);
+                   B.d_kt, B.kt, s, acc);
     }
     if (P.cr.gaunt) {
         // Gaunt: Coulomb integrals over L-S pairs, columns (J, RS, part)
@@ -797,12 +926,35 @@ void batch_half1(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, long long 
         const long long ldg = P.cr.gauge ? B.ldwc : B.ldw;
         if (w == N4) {
             half1_rows(ctx, P.precision, Wg, ldg, P.Dket, 3 * N4, P.Vc + B.row0 * 3 * N4, 3 * N4, B.rows, 3 * N4,
-                       B.d_kg, B.kg, s);
+                       B.d_kg, B.kg, s, acc);
         } else {
             for (int J = 0; J < 3; ++J)
                 half1_rows(ctx, P.precision, Wg, ldg, P.Dket + J * N4 + c0, 3 * N4,
-                           P.Vc + B.row0 * 3 * N4 + J * N4 + c0, 3 * N4, B.rows, w, B.d_kg, B.kg, s);
+                           P.Vc + B.row0 * 3 * N4 + J * N4 + c0, 3 * N4, B.rows, w, B.d_kg, B.kg, s, acc);
         }
+    }
+}
+
+// The transposed blocks of a batch (ClassPlan::mirror): V[later rows] +=
+// W2 Dbra2, with Dbra2 the batch's density rows in W2's column order (all
+// density columns: the mirror path is the AO-driven route's).
+void batch_half1_mirror(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, cudaStream_t s) {
+    if (B.rows2 <= 0) return;
+    const long long N4 = P.N4;
+    split_forget(ctx->split, B.Dbra2, B.Dbra2 + B.ld2 * P.ncolD);     // new rows in the same buffer
+    if (!P.ls) {
+        half1_rows(ctx, P.precision, B.W2, B.ldw2, B.Dbra2, N4, P.Vc + B.row2 * N4, N4, B.rows2, N4, B.d_kt2, B.kt2,
+                   s, true);
+        return;
+    }
+    if (P.cr.gauge)
+        half1_rows(ctx, P.precision, B.W2, B.ldw2, B.Dbra2, N4, P.Vg + B.row2 * 3 * N4, N4, B.rows2 * 3, N4,
+                   B.d_kt2, B.kt2, s, true);
+    if (P.cr.gaunt) {
+        const double *Wg = P.cr.gauge ? B.Wc2 : B.W2;
+        const long long ldg = P.cr.gauge ? B.ld2 : B.ldw2;
+        half1_rows(ctx, P.precision, Wg, ldg, B.Dbra2, 3 * N4, P.Vc + B.row2 * 3 * N4, 3 * N4, B.rows2, 3 * N4,
+                   B.d_kg2, B.kg2, s, true);
     }
 }
 
@@ -915,6 +1067,10 @@ void run_batches(qdt_ctx *ctx, ClassPlan &P, long long c0, long long c1, qdt_sta
                  double &ms_eri, double &ms_h1) {
     PairClass &pc = ctx->cls[P.cr.c];
     cudaStream_t s = ctx->stream;
+    if (P.mirror) {     // every batch adds into V (its own rows and, transposed, the later ones)
+        if (P.Vc) launch_zero(P.Vc, P.M * P.NV, s);
+        if (P.Vg) launch_zero(P.Vg, 3 * P.M * P.N4, s);
+    }
     int b0 = 0;
     while (b0 < pc.nsp) {
         RowBatch B;
@@ -929,15 +1085,19 @@ void run_batches(qdt_ctx *ctx, ClassPlan &P, long long c0, long long c1, qdt_sta
         int te = tm.n; tm.mark();
         launch_zero(B.W, B.rows * P.mult * B.ldw, s);
         if (B.Wc) launch_zero(B.Wc, B.rows * B.ldwc, s);
+        if (B.W2) launch_zero(B.W2, B.rows2 * P.mult * B.ldw2, s);
+        if (B.Wc2) launch_zero(B.Wc2, B.rows2 * B.ld2, s);
         launch_eri(d_prm, d_tk, (int)tk.size(), (int *)ctx->next.get(sizeof(int)), shape, B.prm.gauge != 0, df, how,
                    s);
         ctx->launches += 2 + (B.Wc ? 1 : 0);
         batch_stats(ctx, P, B, c1 - c0, st);
         int th = tm.n; tm.mark();
-        if (P.quarter)
+        if (P.quarter) {
             quarter_half1(ctx, P, B, st, s);
-        else
+        } else {
             batch_half1(ctx, P, B, c0, c1, s);
+            if (P.mirror) batch_half1_mirror(ctx, P, B, s);
+        }
         int tend = tm.n; tm.mark();
         QDT_CUDA_TRY(cudaStreamSynchronize(s));
         ms_eri += tm.ms(te, th);
@@ -973,6 +1133,7 @@ void run_class(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, in
             ctx->launches++;
             order_kets(ctx, P, s);
             split_invalidate(ctx->split);
+            P.mo_blocks = true;
             class_finish(ctx, P, st);
             run_batches(ctx, P, c0, c1, st, tm, ms_eri, ms_h1);
         }
@@ -1291,7 +1452,8 @@ void release_workspace(qdt_ctx *c) {
     DBuf *bufs[] = {&c->Dbra, &c->Dket, &c->V, &c->Vg, &c->W, &c->Wc, &c->Dmax, &c->wsort, &c->ketsp, &c->ketcol,
                     &c->prefix, &c->ktile, &c->tasks, &c->O, &c->partial, &c->stage, &c->kpos, &c->prms,
                     &c->next, &c->ktile2, &c->qcols, &c->qWL, &c->qWS, &c->qT1, &c->qT, &c->qVf, &c->qkt[0],
-                    &c->qkt[1], &c->qkt[2]};
+                    &c->qkt[1], &c->qkt[2], &c->W2, &c->Wc2, &c->ktile3, &c->ktile4, &c->col2, &c->ketsp2,
+                    &c->ketcol2, &c->Dbra2};
     for (DBuf *b : bufs) b->release();
     split_release(c->split);
     for (GraphEntry &g : c->graph) {

@@ -143,6 +143,8 @@ struct PairClass {
     float *d_E1 = nullptr;      // the high parts alone, for the quartets run in plain FP32
     double *d_Q = nullptr;
     int *d_bra_order = nullptr;
+    std::vector<int> bra_pos;   // bra position of every shell pair (inverse of bra_order)
+    int *d_bra_pos = nullptr;
     long long npp_total = 0, e_total = 0;
     int maxnfp = 0, maxLab = 0, maxnpp = 0;
 };
@@ -165,11 +167,25 @@ struct EriParams {
     int with_coulomb;           // gauge mode: also write the plain Coulomb block
     double *Wc;                 // gauge mode: Coulomb block output (may be null)
     long long ldwc;
-    // bra-ket symmetry (all rows in one batch): (CD|AB) is written from the
-    // (AB|CD) block when both survive; the task of the lower pair id computes it
+    // bra-ket symmetry: when (AB|CD) and (CD|AB) both survive, one block
+    // serves both.  sym 1 (all rows in one batch): the task of the lower pair
+    // id computes it and writes both.  sym 2 (row batches b0 <= bra position <
+    // b1): a ket pair CD of the same batch as in sym 1; of a later batch, the
+    // block is computed here and its transpose written into W2 (rows of the
+    // later pairs, columns of this batch's pairs), which the first half
+    // contracts into the later rows; of an earlier batch, skipped (its
+    // transpose came from W2 of that batch).
     int sym;
     const int *ket_pos;         // sorted ket position of every pair id
     const int *prefix;          // kept ket prefix length of every pair id
+    const int *bra_pos;         // sym 2: bra position of every pair id
+    int b0, b1;                 // sym 2: this batch's bra positions
+    double *W2;                 // sym 2: transposed blocks for later rows (gauge: 9 components)
+    long long ldw2;
+    long long row2;             // bra-order row of W2's first row (the first row after the batch)
+    double *Wc2;                // sym 2, gauge mode: transposed plain Coulomb blocks (may be null)
+    long long ldwc2;
+    const long long *col2;      // sym 2: W2 column of every pair id of the batch
 };
 
 struct EriTask {                // one tile: bra shell pair x range of sorted ket positions
@@ -228,9 +244,10 @@ void launch_gather_rows(const double *src, const PairDev *pairs, const int *ket_
                         cudaStream_t s);
 
 // GEMMs
+// C (=, or += with accumulate) A B, K per 64-row tile from ktile.
 void gemm_fp64_nn_ragged(const double *A, long long lda, const double *B, long long ldb,
                          double *C, long long ldc, long long M, long long N,
-                         const long long *ktile, int tileM, cudaStream_t s);
+                         const long long *ktile, int tileM, cudaStream_t s, bool accumulate = false);
 void gemm_fp64_tn_sym(const double *A, long long lda, const double *B, long long ldb, double *C,
                       long long N, long long K, double *partial, size_t partial_elems,
                       cudaStream_t s);

@@ -42,10 +42,16 @@ void split_end_deferred(SplitWorkspace &w, cudaStream_t s);
 // given limit; true when the wait gave up and reported it (the expected case).
 bool split_wait_probe(SplitWorkspace &w, double limit_s, cudaStream_t s);
 
-// C[M x N] = A[M x K_t] B[K_t x N], K_t from the per-64-row-tile extents.
+// Drop the cached slices of the first-half B operands inside [lo, hi)
+// (a buffer whose contents change).
+void split_forget(SplitWorkspace &w, const void *lo, const void *hi);
+
+// C[M x N] = A[M x K_t] B[K_t x N] (+= with accumulate), K_t from the
+// per-64-row-tile extents.
 void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B,
                 long long ldb, double *C, long long ldc, long long M, long long N,
-                const long long *d_ktile, const std::vector<long long> &h_ktile, cudaStream_t s);
+                const long long *d_ktile, const std::vector<long long> &h_ktile, cudaStream_t s,
+                bool accumulate = false);
 
 // C[N x N] += A^T B over K rows (upper block tiles valid).
 void gemm_half2(SplitWorkspace &w, int precision, const double *A, long long lda, const double *B,

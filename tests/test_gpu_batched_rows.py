@@ -1,8 +1,10 @@
 """The row-batched path of a transformation: when a class's integral rows do
-not fit one batch, they run in batches of bra rows without bra-ket symmetry
-(large systems take this path).  QDT_W_BUDGET forces it on a small input;
-both forms, all three blocks, against the oracle and against the one-batch
-result."""
+not fit one batch, they run in batches of bra rows (large systems take this
+path).  Bra-ket symmetry holds across batches: a block whose mirror is kept
+too is computed once and its transpose contracted into the later rows.
+QDT_W_BUDGET forces the path on a small input, QDT_BATCH_SYM=0 turns the
+symmetry off; both forms, all three blocks, against the oracle and against
+the one-batch result."""
 import os
 
 import numpy as np
@@ -23,11 +25,14 @@ def torch_cuda():
     return torch
 
 
-def run(p, blocks, precision, budget=None):
+def run(p, blocks, precision, budget=None, sym=True):
     from paper_2606_04316_gb300 import qdt
     old = os.environ.get("QDT_W_BUDGET")
+    old_sym = os.environ.get("QDT_BATCH_SYM")
     if budget is not None:
         os.environ["QDT_W_BUDGET"] = str(budget)
+    if not sym:
+        os.environ["QDT_BATCH_SYM"] = "0"
     try:
         ctx = qdt.Context(0)
         ctx.set_basis(p.basis)
@@ -40,17 +45,23 @@ def run(p, blocks, precision, budget=None):
             os.environ.pop("QDT_W_BUDGET", None)
         else:
             os.environ["QDT_W_BUDGET"] = old
+        if old_sym is None:
+            os.environ.pop("QDT_BATCH_SYM", None)
+        else:
+            os.environ["QDT_BATCH_SYM"] = old_sym
     return out.reshape(len(blocks), -1), st
 
 
+@pytest.mark.parametrize("sym", [True, False])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_forced_row_batches_match_oracle_and_one_batch(oracle, torch_cuda, precision):
+def test_forced_row_batches_match_oracle_and_one_batch(oracle, torch_cuda, precision, sym):
     blocks = ["coulomb", "gaunt", "gauge"]
     # 4 centres of a jittered cluster, s+p with 2 primitives: class 0 has 1312
     # function-pair rows (W about 14 MB), the L-S class 768 (gauge W about 42 MB);
-    # a 2 MB budget cuts them into many batches with ragged last ones
+    # a 2 MB budget cuts them into many batches with ragged last ones.  tau
+    # 1e-10 drops quartets, some of them in one direction only
     p = synth.cluster_problem((2, 2, 1), 3, seed=611, nprim=2, blocks=blocks, tau=1e-10)
-    got, st = run(p, blocks, precision, budget=2 << 20)
+    got, st = run(p, blocks, precision, budget=2 << 20, sym=sym)
     one, st1 = run(p, blocks, precision)
     tr = oracle.Transform(p)
     tol = TOL_FP64 if precision == 0 else TOL_SPLIT
@@ -58,7 +69,11 @@ def test_forced_row_batches_match_oracle_and_one_batch(oracle, torch_cuda, preci
         ref = tr.packed(b).reshape(-1)
         assert np.abs(got[i] - ref).max() <= tol, b
         assert np.abs(got[i] - one[i]).max() <= tol, b
-    # the same quartets are kept either way; without bra-ket symmetry the
-    # batched path computes more integral blocks
+    # the same quartets are kept either way; with bra-ket symmetry every block
+    # is computed once, as in one batch, without it the batches compute more
     assert st["quartets_kept"] == st1["quartets_kept"]
-    assert st["flops_eri"] > st1["flops_eri"]
+    if sym:
+        assert st["flops_eri"] == st1["flops_eri"]
+        assert st["flops_half1"] > st1["flops_half1"]      # the transposed blocks' contraction
+    else:
+        assert st["flops_eri"] > st1["flops_eri"]

@@ -13,7 +13,7 @@ from paper_2606_04316_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-F32_REL = 1024.0 / 2 ** 24          # the error model: |FP32 - exact| <= F32_REL Q_A Q_C
+F32_REL = 256.0 / 2 ** 24           # the error model: |FP32 - exact| <= F32_REL Q_A Q_C
 BLOCKS = ("coulomb", "gaunt", "gauge")
 
 
@@ -55,7 +55,7 @@ def test_fp32_quartets_in_use_and_within_tolerance(oracle, torch_cuda):
     st = ctx.transform(list(BLOCKS), 0, 4, p.tau, 1, o_split)
     ctx.transform(list(BLOCKS), 0, 4, p.tau, 0, o_fp64)
     assert st["quartets_f32"][0] > 0 and st["quartets_f32"][1] > 0
-    assert 0.0 < st["f32_bound"] <= 1e-11
+    assert 0.0 < st["f32_bound"] <= 3e-11
     assert 0.0 < st["flops_eri_f32"] < st["flops_eri"]
     assert (o_split - o_fp64).abs().max().item() <= 1e-10
     got = o_split.cpu().numpy().reshape(len(BLOCKS), -1)
