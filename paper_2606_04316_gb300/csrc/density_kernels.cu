@@ -106,22 +106,45 @@ __device__ inline double block_max(double v) {
 // KU (Kramers-unrestricted input): R, S are spinors with their own
 // coefficients; only A is formed, 2 parts (Re A, Im A) per spinor pair.
 //
-// One CTA per shell pair; its function pairs run one after another (uniform
-// across the CTA), the two coefficient rows of a function pair are staged in
-// shared memory, and the threads run over the column pairs RS, each writing
-// its parts as 16-byte stores next to its neighbours' (a warp writes one
-// contiguous run of the row).
+// One CTA per shell pair: the coefficient rows of its shells (active range)
+// are staged in shared memory once, then the threads run over the flattened
+// (function pair, column pair RS) range, each element's parts written as
+// 16-byte stores next to its neighbours' (a warp writes contiguous runs of a
+// row).  One barrier per CTA.
 constexpr int kDensityThreads = 256;
 
-// Coefficient rows a and b (active range k0 .. k0 + nKa) into shared memory,
-// as the real type R.
+// Shared-memory layout of a density CTA: rows of shell A, rows of shell B
+// (none for a diagonal pair), then the packed (a, b) of every function pair.
 template <class R>
-__device__ inline void stage_rows(const double *Cq, int nK, int k0, int nKa, int ia, int ib, R *ca, R *cb) {
-    const double *ra = Cq + ((size_t)ia * nK + k0) * 4, *rb = Cq + ((size_t)ib * nK + k0) * 4;
-    for (int i = threadIdx.x; i < 4 * nKa; i += blockDim.x) {
-        ca[i] = real_of(ra[i], R{});
-        cb[i] = real_of(rb[i], R{});
+struct DensityStage {
+    const R *ca, *cb;
+    const int *ftab;
+};
+
+template <class R>
+__device__ inline DensityStage<R> stage_pair(const PairDev &pr, const ShellDev &A, const ShellDev &B,
+                                             const double *Cq, int nK, int k0, int nKa, double *raw) {
+    const int row = 4 * nKa;
+    const bool diag = pr.sa == pr.sb;
+    R *ca = reinterpret_cast<R *>(raw);
+    R *cb = diag ? ca : ca + (size_t)A.nfunc * row;
+    int *ftab = reinterpret_cast<int *>(ca + (size_t)(A.nfunc + (diag ? 0 : B.nfunc)) * row);
+    for (int i = threadIdx.x; i < A.nfunc * row; i += blockDim.x) {
+        const int f = i / row, j = i - f * row;
+        ca[i] = real_of(Cq[((size_t)(A.foff + f) * nK + k0) * 4 + j], R{});
     }
+    if (!diag)
+        for (int i = threadIdx.x; i < B.nfunc * row; i += blockDim.x) {
+            const int f = i / row, j = i - f * row;
+            cb[i] = real_of(Cq[((size_t)(B.foff + f) * nK + k0) * 4 + j], R{});
+        }
+    for (int fp = threadIdx.x; fp < pr.nfp; fp += blockDim.x) {
+        int fa, fb;
+        decode_fp(pr, B.nfunc, fp, fa, fb);
+        ftab[fp] = fa | (fb << 16);
+    }
+    __syncthreads();
+    return {ca, cb, ftab};
 }
 
 template <class R>
@@ -135,47 +158,40 @@ __global__ void __launch_bounds__(kDensityThreads) density_coulomb_kernel(
     const PairDev *pairs, const int *bra_order, const ShellDev *shells, const double *Cq, int nK, int k0, int nKa,
     const int *rsR, const int *rsS, int nRS, double *D, double *Dmax) {
     extern __shared__ double crow_raw[];
-    R *ca = reinterpret_cast<R *>(crow_raw), *cb = ca + 4 * nKa;
     const int sp = bra_order[blockIdx.x];
     const PairDev pr = pairs[sp];
     const ShellDev A = shells[pr.sa], B = shells[pr.sb];
     constexpr int parts = KU ? 2 : 4;
     const long long ld = (long long)parts * nRS;
-    const bool diag = pr.sa == pr.sb;
+    const DensityStage<R> st = stage_pair<R>(pr, A, B, Cq, nK, k0, nKa, crow_raw);
+    const int row = 4 * nKa;
     double vmax = 0.0;
-    int fa = 0, fb = 0;
-    for (int fp = 0; fp < pr.nfp; ++fp) {
-        const int ia = A.foff + fa, ib = B.foff + fb;
-        __syncthreads();                       // the previous function pair's readers are done
-        stage_rows(Cq, nK, k0, nKa, ia, ib, ca, cb);
-        __syncthreads();
-        double *row = D + (pr.rowoff + fp) * ld;
-        for (int rs = threadIdx.x; rs < nRS; rs += blockDim.x) {
-            const int Rr = rsR[rs], Ss = rsS[rs];
-            Cx<R> aaR, abR, aaS, abS, baR, bbR, baS, bbS;
-            spinor_s(ca, Rr, aaR, abR);
-            spinor_s(ca, Ss, aaS, abS);
-            spinor_s(cb, Rr, baR, bbR);
-            spinor_s(cb, Ss, baS, bbS);
-            Cx<R> Av = conj_(aaR) * baS + conj_(abR) * bbS;
-            if (ia != ib) Av = Av + (conj_(baR) * aaS + conj_(bbR) * abS);
-            const double are = val_(Av.re), aim = val_(Av.im);
-            double2 *o = reinterpret_cast<double2 *>(row + (long long)parts * rs);
-            o[0] = make_double2(are, aim);
-            vmax = fmax(vmax, fmax(fabs(are), fabs(aim)));
-            if (!KU) {
-                Cx<R> Bv = aaR * bbS - abR * baS;
-                if (ia != ib) Bv = Bv + (baR * abS - bbR * aaS);
-                const double bre = val_(Bv.re), bim = val_(Bv.im);
-                o[1] = make_double2(bre, bim);
-                vmax = fmax(vmax, fmax(fabs(bre), fabs(bim)));
-            }
+    int fp = threadIdx.x / nRS, rs = threadIdx.x - fp * nRS;
+    while (fp < pr.nfp) {
+        const int f = st.ftab[fp], fa = f & 0xffff, fb = f >> 16;
+        const R *ca = st.ca + (size_t)fa * row, *cb = st.cb + (size_t)fb * row;
+        const bool two = A.foff + fa != B.foff + fb;        // a != b: both orders
+        const int Rr = rsR[rs], Ss = rsS[rs];
+        Cx<R> aaR, abR, aaS, abS, baR, bbR, baS, bbS;
+        spinor_s(ca, Rr, aaR, abR);
+        spinor_s(ca, Ss, aaS, abS);
+        spinor_s(cb, Rr, baR, bbR);
+        spinor_s(cb, Ss, baS, bbS);
+        Cx<R> Av = conj_(aaR) * baS + conj_(abR) * bbS;
+        if (two) Av = Av + (conj_(baR) * aaS + conj_(bbR) * abS);
+        const double are = val_(Av.re), aim = val_(Av.im);
+        double2 *o = reinterpret_cast<double2 *>(D + (pr.rowoff + fp) * ld + (long long)parts * rs);
+        o[0] = make_double2(are, aim);
+        vmax = fmax(vmax, fmax(fabs(are), fabs(aim)));
+        if (!KU) {
+            Cx<R> Bv = aaR * bbS - abR * baS;
+            if (two) Bv = Bv + (baR * abS - bbR * aaS);
+            const double bre = val_(Bv.re), bim = val_(Bv.im);
+            o[1] = make_double2(bre, bim);
+            vmax = fmax(vmax, fmax(fabs(bre), fabs(bim)));
         }
-        // next function pair: b runs fastest; a diagonal pair keeps b >= a
-        if (++fb == B.nfunc) {
-            ++fa;
-            fb = diag ? fa : 0;
-        }
+        rs += blockDim.x;
+        while (rs >= nRS) { rs -= nRS; ++fp; }
     }
     // block max -> Dmax[sp]
     vmax = block_max(vmax);
@@ -199,48 +215,43 @@ __global__ void __launch_bounds__(kDensityThreads) density_gaunt_kernel(
     const PairDev *pairs, const int *bra_order, const ShellDev *shells, const double *Cq, int nK, int k0, int nKa,
     const int *rsR, const int *rsS, int nRS, double *D, double *Dmax) {
     extern __shared__ double crow_raw[];
-    R *ca = reinterpret_cast<R *>(crow_raw), *cb = ca + 4 * nKa;
     const int sp = bra_order[blockIdx.x];
     const PairDev pr = pairs[sp];
     const ShellDev A = shells[pr.sa], B = shells[pr.sb];
     constexpr int parts = KU ? 2 : 4;
     const long long ld = 3LL * parts * nRS;
+    const DensityStage<R> st = stage_pair<R>(pr, A, B, Cq, nK, k0, nKa, crow_raw);
+    const int row = 4 * nKa;
     double vmax = 0.0;
-    int fa = 0, fb = 0;
-    for (int fp = 0; fp < pr.nfp; ++fp) {
-        const int ia = A.foff + fa, ib = B.foff + fb;
-        __syncthreads();
-        stage_rows(Cq, nK, k0, nKa, ia, ib, ca, cb);
-        __syncthreads();
-        double *row = D + (pr.rowoff + fp) * ld;
-        for (int rs = threadIdx.x; rs < nRS; rs += blockDim.x) {
-            const int Rr = rsR[rs], Ss = rsS[rs];
-            Cx<R> aaR, abR, aaS, abS, baR, bbR, baS, bbS;
-            spinor_s(ca, Rr, aaR, abR);
-            spinor_s(ca, Ss, aaS, abS);
-            spinor_s(cb, Rr, baR, bbR);
-            spinor_s(cb, Ss, baS, bbS);
+    int fp = threadIdx.x / nRS, rs = threadIdx.x - fp * nRS;
+    while (fp < pr.nfp) {
+        const int f = st.ftab[fp], fa = f & 0xffff, fb = f >> 16;
+        const R *ca = st.ca + (size_t)fa * row, *cb = st.cb + (size_t)fb * row;
+        double *drow = D + (pr.rowoff + fp) * ld;
+        const int Rr = rsR[rs], Ss = rsS[rs];
+        Cx<R> aaR, abR, aaS, abS, baR, bbR, baS, bbS;
+        spinor_s(ca, Rr, aaR, abR);
+        spinor_s(ca, Ss, aaS, abS);
+        spinor_s(cb, Rr, baR, bbR);
+        spinor_s(cb, Ss, baS, bbS);
 #pragma unroll
-            for (int J = 0; J < 3; ++J) {
-                // x = R: (conj alpha, conj beta); x = R': (-beta, alpha)
-                const Cx<R> Av = sigma_form(J, conj_(aaR), conj_(abR), baS, bbS) +
-                                 sigma_form(J, conj_(baR), conj_(bbR), aaS, abS);
-                const double are = val_(Av.re), aim = val_(Av.im);
-                double2 *o = reinterpret_cast<double2 *>(row + (long long)J * parts * nRS + (long long)parts * rs);
-                o[0] = make_double2(are, aim);
-                vmax = fmax(vmax, fmax(fabs(are), fabs(aim)));
-                if (!KU) {
-                    const Cx<R> Bv = sigma_form(J, neg_(abR), aaR, baS, bbS) + sigma_form(J, neg_(bbR), baR, aaS, abS);
-                    const double bre = val_(Bv.re), bim = val_(Bv.im);
-                    o[1] = make_double2(bre, bim);
-                    vmax = fmax(vmax, fmax(fabs(bre), fabs(bim)));
-                }
+        for (int J = 0; J < 3; ++J) {
+            // x = R: (conj alpha, conj beta); x = R': (-beta, alpha)
+            const Cx<R> Av = sigma_form(J, conj_(aaR), conj_(abR), baS, bbS) +
+                             sigma_form(J, conj_(baR), conj_(bbR), aaS, abS);
+            const double are = val_(Av.re), aim = val_(Av.im);
+            double2 *o = reinterpret_cast<double2 *>(drow + (long long)J * parts * nRS + (long long)parts * rs);
+            o[0] = make_double2(are, aim);
+            vmax = fmax(vmax, fmax(fabs(are), fabs(aim)));
+            if (!KU) {
+                const Cx<R> Bv = sigma_form(J, neg_(abR), aaR, baS, bbS) + sigma_form(J, neg_(bbR), baR, aaS, abS);
+                const double bre = val_(Bv.re), bim = val_(Bv.im);
+                o[1] = make_double2(bre, bim);
+                vmax = fmax(vmax, fmax(fabs(bre), fabs(bim)));
             }
         }
-        if (++fb == B.nfunc) {
-            ++fa;
-            fb = 0;
-        }
+        rs += blockDim.x;
+        while (rs >= nRS) { rs -= nRS; ++fp; }
     }
     vmax = block_max(vmax);
     if (threadIdx.x == 0) atomic_max_nonneg(Dmax + sp, vmax);
@@ -248,9 +259,11 @@ __global__ void __launch_bounds__(kDensityThreads) density_gaunt_kernel(
 
 template <bool KU, class R>
 void launch_density_t(bool gaunt, const PairDev *pairs, const int *bra_order, int nsp, const ShellDev *shells,
-                      const double *Cq, int nK, int k0, int nKa, const int *rsR, const int *rsS, int nRS, double *D,
-                      double *Dmax, cudaStream_t s) {
-    const size_t smem = 2 * 4 * (size_t)(nKa > 0 ? nKa : 1) * sizeof(R);
+                      const double *Cq, int nK, int k0, int nKa, int maxnf, int maxnfp, const int *rsR,
+                      const int *rsS, int nRS, double *D, double *Dmax, cudaStream_t s) {
+    // two shells' coefficient rows (active range) and the function-pair table
+    const size_t smem = 2 * (size_t)maxnf * 4 * (size_t)(nKa > 0 ? nKa : 1) * sizeof(R) +
+                        (size_t)maxnfp * sizeof(int) + 16;
     if (smem > (size_t)200 * 1024) throw Error{QDT_ERR_ARG, "density: too many active columns"};
     if (gaunt) {
         if (smem > (size_t)48 * 1024)
@@ -269,9 +282,10 @@ void launch_density_t(bool gaunt, const PairDev *pairs, const int *bra_order, in
 }
 
 // The split form (pairs = true) computes the density in compensated FP32
-// pairs, the FP64 form in FP64.
+// pairs, the FP64 form in FP64.  maxnf: functions of the largest shell;
+// maxnfp: function pairs of the largest shell pair.
 void launch_density(bool gaunt, bool ku, bool pairs_arith, const PairDev *pairs, const int *bra_order, int nsp,
-                    const ShellDev *shells, const double *Cq, int nK, int k0, const int *rsR,
+                    const ShellDev *shells, int maxnf, int maxnfp, const double *Cq, int nK, int k0, const int *rsR,
                     const int *rsS, int nRS, double *D, double *Dmax, cudaStream_t s) {
     if (nsp <= 0) return;
     // active units: every R and S index of the column list lies in [0, nKa)
@@ -279,11 +293,11 @@ void launch_density(bool gaunt, bool ku, bool pairs_arith, const PairDev *pairs,
     int nKa = 0;
     while ((long long)nKa * (nKa + 1) / 2 < nRS) ++nKa;
     if (ku) {
-        if (pairs_arith) launch_density_t<true, dfl>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, rsR, rsS, nRS, D, Dmax, s);
-        else launch_density_t<true, double>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, rsR, rsS, nRS, D, Dmax, s);
+        if (pairs_arith) launch_density_t<true, dfl>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, maxnf, maxnfp, rsR, rsS, nRS, D, Dmax, s);
+        else launch_density_t<true, double>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, maxnf, maxnfp, rsR, rsS, nRS, D, Dmax, s);
     } else {
-        if (pairs_arith) launch_density_t<false, dfl>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, rsR, rsS, nRS, D, Dmax, s);
-        else launch_density_t<false, double>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, rsR, rsS, nRS, D, Dmax, s);
+        if (pairs_arith) launch_density_t<false, dfl>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, maxnf, maxnfp, rsR, rsS, nRS, D, Dmax, s);
+        else launch_density_t<false, double>(gaunt, pairs, bra_order, nsp, shells, Cq, nK, k0, nKa, maxnf, maxnfp, rsR, rsS, nRS, D, Dmax, s);
     }
 }
 

@@ -842,14 +842,12 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
             for (int q = tid; q < nq; q += nt) {
                 const int ijl = q / nk, kl = q - ijl * nk;
                 // plain-FP32 quartets of the Coulomb kernel: FP32 header; those of
-                // the gauge kernel keep the FP64 header (its r12 tensor takes
-                // differences F_n - F_{n-1} that lose digits in FP32; measured
-                // 13x the Coulomb kernel's error ratio)
+                // the gauge kernel take the FP32-pair header (its r12 tensor takes
+                // differences F_n - F_{n-1} that lose digits in FP32: measured 13x
+                // the Coulomb kernel's error ratio with an FP32 header), of which
+                // the FP32 recursion reads the high parts
                 if constexpr (DF && F32 && !GAUGE)
                     quartet_header_f32<GAUGE>(boys, pp + X.ppoff + i0 + ijl, pp + Y.ppoff + k0 + kl, L, H + (size_t)q * hs);
-                else if constexpr (DF && F32)
-                    quartet_header<GAUGE, true>(boys, pp + X.ppoff + i0 + ijl, pp + Y.ppoff + k0 + kl, L,
-                                                H + (size_t)q * hs);
                 else if constexpr (DF)
                     quartet_header_pairs<GAUGE>(boys, pp + X.ppoff + i0 + ijl, pp + Y.ppoff + k0 + kl, L,
                                                 H + (size_t)q * hs);
@@ -926,8 +924,14 @@ __device__ void block_chunk(const PrimPairDev *pp, const double *E, const float2
                     float2 *T2 = reinterpret_cast<float2 *>(T);
                     const float2 *RC2 = reinterpret_cast<const float2 *>(RC), *RR2 = reinterpret_cast<const float2 *>(RR);
                     const void *ey = F32 ? (const void *)(E1 + b.eY[k0] + y0) : (const void *)(E2 + b.eY[k0] + y0);
-                    ket_pass_tiled<4, 2, !F32, GAUGE>(nij, nT, nhx, ych, Ly, b.trip, T2, tsz, RC2, nrC, RR2, nrR, nk,
-                                                      ey, Y.nfp, sE);
+                    // plain FP32 waits on the loads: 3 inner function pairs per thread when the
+                    // chunk comes in threes (the derivative functions do), so 7 loads serve 12 FMAs
+                    if (F32 && ych % 3 == 0)
+                        ket_pass_tiled<4, 3, false, GAUGE>(nij, nT, nhx, ych, Ly, b.trip, T2, tsz, RC2, nrC, RR2, nrR,
+                                                           nk, ey, Y.nfp, sE);
+                    else
+                        ket_pass_tiled<4, 2, !F32, GAUGE>(nij, nT, nhx, ych, Ly, b.trip, T2, tsz, RC2, nrC, RR2, nrR,
+                                                          nk, ey, Y.nfp, sE);
                 }
             } else if constexpr (DF && F32 && !GAUGE) {
                 // two T rows per thread sharing the E loads

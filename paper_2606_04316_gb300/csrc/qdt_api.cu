@@ -31,7 +31,7 @@ void launch_prim_pairs_map(const ShellDev *shells, const PairDev *pairs, const i
                            long long npp, const double *exps, const double *coefs,
                            const double *norms, PrimPairDev *pp, double *E, cudaStream_t s);
 void launch_density(bool gaunt, bool ku, bool pairs_arith, const PairDev *pairs, const int *bra_order, int nsp,
-                    const ShellDev *shells, const double *Cq, int nK, int k0, const int *rsR,
+                    const ShellDev *shells, int maxnf, int maxnfp, const double *Cq, int nK, int k0, const int *rsR,
                     const int *rsS, int nRS, double *D, double *Dmax, cudaStream_t s);
 }  // namespace qdt
 
@@ -503,8 +503,11 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
     P.Dbra = (double *)ctx->Dbra.get(std::max<long long>(1, P.M * P.ncolD) * sizeof(double));
     P.Dmax = (double *)ctx->Dmax.get(std::max(1, pc.nsp) * sizeof(double));
     QDT_CUDA_TRY(cudaMemsetAsync(P.Dmax, 0, pc.nsp * sizeof(double), s));
-    launch_density(P.ls, P.ku, precision == QDT_SPLIT, pc.d_pairs, pc.d_bra_order, pc.nsp, (const ShellDev *)ctx->shells.p,
-                   (const double *)ctx->Cq.p, ctx->nK, k0, d_rsR, d_rsS, P.nRS, P.Dbra, P.Dmax, s);
+    int maxnf = 1;
+    for (const ShellDev &sh : ctx->h_shells) maxnf = std::max(maxnf, sh.nfunc);
+    launch_density(P.ls, P.ku, precision == QDT_SPLIT, pc.d_pairs, pc.d_bra_order, pc.nsp,
+                   (const ShellDev *)ctx->shells.p, maxnf, pc.maxnfp, (const double *)ctx->Cq.p, ctx->nK, k0, d_rsR,
+                   d_rsS, P.nRS, P.Dbra, P.Dmax, s);
     ctx->launches++;
     if (P.quarter) {   // the quarter route screens on coefficient bounds, not on the density
         launch_coef_bound(pc.d_pairs, (const ShellDev *)ctx->shells.p, (const double *)ctx->Cq.p, ctx->nK, k0,
