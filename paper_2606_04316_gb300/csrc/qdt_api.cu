@@ -72,6 +72,60 @@ T *dcopy(DBuf &b, const std::vector<T> &v, cudaStream_t s) {
     return d;
 }
 
+// Page-locked staging of the uploads inside a transformation (tile extents,
+// parameter sets, screening lists): each host array is copied into the arena
+// and sent from there, so every upload is an asynchronous DMA instead of a
+// staged copy from pageable memory.  Space is taken in order and only handed
+// back by reset(), which the entry points call at their start, when the
+// context's stream has drained (every transformation ends by synchronising
+// it); a buffer outgrown in between is kept until then, because copies in
+// flight may still read it.
+struct PinnedArena {
+    char *p = nullptr;
+    size_t n = 0, used = 0;
+    std::vector<char *> retired;
+    void *take(size_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        if (used + bytes > n) {
+            const size_t nn = std::max(bytes, 2 * n + ((size_t)1 << 20));
+            char *q = nullptr;
+            if (cudaMallocHost(&q, nn) != cudaSuccess) {
+                cudaGetLastError();
+                throw Error{QDT_ERR_OOM, "cudaMallocHost of " + std::to_string(nn) + " bytes failed"};
+            }
+            if (p) retired.push_back(p);
+            p = q;
+            n = nn;
+            used = 0;
+        }
+        void *r = p + used;
+        used += bytes;
+        return r;
+    }
+    void reset() {
+        for (char *q : retired) cudaFreeHost(q);
+        retired.clear();
+        used = 0;
+    }
+    void release() {
+        reset();
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+template <class T>
+T *dcopy_pinned(PinnedArena &a, DBuf &b, const std::vector<T> &v, cudaStream_t s) {
+    T *d = (T *)b.get(std::max<size_t>(1, v.size()) * sizeof(T));
+    if (!v.empty()) {
+        void *h = a.take(v.size() * sizeof(T));
+        std::memcpy(h, v.data(), v.size() * sizeof(T));
+        QDT_CUDA_TRY(cudaMemcpyAsync(d, h, v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    return d;
+}
+
 struct ClassBufs {
     DBuf pairs, pp, E, E2, E1, Q, bra, brapos, pp_pair;
 };
@@ -110,6 +164,10 @@ struct qdt_ctx {
     // row batches with bra-ket symmetry: transposed blocks for later rows, their
     // tile extents, the W2 column of each batch pair and the batch's density rows
     DBuf W2, Wc2, ktile3, ktile4, col2, ketsp2, ketcol2, Dbra2;
+    // tile lists built on the device: the batch's bra pairs in tile order, their
+    // first tile, and the FP32 split points of the class
+    DBuf tbras, toff, dsplit;
+    PinnedArena pin;            // page-locked staging of a transformation's uploads
     SplitWorkspace split;
     // first-half route of the Coulomb block: density (Eq. firsthalf) or the
     // two-quarter comparator, and the comparator's workspace
@@ -192,6 +250,60 @@ void build_tiles(const std::vector<int> &bras, const std::vector<int> &prefix, i
         for (int q = 0; q < mid; q += kets) out.push_back({sp, q, std::min(mid, q + kets), req, 0});
         for (int q = mid; q < prefix[sp]; q += kets) out.push_back({sp, q, std::min(prefix[sp], q + kets), req, 1});
     }
+}
+
+// The same tiles written on the device, one warp per bra pair: bras[i] (tile
+// order) starts at tile off[i]; its kept prefix and FP32 split point come from
+// the device copies of the screening outcome (split null: no FP32 tiles).
+// Only the bra list and the offsets are uploaded, not the tiles.
+__global__ void build_tiles_kernel(const int *bras, const long long *off, const int *prefix, const int *split,
+                                   int n, int kets, int req, EriTask *out) {
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const int sp = bras[w];
+    const int pre = prefix[sp], mid = split ? split[sp] : pre;
+    const int n1 = (mid + kets - 1) / kets, n2 = (pre - mid + kets - 1) / kets;
+    EriTask *o = out + off[w];
+    for (int j = lane; j < n1 + n2; j += 32) {
+        EriTask t;
+        t.bra_sp = sp;
+        t.req = req;
+        if (j < n1) {
+            t.k0 = j * kets;
+            t.k1 = min(mid, t.k0 + kets);
+            t.f32 = 0;
+        } else {
+            t.k0 = mid + (j - n1) * kets;
+            t.k1 = min(pre, t.k0 + kets);
+            t.f32 = 1;
+        }
+        o[j] = t;
+    }
+}
+
+// Host side of build_tiles_kernel: per-bra tile offsets (from the host copy of
+// the screening outcome), the uploads, the launch; returns the tile count.
+int launch_build_tiles(qdt_ctx *ctx, const std::vector<int> &bras, const std::vector<int> &prefix,
+                       const std::vector<int> *split, const int *d_prefix, const int *d_split, int kets,
+                       EriTask *&d_tiles, cudaStream_t s) {
+    std::vector<long long> off(bras.size() + 1, 0);
+    for (size_t i = 0; i < bras.size(); ++i) {
+        const int sp = bras[i], pre = prefix[sp], mid = split ? (*split)[sp] : pre;
+        off[i + 1] = off[i] + (mid + kets - 1) / kets + (pre - mid + kets - 1) / kets;
+    }
+    const long long nt = off.back();
+    if (nt > 0x7fffffffLL) throw Error{QDT_ERR_ARG, "integral tiles: more than 2^31 tiles in one batch"};
+    d_tiles = (EriTask *)ctx->tasks.get((size_t)std::max<long long>(1, nt) * sizeof(EriTask));
+    if (nt == 0) return 0;
+    const int *d_bras = dcopy_pinned(ctx->pin, ctx->tbras, bras, s);
+    const long long *d_off = dcopy_pinned(ctx->pin, ctx->toff, off, s);
+    const long long threads = 32LL * (long long)bras.size();
+    build_tiles_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(d_bras, d_off, d_prefix, split ? d_split : nullptr,
+                                                                          (int)bras.size(), kets, 0, d_tiles);
+    QDT_CHECK_KERNEL("build_tiles_kernel");
+    ctx->launches++;
+    return (int)nt;
 }
 
 // ---------------------------------------------------------------- autotuner
@@ -427,6 +539,7 @@ struct ClassPlan {
     long long *ketcol = nullptr;
     std::vector<int> h_prefix, h_ketsp, h_kpos;
     std::vector<int> h_split;     // per bra pair: kept ket positions [h_split, h_prefix) run in plain FP32
+    int *d_split = nullptr;       // its device copy (split form)
     std::vector<double> h_Dmax;
     std::vector<long long> h_col, Krow;
     size_t wbudget = 0;
@@ -495,7 +608,7 @@ void class_issue(qdt_ctx *ctx, const ClassRun &cr, int k0, int nKa, double tau, 
     std::vector<int> hR, hS;
     for (int r = 0; r < nKa; ++r)
         for (int q = r; q < nKa; ++q) { hR.push_back(r); hS.push_back(q); }
-    int *d_rsR = dcopy(ctx->rsR, hR, s), *d_rsS = dcopy(ctx->rsS, hS, s);
+    int *d_rsR = dcopy_pinned(ctx->pin, ctx->rsR, hR, s), *d_rsS = dcopy_pinned(ctx->pin, ctx->rsS, hS, s);
     split_invalidate(ctx->split);
 
     // 1. density in bra order + Dmax
@@ -633,7 +746,8 @@ void class_finish(qdt_ctx *ctx, ClassPlan &P, qdt_stats *st) {
     }
     P.h_kpos.assign(pc.nsp, 0);
     for (int q = 0; q < pc.nsp; ++q) P.h_kpos[P.h_ketsp[q]] = q;
-    P.d_kpos = (P.one_batch || P.mirror) ? dcopy(ctx->kpos, P.h_kpos, s) : nullptr;
+    P.d_kpos = (P.one_batch || P.mirror) ? dcopy_pinned(ctx->pin, ctx->kpos, P.h_kpos, s) : nullptr;
+    P.d_split = P.precision == QDT_SPLIT ? dcopy_pinned(ctx->pin, ctx->dsplit, P.h_split, s) : nullptr;
 }
 
 // One batch of bra rows of a class.
@@ -703,12 +817,12 @@ void batch_prepare_mirror(qdt_ctx *ctx, const ClassPlan &P, RowBatch &B) {
         if (gaunt_too)
             for (long long t = r0 / TMr; t <= (r0 + pr.nfp - 1) / TMr; ++t) B.kg2[t] = std::max(B.kg2[t], ext);
     }
-    B.d_kt2 = dcopy(ctx->ktile3, B.kt2, s);
-    if (gaunt_too) B.d_kg2 = dcopy(ctx->ktile4, B.kg2, s);
+    B.d_kt2 = dcopy_pinned(ctx->pin, ctx->ktile3, B.kt2, s);
+    if (gaunt_too) B.d_kg2 = dcopy_pinned(ctx->pin, ctx->ktile4, B.kg2, s);
     else { B.kg2 = B.kt2; B.d_kg2 = B.d_kt2; }
     // the batch's density rows in W2 column order
-    int *d_k2 = dcopy(ctx->ketsp2, k2, s);
-    long long *d_kcol = dcopy(ctx->ketcol2, kcol, s);
+    int *d_k2 = dcopy_pinned(ctx->pin, ctx->ketsp2, k2, s);
+    long long *d_kcol = dcopy_pinned(ctx->pin, ctx->ketcol2, kcol, s);
     B.Dbra2 = (double *)ctx->Dbra2.get((size_t)B.ld2 * P.ncolD * sizeof(double));
     launch_gather_rows(P.Dbra, pc.d_pairs, d_k2, d_kcol, (int)k2.size(), P.ncolD, B.Dbra2, s);
     ctx->launches++;
@@ -718,7 +832,7 @@ void batch_prepare_mirror(qdt_ctx *ctx, const ClassPlan &P, RowBatch &B) {
     prm.row2 = B.row2;
     prm.Wc2 = B.Wc2;
     prm.ldwc2 = B.ld2;
-    prm.col2 = dcopy(ctx->col2, col2, s);
+    prm.col2 = dcopy_pinned(ctx->pin, ctx->col2, col2, s);
 }
 
 // Next batch from bra position b0: sizes, integral-row buffers, the integral
@@ -789,7 +903,7 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
         long long kk = P.Krow[pc.bra_order[k]] * mult;
         for (long long t = r0 / TMr; t <= (r1 - 1) / TMr; ++t) B.kt[t] = std::max(B.kt[t], kk);
     }
-    B.d_kt = dcopy(ctx->ktile, B.kt, s);
+    B.d_kt = dcopy_pinned(ctx->pin, ctx->ktile, B.kt, s);
     if (P.ls && P.cr.gaunt && P.cr.gauge) {
         B.kg.assign((rows + TMr - 1) / TMr, 0);
         for (int k = b0; k < b1; ++k) {
@@ -797,7 +911,7 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
             long long r0 = pr.rowoff - B.row0, r1 = r0 + pr.nfp;
             for (long long t = r0 / TMr; t <= (r1 - 1) / TMr; ++t) B.kg[t] = std::max(B.kg[t], P.Krow[pc.bra_order[k]]);
         }
-        B.d_kg = dcopy(ctx->ktile2, B.kg, s);
+        B.d_kg = dcopy_pinned(ctx->pin, ctx->ktile2, B.kg, s);
     } else {
         B.kg = B.kt;
         B.d_kg = B.d_kt;
@@ -1000,7 +1114,7 @@ void quarter_half1(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, qdt_stat
     long long *dk[3];
     for (int g = 0; g < 3; ++g) {
         hk[g].assign((size_t)((Ms[g] + TMr - 1) / TMr), Ks[g]);
-        dk[g] = dcopy(ctx->qkt[g], hk[g], s);
+        dk[g] = dcopy_pinned(ctx->pin, ctx->qkt[g], hk[g], s);
     }
     auto sub = [&](int g, long long m) {
         return std::vector<long long>(hk[g].begin(), hk[g].begin() + (m + TMr - 1) / TMr);
@@ -1078,20 +1192,19 @@ void run_batches(qdt_ctx *ctx, ClassPlan &P, long long c0, long long c1, qdt_sta
     while (b0 < pc.nsp) {
         RowBatch B;
         batch_prepare(ctx, P, b0, B);
-        const EriParams *d_prm = dcopy(ctx->prms, std::vector<EriParams>{B.prm}, s);
+        const EriParams *d_prm = dcopy_pinned(ctx->pin, ctx->prms, std::vector<EriParams>{B.prm}, s);
         const EriShape shape{pc.maxnfp, pc.maxLab, pc.maxnpp};
         const bool df = B.prm.E2 != nullptr;
         const EriLaunch how = eri_launch_for(ctx, pc, shape, B.prm.gauge != 0, df, d_prm, B.bras, P.h_prefix, s);
-        std::vector<EriTask> tk;
-        build_tiles(tile_order(pc, B.bras, how.order), P.h_prefix, how.kets, 0, tk, df ? &P.h_split : nullptr);
-        EriTask *d_tk = dcopy(ctx->tasks, tk, s);
+        EriTask *d_tk = nullptr;
+        const int ntiles = launch_build_tiles(ctx, tile_order(pc, B.bras, how.order), P.h_prefix,
+                                              df ? &P.h_split : nullptr, P.prefix, P.d_split, how.kets, d_tk, s);
         int te = tm.n; tm.mark();
         launch_zero(B.W, B.rows * P.mult * B.ldw, s);
         if (B.Wc) launch_zero(B.Wc, B.rows * B.ldwc, s);
         if (B.W2) launch_zero(B.W2, B.rows2 * P.mult * B.ldw2, s);
         if (B.Wc2) launch_zero(B.Wc2, B.rows2 * B.ld2, s);
-        launch_eri(d_prm, d_tk, (int)tk.size(), (int *)ctx->next.get(sizeof(int)), shape, B.prm.gauge != 0, df, how,
-                   s);
+        launch_eri(d_prm, d_tk, ntiles, (int *)ctx->next.get(sizeof(int)), shape, B.prm.gauge != 0, df, how, s);
         ctx->launches += 2 + (B.Wc ? 1 : 0);
         batch_stats(ctx, P, B, c1 - c0, st);
         int th = tm.n; tm.mark();
@@ -1336,7 +1449,7 @@ void batch_round(qdt_ctx *owner, std::vector<BatchReq> &R, int round, unsigned f
         std::vector<EriTask> tiles[kKinds];
         for (int k = 0; k < kKinds; ++k) {
             if (prms[k].empty()) continue;
-            d_prms[k] = dcopy(owner->bprms[k], prms[k], s0);
+            d_prms[k] = dcopy_pinned(owner->pin, owner->bprms[k], prms[k], s0);
             owner->bnext[k].get(sizeof(int));
             // the tuner samples the first request of this kind
             size_t first = 0;
@@ -1363,7 +1476,7 @@ void batch_round(qdt_ctx *owner, std::vector<BatchReq> &R, int round, unsigned f
                 for (int q = mid; q < pre[o.sp]; q += how[k].kets)
                     tiles[k].push_back({o.sp, q, std::min(pre[o.sp], q + how[k].kets), req_of[o.i], 1});
             }
-            d_tiles[k] = dcopy(owner->btasks[k], tiles[k], s0);
+            d_tiles[k] = dcopy_pinned(owner->pin, owner->btasks[k], tiles[k], s0);
             ntiles[k] = (int)tiles[k].size();
         }
         for (BatchReq *r : fz) r->c->split.deferred = true;
@@ -1456,7 +1569,7 @@ void release_workspace(qdt_ctx *c) {
                     &c->prefix, &c->ktile, &c->tasks, &c->O, &c->partial, &c->stage, &c->kpos, &c->prms,
                     &c->next, &c->ktile2, &c->qcols, &c->qWL, &c->qWS, &c->qT1, &c->qT, &c->qVf, &c->qkt[0],
                     &c->qkt[1], &c->qkt[2], &c->W2, &c->Wc2, &c->ktile3, &c->ktile4, &c->col2, &c->ketsp2,
-                    &c->ketcol2, &c->Dbra2};
+                    &c->ketcol2, &c->Dbra2, &c->tbras, &c->toff, &c->dsplit};
     for (DBuf *b : bufs) b->release();
     split_release(c->split);
     for (GraphEntry &g : c->graph) {
@@ -1512,13 +1625,15 @@ void qdt_destroy(qdt_ctx *c) {
                     &c->bprms[2], &c->bprms[3], &c->btasks[0], &c->btasks[1], &c->btasks[2],
                     &c->btasks[3], &c->bnext[0], &c->bnext[1], &c->bnext[2], &c->bnext[3], &c->qcols,
                     &c->qWL, &c->qWS, &c->qT1, &c->qT, &c->qVf, &c->qCr1, &c->qCr2, &c->qkt[0],
-                    &c->qkt[1], &c->qkt[2]};
+                    &c->qkt[1], &c->qkt[2], &c->W2, &c->Wc2, &c->ktile3, &c->ktile4, &c->col2, &c->ketsp2,
+                    &c->ketcol2, &c->Dbra2, &c->tbras, &c->toff, &c->dsplit};
     for (DBuf *b : bufs) b->release();
     for (int k = 0; k < 2; ++k) {
         c->cb[k].pairs.release(); c->cb[k].pp.release(); c->cb[k].E.release(); c->cb[k].E2.release(); c->cb[k].E1.release();
-        c->cb[k].Q.release(); c->cb[k].bra.release(); c->cb[k].pp_pair.release();
+        c->cb[k].Q.release(); c->cb[k].bra.release(); c->cb[k].brapos.release(); c->cb[k].pp_pair.release();
     }
     split_release(c->split);
+    c->pin.release();
     for (GraphEntry &g : c->graph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     for (int i = 0; i < 16; ++i) cudaEventDestroy(c->ev[i]);
@@ -1785,6 +1900,8 @@ int qdt_transform(qdt_ctx *c, unsigned blocks, int k_begin, int k_end, double ta
         cudaGetLastError();      // start from a clean error state
         QDT_CUDA_TRY(cudaSetDevice(c->device));
         if (!c->has_basis || !c->has_coef) throw Error{QDT_ERR_STATE, "qdt_transform: basis or coefficients not set"};
+        QDT_CUDA_TRY(cudaStreamSynchronize(c->stream));      // staged uploads of earlier calls have landed
+        c->pin.reset();
         arg_check(blocks != 0 && (blocks & ~7u) == 0, "qdt_transform: blocks must be a non-empty subset of COULOMB|GAUNT|GAUGE");
         arg_check(k_begin >= 0 && k_end > k_begin && k_end <= c->nK, "qdt_transform: bad Kramers-pair (or spinor) range");
         arg_check(tau >= 0.0, "qdt_transform: negative Schwarz threshold");
@@ -1868,6 +1985,8 @@ int qdt_transform_batch(qdt_batch_item *items, int n, unsigned flags) {
             r.st.precision = it.precision;
             r.st.slices = split_slices(r.c->split);
             r.c->launches = 0;
+            QDT_CUDA_TRY(cudaStreamSynchronize(r.c->stream));  // staged uploads of earlier calls have landed
+            r.c->pin.reset();
         } catch (const Error &e) {
             r.status = e.code;
             r.err = e.msg;
