@@ -157,15 +157,21 @@ __device__ inline void digits7(double x, int e, __nv_bfloat16 *d, size_t plane) 
 }
 
 // A operand: rows of X (row-major, ld) scaled per row; out[i][r][k] for
-// r < Mpad, k < Kpad (zeros outside the matrix).  One CTA per row.
+// r < Mpad, k < Kpad (zeros outside the matrix).  One CTA per row.  With the
+// K extents of the 128-row tiles (kt128), a row is sliced only as far as the
+// contraction reads it, its tile's extent rounded up to the 64-wide K
+// subtile (the digits past it are never loaded).
 __global__ void slice_rows_kernel(const double *X, long long ld, long long M, long long K,
-                                  long long Mpad, long long Kpad, __nv_bfloat16 *out, int *rowexp) {
+                                  long long Mpad, long long Kpad, __nv_bfloat16 *out, int *rowexp,
+                                  const long long *kt128) {
     long long r = blockIdx.x;
     __shared__ double wm[32];
     __shared__ int e_sh;
+    const long long Kr = kt128 ? min(Kpad, (kt128[r / SBM] + SBK - 1) / SBK * SBK) : Kpad;
+    const long long Kx = min(K, Kr);
     double m = 0.0;
     if (r < M)
-        for (long long k = threadIdx.x; k < K; k += blockDim.x) m = fmax(m, fabs(X[r * ld + k]));
+        for (long long k = threadIdx.x; k < Kx; k += blockDim.x) m = fmax(m, fabs(X[r * ld + k]));
     // row maximum: warp shuffles, then the warps' maxima in the first warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -181,8 +187,8 @@ __global__ void slice_rows_kernel(const double *X, long long ld, long long M, lo
     const int e = e_sh;
     if (threadIdx.x == 0) rowexp[r] = e;
     size_t plane = (size_t)Mpad * Kpad;
-    for (long long k = threadIdx.x; k < Kpad; k += blockDim.x) {
-        double x = (r < M && k < K) ? X[r * ld + k] : 0.0;
+    for (long long k = threadIdx.x; k < Kr; k += blockDim.x) {
+        double x = (r < M && k < Kx) ? X[r * ld + k] : 0.0;
         digits7(x, e, out + (size_t)r * Kpad + k, plane);
     }
 }
@@ -673,7 +679,7 @@ void gemm_half1(SplitWorkspace &w, int precision, const double *A, long long lda
     // A slices (row scaled)
     int *rowexp = (int *)ws_get(w, WS_EXP, (size_t)(Mpad + Npad + 64) * sizeof(int) * 2);
     __nv_bfloat16 *Asl = (__nv_bfloat16 *)ws_get(w, WS_A, (size_t)kSlices * Mpad * KpadA * 2);
-    slice_rows_kernel<<<(unsigned)Mpad, 256, 0, s>>>(A, lda, M, std::min(kmax, lda), Mpad, KpadA, Asl, rowexp);
+    slice_rows_kernel<<<(unsigned)Mpad, 256, 0, s>>>(A, lda, M, std::min(kmax, lda), Mpad, KpadA, Asl, rowexp, d_kt);
     QDT_CHECK_KERNEL("slice_rows_kernel");
     // B slices (column scaled, transposed), cached per (pointer, shape) until
     // split_invalidate(): the densities are the same for every row batch.
