@@ -428,8 +428,8 @@ METRIC = "DCB AO->MO transform MO-integrals/s (split vs FP64 @1e-10 Eh)"
 WORKLOAD_NOTES = {
     "chain40-sp": "the 40-centre s+p chain (nL 160, nS 480, 40 Kramers pairs, Schwarz 1e-12) with the "
                   "Dirac-Coulomb-Breit blocks: the largest DCB workload whose 20 + 5 steps fit the bench's "
-                  "minute of timed work; the 64-centre DCB cluster (nL 256, nK 64) takes 285 s per split "
-                  "step (row batches; its first half alone is 7.3e15 FP64-equivalent flops) and is measured "
+                  "minute of timed work; the 64-centre DCB cluster (nL 256, nK 64) takes 211 s per split "
+                  "step (row batches; its first half alone is 5.0e15 FP64-equivalent flops) and is measured "
                   "separately (--workload cluster64-sp)",
 }
 

@@ -68,4 +68,55 @@ inline double f32_tail_split(const std::vector<double> &w, const std::vector<int
     return lo;
 }
 
+// Ket list of one row batch when a class runs in row batches with bra-ket
+// symmetry (bra positions [b0, b1) in this batch; shell pairs 0..n-1):
+//   order[q]   shell pair at global ket position q (w descending)
+//   kpos[i]    global ket position of pair i (the inverse of order)
+//   prefix[i]  kept ket prefix of pair i: row i keeps the positions q < prefix[i]
+//   bpos[i]    bra position of pair i
+//   batch      the batch's pairs
+// A kept block (AB|CD) whose mirror (CD|AB) is kept too (kpos(AB) < prefix(CD))
+// and whose ket pair CD lies in an earlier batch came, transposed, from CD's
+// batch, so such a CD needs no column here -- unless some row of this batch
+// keeps CD one way only (kpos(AB) >= prefix(CD)), whose block must be computed
+// here.  The list holds the pairs of this and later batches and those earlier
+// pairs, in global ket order; the kernel skips the rows of an earlier pair kept
+// both ways.  Outputs: list (shell pairs), pos[i] (index in list or -1), and
+// cnt[q] (list entries among the global positions < q, q = 0..n): row AB's
+// kept entries are the first cnt[prefix[AB]] of the list.
+struct BatchKets {
+    std::vector<int> list, pos, cnt;
+};
+
+inline BatchKets batch_kets(const std::vector<int> &order, const std::vector<int> &kpos,
+                            const std::vector<int> &prefix, const std::vector<int> &bpos, int b0,
+                            const std::vector<int> &batch) {
+    const int n = (int)order.size();
+    // the batch's rows by ket position, and the largest prefix among the rows at
+    // or after each one
+    std::vector<int> rows(batch);
+    std::sort(rows.begin(), rows.end(), [&](int x, int y) { return kpos[x] < kpos[y]; });
+    std::vector<int> kk(rows.size()), smax(rows.size() + 1, -1);
+    for (size_t i = 0; i < rows.size(); ++i) kk[i] = kpos[rows[i]];
+    for (int i = (int)rows.size() - 1; i >= 0; --i) smax[i] = std::max(smax[i + 1], prefix[rows[i]]);
+    BatchKets b;
+    b.pos.assign(n, -1);
+    b.cnt.assign(n + 1, 0);
+    for (int q = 0; q < n; ++q) {
+        const int sp = order[q];
+        bool keep = bpos[sp] >= b0;
+        if (!keep) {
+            // rows AB with kpos(AB) >= prefix(CD) are not kept by CD; does one of them keep CD?
+            const size_t i = (size_t)(std::lower_bound(kk.begin(), kk.end(), prefix[sp]) - kk.begin());
+            keep = smax[i] > q;
+        }
+        if (keep) {
+            b.pos[sp] = (int)b.list.size();
+            b.list.push_back(sp);
+        }
+        b.cnt[q + 1] = (int)b.list.size();
+    }
+    return b;
+}
+
 }  // namespace qdt

@@ -167,6 +167,9 @@ struct qdt_ctx {
     // tile lists built on the device: the batch's bra pairs in tile order, their
     // first tile, and the FP32 split points of the class
     DBuf tbras, toff, dsplit;
+    // ket list of a row batch with bra-ket symmetry: pairs, columns, list position,
+    // kept prefix and FP32 split point per pair in list positions
+    DBuf klist, kcol1, kpos1, kpre1, ksplit1;
     PinnedArena pin;            // page-locked staging of a transformation's uploads
     SplitWorkspace split;
     // first-half route of the Coulomb block: density (Eq. firsthalf) or the
@@ -766,7 +769,47 @@ struct RowBatch {
     double *W2 = nullptr, *Wc2 = nullptr, *Dbra2 = nullptr;
     std::vector<long long> kt2, kg2;
     long long *d_kt2 = nullptr, *d_kg2 = nullptr;
+    // its ket list (plan.h batch_kets): per shell pair the kept prefix and the FP32
+    // split point in list positions, the W columns of a batch row's kept prefix
+    std::vector<int> pre1, split1;
+    std::vector<long long> krow1;
+    int *d_list = nullptr, *d_pos1 = nullptr, *d_pre1 = nullptr, *d_split1 = nullptr;
+    long long *d_col1 = nullptr;
 };
+
+// The ket list of a row batch with bra-ket symmetry (plan.h batch_kets): the
+// kets of this and later batches and the earlier ones some row keeps one way
+// only, in ket order; the W columns follow the list, and the density rows of
+// the list are gathered into the ket-ordered density buffer (which the
+// first half of this batch reads).  Each shell pair's prefix and FP32 split
+// point become list positions, which is all the integral kernel needs: for a
+// batch row AB (in the list), list position < list prefix of CD exactly when
+// kpos(AB) < prefix(CD).
+void batch_kets_prepare(qdt_ctx *ctx, const ClassPlan &P, RowBatch &B) {
+    PairClass &pc = ctx->cls[P.cr.c];
+    cudaStream_t s = ctx->stream;
+    const BatchKets bk = batch_kets(P.h_ketsp, P.h_kpos, P.h_prefix, pc.bra_pos, B.b0, B.bras);
+    const int L = (int)bk.list.size();
+    std::vector<long long> col1((size_t)L + 1, 0);
+    for (int p = 0; p < L; ++p) col1[p + 1] = col1[p] + pc.h_pairs[bk.list[p]].nfp;
+    B.pre1.assign(pc.nsp, 0);
+    B.split1.assign(pc.nsp, 0);
+    for (int sp = 0; sp < pc.nsp; ++sp) {
+        B.pre1[sp] = bk.cnt[P.h_prefix[sp]];
+        B.split1[sp] = bk.cnt[P.h_split[sp]];
+    }
+    B.krow1.assign(pc.nsp, 0);
+    for (int sp : B.bras) B.krow1[sp] = col1[B.pre1[sp]];
+    B.d_list = dcopy_pinned(ctx->pin, ctx->klist, bk.list, s);
+    B.d_col1 = dcopy_pinned(ctx->pin, ctx->kcol1, col1, s);
+    B.d_pos1 = dcopy_pinned(ctx->pin, ctx->kpos1, bk.pos, s);
+    B.d_pre1 = dcopy_pinned(ctx->pin, ctx->kpre1, B.pre1, s);
+    B.d_split1 = dcopy_pinned(ctx->pin, ctx->ksplit1, B.split1, s);
+    launch_gather_rows(P.Dbra, pc.d_pairs, B.d_list, B.d_col1, L, P.ncolD, P.Dket, s);
+    ctx->launches++;
+    // the buffer's rows changed: its cached digit slices are stale
+    split_forget(ctx->split, P.Dket, P.Dket + P.M * P.ncolD);
+}
 
 // Bra-ket symmetry across row batches (ClassPlan::mirror): a kept block
 // (AB|CD) with CD in a later batch whose (CD|AB) is kept too is computed once,
@@ -864,8 +907,18 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
     }
     B.b1 = b1;
     B.rows = rows;
-    B.kmax = kmax;
     B.row0 = pc.h_pairs[pc.bra_order[b0]].rowoff;
+    B.bras.assign(pc.bra_order.begin() + b0, pc.bra_order.begin() + b1);
+    // W columns per bra row: its kept ket prefix, in the batch's own ket list
+    // when the batches keep bra-ket symmetry
+    const std::vector<long long> *krow = &P.Krow;
+    if (P.mirror) {
+        batch_kets_prepare(ctx, P, B);
+        krow = &B.krow1;
+        kmax = 0;
+        for (int sp : B.bras) kmax = std::max(kmax, B.krow1[sp]);
+    }
+    B.kmax = kmax;
     B.ldw = std::max<long long>(kmax, 1) * mult;
     B.W = (double *)ctx->W.get((size_t)std::max<long long>(rows, 1) * mult * B.ldw * sizeof(double));
     B.ldwc = std::max<long long>(kmax, 1);
@@ -878,8 +931,8 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
     prm.E2 = P.precision == QDT_SPLIT ? pc.d_E2 : nullptr;
     prm.E1 = P.precision == QDT_SPLIT ? pc.d_E1 : nullptr;
     prm.boys = (const double *)ctx->boys.p;
-    prm.ket_sp = P.ketsp;
-    prm.ket_col = P.ketcol;
+    prm.ket_sp = P.mirror ? B.d_list : P.ketsp;
+    prm.ket_col = P.mirror ? B.d_col1 : P.ketcol;
     prm.W = B.W;
     prm.ldw = B.ldw;
     prm.row0 = B.row0;
@@ -888,19 +941,18 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
     prm.Wc = B.Wc;
     prm.ldwc = B.ldwc;
     prm.sym = P.one_batch ? 1 : (P.mirror ? 2 : 0);
-    prm.ket_pos = P.d_kpos;
-    prm.prefix = P.prefix;
+    prm.ket_pos = P.mirror ? B.d_pos1 : P.d_kpos;
+    prm.prefix = P.mirror ? B.d_pre1 : P.prefix;
     prm.bra_pos = pc.d_bra_pos;
     prm.b0 = b0;
     prm.b1 = b1;
-    B.bras.assign(pc.bra_order.begin() + b0, pc.bra_order.begin() + b1);
     // per-tile K extents (rows in units of W rows)
     const long long Wrows = rows * mult;
     B.kt.assign((Wrows + TMr - 1) / TMr, 0);
     for (int k = b0; k < b1; ++k) {
         const PairDev &pr = pc.h_pairs[pc.bra_order[k]];
         long long r0 = (pr.rowoff - B.row0) * mult, r1 = (pr.rowoff - B.row0 + pr.nfp) * mult;
-        long long kk = P.Krow[pc.bra_order[k]] * mult;
+        long long kk = (*krow)[pc.bra_order[k]] * mult;
         for (long long t = r0 / TMr; t <= (r1 - 1) / TMr; ++t) B.kt[t] = std::max(B.kt[t], kk);
     }
     B.d_kt = dcopy_pinned(ctx->pin, ctx->ktile, B.kt, s);
@@ -909,7 +961,7 @@ void batch_prepare(qdt_ctx *ctx, const ClassPlan &P, int b0, RowBatch &B) {
         for (int k = b0; k < b1; ++k) {
             const PairDev &pr = pc.h_pairs[pc.bra_order[k]];
             long long r0 = pr.rowoff - B.row0, r1 = r0 + pr.nfp;
-            for (long long t = r0 / TMr; t <= (r1 - 1) / TMr; ++t) B.kg[t] = std::max(B.kg[t], P.Krow[pc.bra_order[k]]);
+            for (long long t = r0 / TMr; t <= (r1 - 1) / TMr; ++t) B.kg[t] = std::max(B.kg[t], (*krow)[pc.bra_order[k]]);
         }
         B.d_kg = dcopy_pinned(ctx->pin, ctx->ktile2, B.kg, s);
     } else {
@@ -957,7 +1009,8 @@ void batch_stats(qdt_ctx *ctx, const ClassPlan &P, const RowBatch &B, long long 
     st->flops_half1 += 2.0 * f * ncols;
     if (P.ls && P.cr.gaunt) {
         double fg = 0;
-        for (int k = B.b0; k < B.b1; ++k) fg += (double)pc.h_pairs[pc.bra_order[k]].nfp * P.Krow[pc.bra_order[k]];
+        const std::vector<long long> &kr = P.mirror ? B.krow1 : P.Krow;
+        for (int k = B.b0; k < B.b1; ++k) fg += (double)pc.h_pairs[pc.bra_order[k]].nfp * kr[pc.bra_order[k]];
         st->flops_half1 += 2.0 * fg * 3 * width;
     }
     if (P.mirror) {         // the transposed blocks into the later rows
@@ -1195,10 +1248,13 @@ void run_batches(qdt_ctx *ctx, ClassPlan &P, long long c0, long long c1, qdt_sta
         const EriParams *d_prm = dcopy_pinned(ctx->pin, ctx->prms, std::vector<EriParams>{B.prm}, s);
         const EriShape shape{pc.maxnfp, pc.maxLab, pc.maxnpp};
         const bool df = B.prm.E2 != nullptr;
-        const EriLaunch how = eri_launch_for(ctx, pc, shape, B.prm.gauge != 0, df, d_prm, B.bras, P.h_prefix, s);
+        const std::vector<int> &pre = P.mirror ? B.pre1 : P.h_prefix;       // in the kernel's ket list
+        const EriLaunch how = eri_launch_for(ctx, pc, shape, B.prm.gauge != 0, df, d_prm, B.bras, pre, s);
         EriTask *d_tk = nullptr;
-        const int ntiles = launch_build_tiles(ctx, tile_order(pc, B.bras, how.order), P.h_prefix,
-                                              df ? &P.h_split : nullptr, P.prefix, P.d_split, how.kets, d_tk, s);
+        const int ntiles = launch_build_tiles(ctx, tile_order(pc, B.bras, how.order), pre,
+                                              df ? (P.mirror ? &B.split1 : &P.h_split) : nullptr,
+                                              P.mirror ? B.d_pre1 : P.prefix, P.mirror ? B.d_split1 : P.d_split,
+                                              how.kets, d_tk, s);
         int te = tm.n; tm.mark();
         launch_zero(B.W, B.rows * P.mult * B.ldw, s);
         if (B.Wc) launch_zero(B.Wc, B.rows * B.ldwc, s);
@@ -1569,7 +1625,8 @@ void release_workspace(qdt_ctx *c) {
                     &c->prefix, &c->ktile, &c->tasks, &c->O, &c->partial, &c->stage, &c->kpos, &c->prms,
                     &c->next, &c->ktile2, &c->qcols, &c->qWL, &c->qWS, &c->qT1, &c->qT, &c->qVf, &c->qkt[0],
                     &c->qkt[1], &c->qkt[2], &c->W2, &c->Wc2, &c->ktile3, &c->ktile4, &c->col2, &c->ketsp2,
-                    &c->ketcol2, &c->Dbra2, &c->tbras, &c->toff, &c->dsplit};
+                    &c->ketcol2, &c->Dbra2, &c->tbras, &c->toff, &c->dsplit, &c->klist, &c->kcol1, &c->kpos1,
+                    &c->kpre1, &c->ksplit1};
     for (DBuf *b : bufs) b->release();
     split_release(c->split);
     for (GraphEntry &g : c->graph) {
@@ -1626,7 +1683,8 @@ void qdt_destroy(qdt_ctx *c) {
                     &c->btasks[3], &c->bnext[0], &c->bnext[1], &c->bnext[2], &c->bnext[3], &c->qcols,
                     &c->qWL, &c->qWS, &c->qT1, &c->qT, &c->qVf, &c->qCr1, &c->qCr2, &c->qkt[0],
                     &c->qkt[1], &c->qkt[2], &c->W2, &c->Wc2, &c->ktile3, &c->ktile4, &c->col2, &c->ketsp2,
-                    &c->ketcol2, &c->Dbra2, &c->tbras, &c->toff, &c->dsplit};
+                    &c->ketcol2, &c->Dbra2, &c->tbras, &c->toff, &c->dsplit, &c->klist, &c->kcol1, &c->kpos1,
+                    &c->kpre1, &c->ksplit1};
     for (DBuf *b : bufs) b->release();
     for (int k = 0; k < 2; ++k) {
         c->cb[k].pairs.release(); c->cb[k].pp.release(); c->cb[k].E.release(); c->cb[k].E2.release(); c->cb[k].E1.release();

@@ -1,5 +1,6 @@
-"""Host planning of the split form's plain-FP32 integrals (csrc/plan.h),
-compiled with the host compiler and checked on seeded random classes."""
+"""Host planning (csrc/plan.h) -- the split form's plain-FP32 integrals and the
+ket lists of row batches with bra-ket symmetry -- compiled with the host
+compiler and checked on seeded random classes."""
 import os
 import shutil
 import subprocess
