@@ -506,6 +506,28 @@ void launch_zero(double *p, long long n, cudaStream_t s) {
     QDT_CHECK_LAUNCH();
 }
 
+// Integral rows zeroed only as far as a contraction reads them: row r up to
+// the larger K extent of the two 64-row tiles of its 128-row tile, rounded up
+// to 64 (the split form's row tiles are 128 rows and its K subtiles 64 wide),
+// at most ld.  One CTA per row.
+__global__ void zero_rows_kernel(double *W, long long ld, long long rows, const long long *kt64, long long nt64) {
+    const long long r = blockIdx.x;
+    if (r >= rows) return;
+    const long long t = (r / 128) * 2;
+    long long e = kt64[t];
+    if (t + 1 < nt64) e = max(e, kt64[t + 1]);
+    e = min(ld, (e + 63) / 64 * 64);
+    double *row = W + r * ld;
+    for (long long k = threadIdx.x; k < e; k += blockDim.x) row[k] = 0.0;
+}
+
+void launch_zero_rows(double *W, long long ld, long long rows, const long long *kt64, long long nt64,
+                      cudaStream_t s) {
+    if (rows <= 0 || ld <= 0) return;
+    zero_rows_kernel<<<(unsigned)rows, 256, 0, s>>>(W, ld, rows, kt64, nt64);
+    QDT_CHECK_LAUNCH();
+}
+
 // ---------------------------------------------------------------- packing
 // out[t][parts^2], t = pq nP - pq(pq-1)/2 + (rs - pq) for pq <= rs:
 // out[t][parts i + j] = O[parts pq + i][parts rs + j]  (parts 4: Kramers pairs,

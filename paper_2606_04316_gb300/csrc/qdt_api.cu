@@ -1256,10 +1256,14 @@ void run_batches(qdt_ctx *ctx, ClassPlan &P, long long c0, long long c1, qdt_sta
                                               P.mirror ? B.d_pre1 : P.prefix, P.mirror ? B.d_split1 : P.d_split,
                                               how.kets, d_tk, s);
         int te = tm.n; tm.mark();
-        launch_zero(B.W, B.rows * P.mult * B.ldw, s);
-        if (B.Wc) launch_zero(B.Wc, B.rows * B.ldwc, s);
-        if (B.W2) launch_zero(B.W2, B.rows2 * P.mult * B.ldw2, s);
-        if (B.Wc2) launch_zero(B.Wc2, B.rows2 * B.ld2, s);
+        if (P.quarter) {    // the quarter route lays out whole rows
+            launch_zero(B.W, B.rows * P.mult * B.ldw, s);
+        } else {            // the rest reads each row tile only as far as its K extent
+            launch_zero_rows(B.W, B.ldw, B.rows * P.mult, B.d_kt, (long long)B.kt.size(), s);
+            if (B.Wc) launch_zero_rows(B.Wc, B.ldwc, B.rows, B.d_kg, (long long)B.kg.size(), s);
+        }
+        if (B.W2) launch_zero_rows(B.W2, B.ldw2, B.rows2 * P.mult, B.d_kt2, (long long)B.kt2.size(), s);
+        if (B.Wc2) launch_zero_rows(B.Wc2, B.ld2, B.rows2, B.d_kg2, (long long)B.kg2.size(), s);
         launch_eri(d_prm, d_tk, ntiles, (int *)ctx->next.get(sizeof(int)), shape, B.prm.gauge != 0, df, how, s);
         ctx->launches += 2 + (B.Wc ? 1 : 0);
         batch_stats(ctx, P, B, c1 - c0, st);

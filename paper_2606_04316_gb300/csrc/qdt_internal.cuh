@@ -259,6 +259,10 @@ void launch_pack(const double *O, long long ldo, int nP, int parts, double *out,
 // n_units: Kramers pairs (ku false, 2 n spinors) or spinors (ku true)
 void launch_unpack(const double *packed, int n_units, int gaunt_like, bool ku, double *full, cudaStream_t s);
 void launch_zero(double *p, long long n, cudaStream_t s);
+// rows x ld integral rows, zeroed as far as the contractions read them (the
+// K extents kt64 of its 64-row tiles, nt64 of them)
+void launch_zero_rows(double *W, long long ld, long long rows, const long long *kt64, long long nt64,
+                      cudaStream_t s);
 // coefficient rows of the internal small-component basis: row r = in[m0[r]] (+ in[m1[r]])
 // Eq. RKB: c^S[nL][n][4] -> derivative-function coefficients [3 nL][n][4].
 void launch_rkb_map(const double *in, long long nL, long long n, double c_light, double *out,
