@@ -229,8 +229,13 @@ size_t qdt_packed_size(const qdt_ctx *ctx, unsigned blocks, int k_begin, int k_e
  * variable QDT_F32_BUDGET sets the budget, 0 turns it off; stats report the
  * quartets and the bound).  Held to 1e-10 Eh of the FP64 form.
  * `out` (host or device, caller-owned) receives qdt_packed_size() bytes;
- * `out_bytes` must be at least that.  Device scratch is allocated and kept by
- * the context between calls.  `stats` may be NULL.
+ * `out_bytes` must be at least that.  Device scratch, and page-locked host
+ * memory that stages the call's uploads, are allocated and kept by the
+ * context between calls; the call starts by synchronising the context's
+ * stream.  A class whose integral rows do not fit the device runs in row
+ * batches that keep bra-ket symmetry (environment: QDT_W_BUDGET=bytes forces
+ * batches of at most that size, QDT_BATCH_SYM=0 turns the symmetry across
+ * batches off).  `stats` may be NULL.
  */
 int qdt_transform(qdt_ctx *ctx, unsigned blocks, int k_begin, int k_end, double schwarz_tau,
                   int precision, double *out, size_t out_bytes, qdt_stats *stats);
