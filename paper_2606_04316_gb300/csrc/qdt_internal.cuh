@@ -158,8 +158,11 @@ struct EriParams {
     const float2 *E2;           // E as FP32 pairs: non-null selects the compensated FP32 contraction
     const float *E1;            // fl32(E), read by the tiles run in plain FP32
     const double *boys;         // [kBoysGrid][kBoysCols], followed by the same as floats
-    const int *ket_sp;          // shell pair id at each sorted ket position
-    const long long *ket_col;   // first column of each sorted ket position
+    // the ket list the tiles index: the w-sorted ket order of the class, or in
+    // row batches with bra-ket symmetry the batch's own list (plan.h
+    // batch_kets); positions, prefixes and columns below are in that list
+    const int *ket_sp;          // shell pair id at each ket position
+    const long long *ket_col;   // first column of each ket position
     double *W;                  // output rows
     long long ldw;
     long long row0;             // bra-order row of W's first row
@@ -176,8 +179,8 @@ struct EriParams {
     // contracts into the later rows; of an earlier batch, skipped (its
     // transpose came from W2 of that batch).
     int sym;
-    const int *ket_pos;         // sorted ket position of every pair id
-    const int *prefix;          // kept ket prefix length of every pair id
+    const int *ket_pos;         // ket position of every pair id in the list (sym 2: of the batch's pairs)
+    const int *prefix;          // kept ket prefix length of every pair id, in list positions
     const int *bra_pos;         // sym 2: bra position of every pair id
     int b0, b1;                 // sym 2: this batch's bra positions
     double *W2;                 // sym 2: transposed blocks for later rows (gauge: 9 components)
